@@ -1,0 +1,203 @@
+/* gs.h -- C ABI of the GB300 (sm_103a) differentiable Gaussian-splatting rasterizer.
+ *
+ * The library renders RGB, depth, alpha and an n_feat-channel feature map of a set of
+ * 3D Gaussians seen by a pinhole camera, and back-propagates into every Gaussian
+ * parameter and the 6-DoF camera pose.  It implements the rasterizer under the X-GS
+ * Perceiver (arxiv 2603.09632):
+ *   - Gaussians Theta = {mu, Sigma, alpha, c} with Sigma = R S S^T R^T   (App. A)
+ *   - EWA projection Sigma' = J W Sigma W^T J^T                          (App. A)
+ *   - front-to-back blending C = sum_i c_i a'_i prod_{j<i}(1 - a'_j)     (Eq. 1, App. B)
+ *   - depth by substituting c_i -> d_i (App. B), features c_i -> f_i (Sec. 3.1)
+ *   - gradients for mapping (Eq. 3) and tracking (Eq. 2, App. B)
+ *
+ * Conventions (all inputs are plain pointers; no PyTorch types cross this boundary):
+ *   - Pointers named "device" must point to memory on the workspace's device.  The
+ *     caller owns every input and output buffer; the library owns the workspace.
+ *   - Inputs are post-activation: scales > 0, opacities in [0,1], quaternions (w,x,y,z)
+ *     non-zero and not necessarily unit (they are normalised inside).
+ *   - Camera: OpenCV axes (x right, y down, z forward); R (row-major) and t map world to
+ *     camera; pixel (x, y) is sampled at its centre (x + 0.5, y + 0.5); Gaussians with
+ *     camera-space depth <= near_z are culled.  Tiles are 16 x 16 pixels.
+ *   - Image outputs are float32, channel-major: rgb[3][H][W], depth[H][W], alpha[H][W],
+ *     feat[n_feat][H][W].  Any output pointer may be NULL (not written).
+ *   - Every call is asynchronous on the given CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream) unless its comment says it synchronises.
+ *   - Errors are returned, never thrown or aborted.  Errors that kernels detect (an
+ *     instance count above the reserved capacity in the no-sync path) set a device status
+ *     word; gs_workspace_status() reads and clears it.
+ *   - Calls on one workspace must be issued from one host thread at a time and kept in
+ *     stream order: gs_project -> gs_bin_tiles -> gs_render_fwd -> gs_render_bwd.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_ARG = 1,          /* invalid argument (null pointer, size, unsupported option) */
+  GS_ERR_OOM = 2,          /* device allocation failed */
+  GS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  GS_ERR_DEVICE = 4,       /* a kernel reported an error through the device status word */
+  GS_ERR_TIMEOUT = 5,      /* a bounded wait expired */
+  GS_ERR_BUSY = 6,         /* request not finished yet (serving poll) */
+  GS_ERR_OVER_BUDGET = 7,  /* request cannot fit the serving memory budget */
+  GS_ERR_STATE = 8         /* calls out of order (e.g. render before project/bin) */
+} gs_status;
+
+typedef enum { GS_F32 = 0, GS_BF16 = 1 } gs_dtype;
+
+/* Pinhole camera (App. A: "viewing transformation W" and the Jacobian J of the
+ * projection).  cx, cy are free; the synthetic workloads use W/2, H/2.
+ * stride/off_x/off_y select grid-sampled rendering (App. D, "Dynamic Grid Sampling"):
+ * stride 1 with offsets 0 renders every pixel. */
+typedef struct {
+  int32_t W, H;
+  float fx, fy, cx, cy;
+  float R[9];     /* world -> camera rotation, row-major */
+  float t[3];     /* world -> camera translation */
+  float near_z;   /* near-plane depth, > 0 (0.2 in the workloads) */
+  int32_t tile;   /* must be 16 */
+  int32_t stride, off_x, off_y;
+} gs_camera;
+
+/* Scene (App. A parameter set Theta plus the per-Gaussian feature vector f_i of Sec. 3.1).
+ * All arrays are device pointers, row-major, 16-byte aligned. */
+typedef struct {
+  int64_t n;              /* number of Gaussians, 0 <= n < 2^31 */
+  int32_t sh_degree;      /* 0..3; K = (sh_degree+1)^2 coefficients per colour channel */
+  int32_t n_feat;         /* 0..64 feature channels */
+  int32_t feat_dtype;     /* gs_dtype of feats */
+  const float* means;     /* [n][3] world positions */
+  const float* scales;    /* [n][3] > 0 */
+  const float* quats;     /* [n][4] (w, x, y, z) */
+  const float* opacities; /* [n] in [0, 1] */
+  const float* sh;        /* [n][K][3] real SH coefficients, (l, m = -l..l) order */
+  const void* feats;      /* [n][n_feat] float32 or bfloat16 */
+} gs_scene;
+
+typedef struct gs_workspace gs_workspace;
+
+/* Counts of the last projection/binning and forward render (for roofline accounting). */
+typedef struct {
+  int64_t n;            /* Gaussians */
+  int64_t visible;      /* V: Gaussians with a non-empty tile rectangle */
+  int64_t instances;    /* I: (tile, Gaussian) pairs */
+  int64_t inst_eff;     /* I_eff: sum over tiles of the longest list prefix a pixel used */
+  int64_t pixels;       /* P */
+  int64_t tiles;        /* T */
+} gs_stats;
+
+/* Human-readable name of a status code (static string). */
+const char* gs_status_string(gs_status s);
+
+/* Create a workspace bound to CUDA device `device`.  *ws receives the handle.
+ * Errors: GS_ERR_ARG (ws NULL), GS_ERR_CUDA (bad device). */
+gs_status gs_workspace_create(gs_workspace** ws, int device);
+
+/* Free the workspace and all its device memory (synchronises the device). */
+void gs_workspace_destroy(gs_workspace* ws);
+
+/* Pre-allocate capacity for n_gauss Gaussians, n_instances tile instances, n_pixels pixels
+ * and n_feat channels, so that later calls allocate nothing (required for the no-sync
+ * path of gs_bin_tiles and for CUDA-graph capture).  Synchronous.  Errors: GS_ERR_OOM. */
+gs_status gs_workspace_reserve(gs_workspace* ws, int64_t n_gauss, int64_t n_instances,
+                               int64_t n_pixels);
+
+/* Synchronise `stream`, read and clear the device status word.  Returns GS_OK or
+ * GS_ERR_DEVICE (e.g. the instance count exceeded the reserved capacity). */
+gs_status gs_workspace_status(gs_workspace* ws, void* stream);
+
+/* a1. EWA projection and SH colour, one thread per Gaussian (App. A, Sigma and Sigma';
+ * SH colour along the view direction from the camera centre).  Writes, into the
+ * workspace, each Gaussian's 2D mean, conic (inverse of Sigma' + 0.3 I), depth, colour,
+ * tile rectangle (3-sigma bound) and tile count.  Culled Gaussians (depth <= near_z,
+ * degenerate Sigma', empty rectangle) get no tiles.  Grows the workspace if needed. */
+gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
+                     void* stream);
+
+/* a2. Tile/depth binning ("depth-sorted", Eq. 1).  Produces, per 16x16 tile, the list
+ * of Gaussians covering it sorted by (depth, id), with a hand-written LSD radix sort
+ * (depth sort of the visible Gaussians, then a stable sort of the instances by tile).
+ * If n_instances_out is non-NULL the call synchronises the stream once to read the
+ * instance count I, grows the workspace if needed and stores I there.  If it is NULL
+ * the call never synchronises: the reserved instance capacity must be large enough,
+ * otherwise the excess is dropped and the device status word records the overflow. */
+gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream);
+
+/* a3. Forward rendering (Eq. 1 front-to-back alpha blending; depth, App. B; features,
+ * Sec. 3.1), one CTA per tile.  Blending skips a Gaussian with alpha < 1/255, caps alpha
+ * at 0.99 and stops before a Gaussian that would take transmittance below 1e-4;
+ * alpha = 1 - T_final.  Outputs are device pointers (see conventions), any may be NULL.
+ * The per-pixel final transmittance and contributor count are kept for gs_render_bwd.
+ * scene and cam must be those given to gs_project. */
+gs_status gs_render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
+                        float* rgb, float* depth, float* alpha, float* feat, void* stream);
+
+/* a4 + a5. Backward of gs_render_fwd (App. B: the rasterizer is differentiable; Eq. 2
+ * tracking, Eq. 3 mapping).  Inputs are the upstream gradients of the four images (device,
+ * same layout as the outputs; NULL = zero).  Outputs (device, overwritten, zero for culled
+ * Gaussians): g_means [n][3], g_scales [n][3], g_quats [n][4] (w.r.t. the raw quaternion),
+ * g_opac [n], g_sh [n][K][3], g_feats [n][n_feat] (float32 whatever feat_dtype is), and
+ * g_pose6 [6] = dL/dxi of the left twist perturbation T <- Exp(xi) T, xi = (rho, phi).
+ * Any output may be NULL (not written).  Must follow gs_render_fwd on the same
+ * workspace with the same scene and camera. */
+gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
+                        const float* g_rgb, const float* g_depth, const float* g_alpha,
+                        const float* g_feat, float* g_means, float* g_scales, float* g_quats,
+                        float* g_opac, float* g_sh, float* g_feats, float* g_pose6,
+                        void* stream);
+
+/* Upstream gradient of the L1 loss scale * sum|pred - target| (the distillation loss of
+ * the semantic workload): grad = scale * sign(pred - target), 0 where equal.  Device
+ * pointers, n elements.  May alias grad == pred. */
+gs_status gs_l1_grad(const float* pred, const float* target, int64_t n, float scale,
+                     float* grad, void* stream);
+
+/* ---- introspection (synchronous; host pointers) ---------------------------------- */
+
+/* Counts of the last gs_project/gs_bin_tiles/gs_render_fwd.  inst_eff is computed by a
+ * small reduction over the per-pixel contributor counts.  Synchronises `stream`. */
+gs_status gs_get_stats(gs_workspace* ws, gs_stats* out, void* stream);
+
+/* Copy the sorted instance list to host: tile id and Gaussian id per instance, at most
+ * cap entries; *n_out receives I.  ranges_out (may be NULL) receives 2*T uint32
+ * [start, end) per tile.  Synchronises `stream`. */
+gs_status gs_get_instances(gs_workspace* ws, uint32_t* tiles_out, uint32_t* ids_out,
+                           int64_t cap, int64_t* n_out, uint32_t* ranges_out, void* stream);
+
+/* Copy the projection of the last gs_project to host (arrays of n entries; any NULL):
+ * mean2d [n][2], conic [n][3], depth [n], rgb [n][3], rect [n][4] = (x0, y0, x1, y1)
+ * tiles, all zero for culled Gaussians.  Synchronises `stream`. */
+gs_status gs_get_projection(gs_workspace* ws, float* mean2d, float* conic, float* depth,
+                            float* rgb, int32_t* rect, void* stream);
+
+/* Copy the per-pixel final transmittance and contributor count of the last forward
+ * render to host ([H][W] each; either may be NULL).  Synchronises `stream`. */
+gs_status gs_get_pixel_state(gs_workspace* ws, float* T_final, uint32_t* n_contrib,
+                             void* stream);
+
+/* ---- stage timing (CUDA events on the launching stream) ---------------------------- */
+
+enum { GS_TIMER_PROJECT = 0, GS_TIMER_BIN = 1, GS_TIMER_FWD = 2, GS_TIMER_BWD_RASTER = 3,
+       GS_TIMER_BWD_PROJECT = 4, GS_NUM_TIMERS = 5 };
+
+/* Enable (1) or disable (0) event timing of the stages above.  While enabled, each stage
+ * records a CUDA event pair around its kernels on the caller's stream. */
+gs_status gs_timing_enable(gs_workspace* ws, int enable);
+
+/* Synchronise, add up the elapsed times of all recorded event pairs and reset them.
+ * ms_out[GS_NUM_TIMERS] receives total milliseconds, count_out[GS_NUM_TIMERS] (may be
+ * NULL) the number of timed launches of each stage. */
+gs_status gs_timing_collect(gs_workspace* ws, double* ms_out, int64_t* count_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libgs (include/gs.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and forwards torch
+tensors as raw device pointers; all computation happens in the CUDA library.  There is
+no fallback: if ``libgs.so`` cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgs.so")
+
+GS_OK, GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_DEVICE = 0, 1, 2, 3, 4
+GS_ERR_TIMEOUT, GS_ERR_BUSY, GS_ERR_OVER_BUDGET, GS_ERR_STATE = 5, 6, 7, 8
+GS_F32, GS_BF16 = 0, 1
+GS_TIMER_NAMES = ("project", "bin", "fwd", "bwd_raster", "bwd_project")
+GS_NUM_TIMERS = len(GS_TIMER_NAMES)
+
+
+class GSError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class gs_camera(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("R", C.c_float * 9), ("t", C.c_float * 3),
+                ("near_z", C.c_float), ("tile", C.c_int32), ("stride", C.c_int32),
+                ("off_x", C.c_int32), ("off_y", C.c_int32)]
+
+
+class gs_scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32), ("n_feat", C.c_int32),
+                ("feat_dtype", C.c_int32), ("means", C.c_void_p), ("scales", C.c_void_p),
+                ("quats", C.c_void_p), ("opacities", C.c_void_p), ("sh", C.c_void_p),
+                ("feats", C.c_void_p)]
+
+
+class gs_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("visible", C.c_int64), ("instances", C.c_int64),
+                ("inst_eff", C.c_int64), ("pixels", C.c_int64), ("tiles", C.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgs.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python -m paper_2603_09632_gb300._build")
+    L = C.CDLL(LIB_PATH)
+    P, i64, i32, st = C.c_void_p, C.c_int64, C.c_int, C.c_int
+    sig = {
+        "gs_status_string": ([st], C.c_char_p),
+        "gs_workspace_create": ([C.POINTER(C.c_void_p), i32], st),
+        "gs_workspace_destroy": ([P], None),
+        "gs_workspace_reserve": ([P, i64, i64, i64], st),
+        "gs_workspace_status": ([P, P], st),
+        "gs_project": ([P, P, P, P], st),
+        "gs_bin_tiles": ([P, P, P], st),
+        "gs_render_fwd": ([P, P, P, P, P, P, P, P], st),
+        "gs_render_bwd": ([P, P, P] + [P] * 4 + [P] * 7 + [P], st),
+        "gs_l1_grad": ([P, P, i64, C.c_float, P, P], st),
+        "gs_get_stats": ([P, P, P], st),
+        "gs_get_instances": ([P, P, P, i64, P, P, P], st),
+        "gs_get_projection": ([P, P, P, P, P, P, P], st),
+        "gs_get_pixel_state": ([P, P, P, P], st),
+        "gs_timing_enable": ([P, i32], st),
+        "gs_timing_collect": ([P, P, P], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def status_string(s: int) -> str:
+    return lib.gs_status_string(int(s)).decode()
+
+
+def _check(s, where):
+    if s != GS_OK:
+        raise GSError(s, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- value types
+
+def make_camera(W, H, fx, fy, cx, cy, R, t, near=0.2, stride=1, off_x=0, off_y=0) -> gs_camera:
+    c = gs_camera()
+    c.W, c.H, c.fx, c.fy, c.cx, c.cy = int(W), int(H), float(fx), float(fy), float(cx), float(cy)
+    R = np.asarray(R, np.float64).reshape(9)
+    t = np.asarray(t, np.float64).reshape(3)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    for k in range(3):
+        c.t[k] = float(t[k])
+    c.near_z, c.tile, c.stride, c.off_x, c.off_y = float(near), 16, int(stride), int(off_x), int(off_y)
+    return c
+
+
+class Scene:
+    """Device tensors of one scene plus the C struct pointing at them (post-activation)."""
+
+    def __init__(self, means, scales, quats, opacities, sh, feats=None):
+        dev = means.device
+        self.means = means.contiguous().float()
+        self.scales = scales.contiguous().float()
+        self.quats = quats.contiguous().float()
+        self.opacities = opacities.contiguous().float()
+        self.sh = sh.contiguous().float()
+        n = self.means.shape[0]
+        K = self.sh.shape[1] if self.sh.dim() == 3 else 1
+        deg = int(round(math.sqrt(K))) - 1
+        if (deg + 1) ** 2 != K:
+            raise ValueError("sh must be [n, (deg+1)^2, 3]")
+        if feats is None:
+            feats = torch.zeros((n, 0), device=dev, dtype=torch.float32)
+        self.feats = feats.contiguous()
+        if self.feats.dtype not in (torch.float32, torch.bfloat16):
+            raise ValueError("features must be float32 or bfloat16")
+        s = gs_scene()
+        s.n, s.sh_degree, s.n_feat = n, deg, int(self.feats.shape[1])
+        s.feat_dtype = GS_BF16 if self.feats.dtype == torch.bfloat16 else GS_F32
+        s.means, s.scales, s.quats = self.means.data_ptr(), self.scales.data_ptr(), self.quats.data_ptr()
+        s.opacities, s.sh = self.opacities.data_ptr(), self.sh.data_ptr()
+        s.feats = self.feats.data_ptr() if s.n_feat > 0 else None
+        self.c = s
+
+    @property
+    def n(self):
+        return int(self.c.n)
+
+    @property
+    def n_feat(self):
+        return int(self.c.n_feat)
+
+    @property
+    def sh_degree(self):
+        return int(self.c.sh_degree)
+
+
+class Workspace:
+    """Library-owned workspace (gs_workspace_create / gs_workspace_destroy)."""
+
+    def __init__(self, device=None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(torch.device("cuda", device).index if isinstance(device, int) else
+                          torch.device(device).index or 0)
+        h = C.c_void_p()
+        _check(lib.gs_workspace_create(C.byref(h), self.device), "gs_workspace_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib.gs_workspace_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- entry points
+
+def gs_workspace_reserve(ws, n_gauss, n_instances, n_pixels):
+    _check(lib.gs_workspace_reserve(ws.h, int(n_gauss), int(n_instances), int(n_pixels)),
+           "gs_workspace_reserve")
+
+
+def gs_workspace_status(ws, stream=None):
+    return lib.gs_workspace_status(ws.h, _stream(stream))
+
+
+def gs_project(scene, cam, ws, stream=None):
+    _check(lib.gs_project(C.byref(scene.c), C.byref(cam), ws.h, _stream(stream)), "gs_project")
+
+
+def gs_bin_tiles(ws, sync=True, stream=None):
+    """Returns the instance count when ``sync`` (one stream synchronisation), else None."""
+    if sync:
+        n = C.c_int64()
+        _check(lib.gs_bin_tiles(ws.h, C.byref(n), _stream(stream)), "gs_bin_tiles")
+        return int(n.value)
+    _check(lib.gs_bin_tiles(ws.h, None, _stream(stream)), "gs_bin_tiles")
+    return None
+
+
+def gs_render_fwd(scene, cam, ws, rgb=None, depth=None, alpha=None, feat=None, stream=None):
+    _check(lib.gs_render_fwd(C.byref(scene.c), C.byref(cam), ws.h, _ptr(rgb), _ptr(depth),
+                             _ptr(alpha), _ptr(feat), _stream(stream)), "gs_render_fwd")
+
+
+def gs_render_bwd(scene, cam, ws, g_rgb=None, g_depth=None, g_alpha=None, g_feat=None,
+                  g_means=None, g_scales=None, g_quats=None, g_opac=None, g_sh=None,
+                  g_feats=None, g_pose6=None, stream=None):
+    _check(lib.gs_render_bwd(C.byref(scene.c), C.byref(cam), ws.h, _ptr(g_rgb), _ptr(g_depth),
+                             _ptr(g_alpha), _ptr(g_feat), _ptr(g_means), _ptr(g_scales),
+                             _ptr(g_quats), _ptr(g_opac), _ptr(g_sh), _ptr(g_feats),
+                             _ptr(g_pose6), _stream(stream)), "gs_render_bwd")
+
+
+def gs_l1_grad(pred, target, scale, grad, stream=None):
+    _check(lib.gs_l1_grad(_ptr(pred), _ptr(target), int(pred.numel()), float(scale), _ptr(grad),
+                          _stream(stream)), "gs_l1_grad")
+
+
+def gs_get_stats(ws, stream=None) -> dict:
+    s = gs_stats()
+    _check(lib.gs_get_stats(ws.h, C.byref(s), _stream(stream)), "gs_get_stats")
+    return {k: int(getattr(s, k)) for k, _ in gs_stats._fields_}
+
+
+def gs_get_instances(ws, n_tiles, stream=None):
+    n = C.c_int64()
+    _check(lib.gs_get_instances(ws.h, None, None, 0, C.byref(n), None, _stream(stream)),
+           "gs_get_instances")
+    m = int(n.value)
+    tiles = np.zeros(m, np.uint32)
+    ids = np.zeros(m, np.uint32)
+    ranges = np.zeros((n_tiles, 2), np.uint32)
+    P = C.c_void_p
+    _check(lib.gs_get_instances(ws.h, P(tiles.ctypes.data), P(ids.ctypes.data), m, C.byref(n),
+                                P(ranges.ctypes.data), _stream(stream)), "gs_get_instances")
+    return tiles, ids, ranges
+
+
+def gs_get_projection(ws, n, stream=None):
+    out = dict(mean2d=np.zeros((n, 2), np.float32), conic=np.zeros((n, 3), np.float32),
+               depth=np.zeros(n, np.float32), rgb=np.zeros((n, 3), np.float32),
+               rect=np.zeros((n, 4), np.int32))
+    P = C.c_void_p
+    _check(lib.gs_get_projection(ws.h, *(P(out[k].ctypes.data) for k in
+                                         ("mean2d", "conic", "depth", "rgb", "rect")),
+                                 _stream(stream)), "gs_get_projection")
+    return out
+
+
+def gs_get_pixel_state(ws, H, W, stream=None):
+    T = np.zeros((H, W), np.float32)
+    nc = np.zeros((H, W), np.uint32)
+    P = C.c_void_p
+    _check(lib.gs_get_pixel_state(ws.h, P(T.ctypes.data), P(nc.ctypes.data), _stream(stream)),
+           "gs_get_pixel_state")
+    return T, nc
+
+
+def gs_timing_enable(ws, enable=True):
+    _check(lib.gs_timing_enable(ws.h, int(bool(enable))), "gs_timing_enable")
+
+
+def gs_timing_collect(ws) -> dict:
+    ms = (C.c_double * GS_NUM_TIMERS)()
+    cnt = (C.c_int64 * GS_NUM_TIMERS)()
+    _check(lib.gs_timing_collect(ws.h, ms, cnt), "gs_timing_collect")
+    return {name: (float(ms[k]), int(cnt[k])) for k, name in enumerate(GS_TIMER_NAMES)}

@@ -1,0 +1,527 @@
+// C ABI of libgs: workspace management and the entry points declared in include/gs.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+int padded_feat(int D);
+}
+
+using namespace gs;
+
+namespace {
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;   // elements
+  cudaError_t ensure(size_t n) {
+    if (n <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    const size_t m = std::max<size_t>(n, 16);
+    cudaError_t e = cudaMalloc(&p, m * sizeof(T));
+    if (e == cudaSuccess) cap = m;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+constexpr int kTimerRing = 256;
+
+}  // namespace
+
+struct gs_workspace {
+  int device = 0;
+  // per Gaussian
+  DevBuf<GaussRec> rec;
+  DevBuf<uint32_t> depth_key, ntiles, flags, vis_keys, vis_ids, alt_keys, alt_vals, offsets;
+  DevBuf<uint2> rect;
+  DevBuf<float> g2d;
+  DevBuf<float> pose_partials;
+  // per instance
+  DevBuf<uint32_t> inst_tile, inst_id, inst_tile2, inst_id2;
+  // per tile / pixel
+  DevBuf<uint2> ranges;
+  DevBuf<float> T_final;
+  DevBuf<uint32_t> n_contrib;
+  // scratch
+  DevBuf<uint32_t> hist, scan_temp, counters;
+  uint32_t* h_counters = nullptr;   // pinned mirror
+  // state
+  int64_t n = 0;
+  int W = 0, H = 0, TX = 0, TY = 0;
+  int stage = 0;             // 1 projected, 2 binned, 3 rendered
+  int64_t inst_bound = 0;    // host bound on I used for grids
+  const uint32_t* sorted_ids = nullptr;   // depth-sorted visible ids
+  const uint32_t* tile_sorted = nullptr;  // instance tiles after the tile sort
+  const uint32_t* id_sorted = nullptr;    // instance ids after the tile sort
+  // timing
+  bool timing = false;
+  cudaEvent_t ev[GS_NUM_TIMERS][kTimerRing][2];
+  int ev_count[GS_NUM_TIMERS] = {0};
+  bool ev_created = false;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+gs_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return GS_OK;
+  if (e == cudaErrorMemoryAllocation) return GS_ERR_OOM;
+  return GS_ERR_CUDA;
+}
+
+#define GS_TRY(expr)                              \
+  do {                                            \
+    cudaError_t _e = (expr);                      \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+gs_status check_scene(const gs_scene* sc) {
+  if (!sc) return GS_ERR_ARG;
+  if (sc->n < 0 || sc->n >= (int64_t(1) << 31)) return GS_ERR_ARG;
+  if (sc->sh_degree < 0 || sc->sh_degree > 3) return GS_ERR_ARG;
+  if (sc->n_feat < 0 || sc->n_feat > kMaxFeat) return GS_ERR_ARG;
+  if (sc->feat_dtype != GS_F32 && sc->feat_dtype != GS_BF16) return GS_ERR_ARG;
+  if (sc->n > 0) {
+    if (!sc->means || !sc->scales || !sc->quats || !sc->opacities || !sc->sh) return GS_ERR_ARG;
+    if (sc->n_feat > 0 && !sc->feats) return GS_ERR_ARG;
+    if (!aligned16(sc->means) || !aligned16(sc->scales) || !aligned16(sc->quats) ||
+        !aligned16(sc->sh) || (sc->feats && !aligned16(sc->feats)))
+      return GS_ERR_ARG;
+  }
+  return GS_OK;
+}
+
+gs_status make_cam(const gs_camera* c, CamDev* out) {
+  if (!c) return GS_ERR_ARG;
+  if (c->W <= 0 || c->H <= 0 || c->W > 65535 * kTile || c->H > 65535 * kTile) return GS_ERR_ARG;
+  if (c->tile != kTile) return GS_ERR_ARG;
+  if (!(c->fx > 0.f) || !(c->fy > 0.f) || !(c->near_z > 0.f)) return GS_ERR_ARG;
+  if (c->stride != 1 || c->off_x != 0 || c->off_y != 0) return GS_ERR_ARG;
+  out->W = c->W;
+  out->H = c->H;
+  out->TX = (c->W + kTile - 1) / kTile;
+  out->TY = (c->H + kTile - 1) / kTile;
+  out->fx = c->fx;
+  out->fy = c->fy;
+  out->cx = c->cx;
+  out->cy = c->cy;
+  std::memcpy(out->R, c->R, sizeof(out->R));
+  std::memcpy(out->t, c->t, sizeof(out->t));
+  out->near_z = c->near_z;
+  return GS_OK;
+}
+
+int bits_for(int64_t n_values) {
+  int b = 0;
+  while ((int64_t(1) << b) < n_values) ++b;
+  return b;
+}
+
+struct StageTimer {
+  gs_workspace* ws;
+  int which;
+  cudaStream_t st;
+  int slot = -1;
+  StageTimer(gs_workspace* w, int k, cudaStream_t s) : ws(w), which(k), st(s) {
+    if (ws->timing && ws->ev_count[k] < kTimerRing) {
+      slot = ws->ev_count[k]++;
+      cudaEventRecord(ws->ev[k][slot][0], st);
+    }
+  }
+  ~StageTimer() {
+    if (slot >= 0) cudaEventRecord(ws->ev[which][slot][1], st);
+  }
+};
+
+cudaError_t ensure_gauss(gs_workspace* ws, int64_t n) {
+  const size_t m = (size_t)std::max<int64_t>(n, 1);
+  cudaError_t e;
+  if ((e = ws->rec.ensure(m)) || (e = ws->depth_key.ensure(m)) || (e = ws->ntiles.ensure(m)) ||
+      (e = ws->flags.ensure(m)) || (e = ws->vis_keys.ensure(m)) || (e = ws->vis_ids.ensure(m)) ||
+      (e = ws->alt_keys.ensure(m)) || (e = ws->alt_vals.ensure(m)) ||
+      (e = ws->offsets.ensure(m)) || (e = ws->rect.ensure(m)) ||
+      (e = ws->g2d.ensure(m * kG2D)) ||
+      (e = ws->pose_partials.ensure((size_t)project_bwd_blocks(n) * 8)))
+    return e;
+  if ((e = ws->hist.ensure(radix_hist_words(n))) || (e = ws->scan_temp.ensure(scan_temp_words(n)))) return e;
+  return ws->scan_temp.ensure(scan_temp_words((int64_t)radix_hist_words(n)));
+}
+
+cudaError_t ensure_inst(gs_workspace* ws, int64_t cap) {
+  const size_t m = (size_t)std::max<int64_t>(cap, 1);
+  cudaError_t e;
+  if ((e = ws->inst_tile.ensure(m)) || (e = ws->inst_id.ensure(m)) ||
+      (e = ws->inst_tile2.ensure(m)) || (e = ws->inst_id2.ensure(m)))
+    return e;
+  if ((e = ws->hist.ensure(radix_hist_words(cap)))) return e;
+  return ws->scan_temp.ensure(scan_temp_words((int64_t)radix_hist_words(cap)));
+}
+
+cudaError_t ensure_pix(gs_workspace* ws, int64_t npix, int64_t ntiles) {
+  cudaError_t e;
+  if ((e = ws->T_final.ensure((size_t)std::max<int64_t>(npix, 1))) ||
+      (e = ws->n_contrib.ensure((size_t)std::max<int64_t>(npix, 1))))
+    return e;
+  return ws->ranges.ensure((size_t)std::max<int64_t>(ntiles, 1));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gs_status_string(gs_status s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_ARG: return "invalid argument";
+    case GS_ERR_OOM: return "out of device memory";
+    case GS_ERR_CUDA: return "CUDA runtime error";
+    case GS_ERR_DEVICE: return "device-side error";
+    case GS_ERR_TIMEOUT: return "timeout";
+    case GS_ERR_BUSY: return "busy";
+    case GS_ERR_OVER_BUDGET: return "over memory budget";
+    case GS_ERR_STATE: return "calls out of order";
+  }
+  return "unknown status";
+}
+
+gs_status gs_workspace_create(gs_workspace** out, int device) {
+  if (!out) return GS_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return GS_ERR_CUDA;
+  gs_workspace* ws = new (std::nothrow) gs_workspace();
+  if (!ws) return GS_ERR_OOM;
+  ws->device = device;
+  DeviceGuard g(device);
+  if (ws->counters.ensure(kCntNum) != cudaSuccess ||
+      cudaMemset(ws->counters.p, 0, kCntNum * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMallocHost(&ws->h_counters, kCntNum * sizeof(uint32_t)) != cudaSuccess) {
+    gs_workspace_destroy(ws);
+    return GS_ERR_OOM;
+  }
+  *out = ws;
+  return GS_OK;
+}
+
+void gs_workspace_destroy(gs_workspace* ws) {
+  if (!ws) return;
+  {
+    DeviceGuard g(ws->device);
+    cudaDeviceSynchronize();
+    ws->rec.release(); ws->depth_key.release(); ws->ntiles.release(); ws->flags.release();
+    ws->vis_keys.release(); ws->vis_ids.release(); ws->alt_keys.release(); ws->alt_vals.release();
+    ws->offsets.release(); ws->rect.release(); ws->g2d.release(); ws->pose_partials.release();
+    ws->inst_tile.release(); ws->inst_id.release(); ws->inst_tile2.release(); ws->inst_id2.release();
+    ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
+    ws->hist.release(); ws->scan_temp.release(); ws->counters.release();
+    if (ws->h_counters) cudaFreeHost(ws->h_counters);
+    if (ws->ev_created)
+      for (int k = 0; k < GS_NUM_TIMERS; ++k)
+        for (int s = 0; s < kTimerRing; ++s) {
+          cudaEventDestroy(ws->ev[k][s][0]);
+          cudaEventDestroy(ws->ev[k][s][1]);
+        }
+  }
+  delete ws;
+}
+
+gs_status gs_workspace_reserve(gs_workspace* ws, int64_t n_gauss, int64_t n_instances,
+                               int64_t n_pixels) {
+  if (!ws || n_gauss < 0 || n_instances < 0 || n_pixels < 0) return GS_ERR_ARG;
+  DeviceGuard g(ws->device);
+  GS_TRY(ensure_gauss(ws, n_gauss));
+  GS_TRY(ensure_inst(ws, n_instances));
+  GS_TRY(ensure_pix(ws, n_pixels, gs::ceil_div(n_pixels, 256) + 4096));
+  GS_TRY(cudaDeviceSynchronize());
+  return GS_OK;
+}
+
+gs_status gs_workspace_status(gs_workspace* ws, void* stream) {
+  if (!ws) return GS_ERR_ARG;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  GS_TRY(cudaMemcpyAsync(ws->h_counters, ws->counters.p, kCntNum * sizeof(uint32_t),
+                         cudaMemcpyDeviceToHost, st));
+  GS_TRY(cudaStreamSynchronize(st));
+  const uint32_t s = ws->h_counters[kCntStatus];
+  if (s) {
+    GS_TRY(cudaMemsetAsync(ws->counters.p + kCntStatus, 0, 4, st));
+    GS_TRY(cudaStreamSynchronize(st));
+    return GS_ERR_DEVICE;
+  }
+  return GS_OK;
+}
+
+gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws, void* stream) {
+  if (!ws) return GS_ERR_ARG;
+  gs_status s = check_scene(scene);
+  if (s != GS_OK) return s;
+  CamDev cd;
+  if ((s = make_cam(cam, &cd)) != GS_OK) return s;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  GS_TRY(ensure_gauss(ws, scene->n));
+  GS_TRY(ensure_pix(ws, (int64_t)cd.W * cd.H, (int64_t)cd.TX * cd.TY));
+  StageTimer tm(ws, GS_TIMER_PROJECT, st);
+  launch_project(*scene, cd, ws->rec.p, ws->depth_key.p, ws->ntiles.p, ws->rect.p, st);
+  GS_TRY(cudaGetLastError());
+  ws->n = scene->n;
+  ws->W = cd.W;
+  ws->H = cd.H;
+  ws->TX = cd.TX;
+  ws->TY = cd.TY;
+  ws->stage = 1;
+  return GS_OK;
+}
+
+gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream) {
+  if (!ws) return GS_ERR_ARG;
+  if (ws->stage < 1) return GS_ERR_STATE;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = ws->n;
+  const int ntl = ws->TX * ws->TY;
+  StageTimer tm(ws, GS_TIMER_BIN, st);
+  uint32_t* cnt = ws->counters.p;
+  // 1. visible compaction (id order), 2. depth sort
+  launch_compact_visible(ws->ntiles.p, ws->depth_key.p, n, ws->flags.p, ws->vis_keys.p,
+                         ws->vis_ids.p, cnt, ws->scan_temp.p, st);
+  const int which = radix_sort_pairs(cnt + kCntVisible, n, ws->vis_keys.p, ws->vis_ids.p,
+                                     ws->alt_keys.p, ws->alt_vals.p, 32, ws->hist.p,
+                                     ws->scan_temp.p, st);
+  const uint32_t* sorted_ids = which ? ws->alt_vals.p : ws->vis_ids.p;
+  // 3. tile counts in depth order -> offsets, I
+  launch_tile_offsets(sorted_ids, ws->ntiles.p, n, cnt, ws->offsets.p, ws->scan_temp.p, st);
+  int64_t bound;
+  if (n_instances_out) {
+    GS_TRY(cudaMemcpyAsync(ws->h_counters, cnt, kCntNum * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    GS_TRY(cudaStreamSynchronize(st));
+    bound = (int64_t)ws->h_counters[kCntInst];
+    GS_TRY(ensure_inst(ws, bound));
+    *n_instances_out = bound;
+  } else {
+    bound = (int64_t)ws->inst_tile.cap;
+  }
+  const int64_t cap = (int64_t)ws->inst_tile.cap;
+  // 4. emit instances, 5. stable sort by tile, 6. ranges
+  launch_emit_instances(sorted_ids, ws->rect.p, ws->offsets.p, n, ws->TX, cnt, cap,
+                        ws->inst_tile.p, ws->inst_id.p, st);
+  const int w2 = radix_sort_pairs(cnt + kCntInst, std::min(bound, cap), ws->inst_tile.p,
+                                  ws->inst_id.p, ws->inst_tile2.p, ws->inst_id2.p, bits_for(ntl),
+                                  ws->hist.p, ws->scan_temp.p, st);
+  ws->tile_sorted = w2 ? ws->inst_tile2.p : ws->inst_tile.p;
+  ws->id_sorted = w2 ? ws->inst_id2.p : ws->inst_id.p;
+  ws->sorted_ids = sorted_ids;
+  launch_tile_ranges(ws->tile_sorted, cnt, std::min(bound, cap), cap, ntl, ws->ranges.p, st);
+  GS_TRY(cudaGetLastError());
+  ws->inst_bound = std::min(bound, cap);
+  ws->stage = 2;
+  return GS_OK;
+}
+
+gs_status gs_render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws, float* rgb,
+                        float* depth, float* alpha, float* feat, void* stream) {
+  if (!ws) return GS_ERR_ARG;
+  gs_status s = check_scene(scene);
+  if (s != GS_OK) return s;
+  CamDev cd;
+  if ((s = make_cam(cam, &cd)) != GS_OK) return s;
+  if (ws->stage < 2 || scene->n != ws->n || cd.W != ws->W || cd.H != ws->H) return GS_ERR_STATE;
+  if (feat && scene->n_feat > 0 && !aligned16(feat)) return GS_ERR_ARG;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  StageTimer tm(ws, GS_TIMER_FWD, st);
+  launch_raster_fwd(cd, ws->rec.p, scene->feats, scene->feat_dtype, scene->n_feat, ws->ranges.p,
+                    ws->id_sorted, rgb, depth, alpha, scene->n_feat > 0 ? feat : nullptr,
+                    ws->T_final.p, ws->n_contrib.p, st);
+  GS_TRY(cudaGetLastError());
+  ws->stage = 3;
+  return GS_OK;
+}
+
+gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
+                        const float* g_rgb, const float* g_depth, const float* g_alpha,
+                        const float* g_feat, float* g_means, float* g_scales, float* g_quats,
+                        float* g_opac, float* g_sh, float* g_feats, float* g_pose6, void* stream) {
+  if (!ws) return GS_ERR_ARG;
+  gs_status s = check_scene(scene);
+  if (s != GS_OK) return s;
+  CamDev cd;
+  if ((s = make_cam(cam, &cd)) != GS_OK) return s;
+  if (ws->stage < 3 || scene->n != ws->n || cd.W != ws->W || cd.H != ws->H) return GS_ERR_STATE;
+  if (g_feats && !aligned16(g_feats)) return GS_ERR_ARG;
+  if (g_quats && !aligned16(g_quats)) return GS_ERR_ARG;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = scene->n;
+  const int D = scene->n_feat;
+  {
+    StageTimer tm(ws, GS_TIMER_BWD_RASTER, st);
+    if (n > 0) GS_TRY(cudaMemsetAsync(ws->g2d.p, 0, sizeof(float) * kG2D * (size_t)n, st));
+    if (g_feats && n > 0 && D > 0)
+      GS_TRY(cudaMemsetAsync(g_feats, 0, sizeof(float) * (size_t)n * D, st));
+    launch_raster_bwd(cd, ws->rec.p, scene->feats, scene->feat_dtype, D, ws->ranges.p,
+                      ws->id_sorted, ws->T_final.p, ws->n_contrib.p, g_rgb, g_depth, g_alpha,
+                      D > 0 ? g_feat : nullptr, ws->g2d.p, D > 0 ? g_feats : nullptr, st);
+    GS_TRY(cudaGetLastError());
+  }
+  {
+    StageTimer tm(ws, GS_TIMER_BWD_PROJECT, st);
+    launch_project_bwd(*scene, cd, ws->rec.p, ws->ntiles.p, ws->g2d.p, g_means, g_scales, g_quats,
+                       g_opac, g_sh, ws->pose_partials.p, g_pose6, st);
+    GS_TRY(cudaGetLastError());
+  }
+  return GS_OK;
+}
+
+gs_status gs_l1_grad(const float* pred, const float* target, int64_t n, float scale, float* grad,
+                     void* stream) {
+  if (n < 0 || (n > 0 && (!pred || !target || !grad))) return GS_ERR_ARG;
+  launch_l1_grad(pred, target, n, scale, grad, (cudaStream_t)stream);
+  GS_TRY(cudaGetLastError());
+  return GS_OK;
+}
+
+gs_status gs_get_stats(gs_workspace* ws, gs_stats* out, void* stream) {
+  if (!ws || !out) return GS_ERR_ARG;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ws->stage >= 3)
+    launch_inst_eff(ws->ranges.p, ws->n_contrib.p, ws->TX, ws->TY, ws->W, ws->H, ws->counters.p, st);
+  GS_TRY(cudaMemcpyAsync(ws->h_counters, ws->counters.p, kCntNum * sizeof(uint32_t),
+                         cudaMemcpyDeviceToHost, st));
+  GS_TRY(cudaStreamSynchronize(st));
+  out->n = ws->n;
+  out->visible = ws->stage >= 2 ? ws->h_counters[kCntVisible] : 0;
+  out->instances = ws->stage >= 2 ? ws->h_counters[kCntInst] : 0;
+  out->inst_eff = ws->stage >= 3 ? ws->h_counters[kCntInstEff] : 0;
+  out->pixels = (int64_t)ws->W * ws->H;
+  out->tiles = (int64_t)ws->TX * ws->TY;
+  return GS_OK;
+}
+
+gs_status gs_get_instances(gs_workspace* ws, uint32_t* tiles_out, uint32_t* ids_out, int64_t cap,
+                           int64_t* n_out, uint32_t* ranges_out, void* stream) {
+  if (!ws || cap < 0) return GS_ERR_ARG;
+  if (ws->stage < 2) return GS_ERR_STATE;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  GS_TRY(cudaMemcpyAsync(ws->h_counters, ws->counters.p, kCntNum * sizeof(uint32_t),
+                         cudaMemcpyDeviceToHost, st));
+  GS_TRY(cudaStreamSynchronize(st));
+  const int64_t I = std::min<int64_t>(ws->h_counters[kCntInst], ws->inst_bound);
+  if (n_out) *n_out = ws->h_counters[kCntInst];
+  const int64_t m = std::min(I, cap);
+  if (m > 0 && tiles_out)
+    GS_TRY(cudaMemcpyAsync(tiles_out, ws->tile_sorted, m * 4, cudaMemcpyDeviceToHost, st));
+  if (m > 0 && ids_out)
+    GS_TRY(cudaMemcpyAsync(ids_out, ws->id_sorted, m * 4, cudaMemcpyDeviceToHost, st));
+  if (ranges_out)
+    GS_TRY(cudaMemcpyAsync(ranges_out, ws->ranges.p, sizeof(uint2) * (size_t)ws->TX * ws->TY,
+                           cudaMemcpyDeviceToHost, st));
+  GS_TRY(cudaStreamSynchronize(st));
+  return GS_OK;
+}
+
+gs_status gs_get_projection(gs_workspace* ws, float* mean2d, float* conic, float* depth, float* rgb,
+                            int32_t* rect, void* stream) {
+  if (!ws) return GS_ERR_ARG;
+  if (ws->stage < 1) return GS_ERR_STATE;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = ws->n;
+  std::vector<GaussRec> rec((size_t)n);
+  std::vector<uint2> rc((size_t)n);
+  if (n > 0) {
+    GS_TRY(cudaMemcpyAsync(rec.data(), ws->rec.p, sizeof(GaussRec) * n, cudaMemcpyDeviceToHost, st));
+    GS_TRY(cudaMemcpyAsync(rc.data(), ws->rect.p, sizeof(uint2) * n, cudaMemcpyDeviceToHost, st));
+  }
+  GS_TRY(cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < n; ++i) {
+    const GaussRec& r = rec[i];
+    if (mean2d) { mean2d[2 * i] = r.r0.x; mean2d[2 * i + 1] = r.r0.y; }
+    if (conic) { conic[3 * i] = r.r0.z; conic[3 * i + 1] = r.r0.w; conic[3 * i + 2] = r.r1.x; }
+    if (depth) depth[i] = r.r1.z;
+    if (rgb) { rgb[3 * i] = r.r2.x; rgb[3 * i + 1] = r.r2.y; rgb[3 * i + 2] = r.r2.z; }
+    if (rect) {
+      rect[4 * i] = (int32_t)(rc[i].x & 0xFFFF);
+      rect[4 * i + 1] = (int32_t)(rc[i].x >> 16);
+      rect[4 * i + 2] = (int32_t)(rc[i].y & 0xFFFF);
+      rect[4 * i + 3] = (int32_t)(rc[i].y >> 16);
+    }
+  }
+  return GS_OK;
+}
+
+gs_status gs_get_pixel_state(gs_workspace* ws, float* T_final, uint32_t* n_contrib, void* stream) {
+  if (!ws) return GS_ERR_ARG;
+  if (ws->stage < 3) return GS_ERR_STATE;
+  DeviceGuard g(ws->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = (size_t)ws->W * ws->H;
+  if (T_final) GS_TRY(cudaMemcpyAsync(T_final, ws->T_final.p, P * 4, cudaMemcpyDeviceToHost, st));
+  if (n_contrib) GS_TRY(cudaMemcpyAsync(n_contrib, ws->n_contrib.p, P * 4, cudaMemcpyDeviceToHost, st));
+  GS_TRY(cudaStreamSynchronize(st));
+  return GS_OK;
+}
+
+gs_status gs_timing_enable(gs_workspace* ws, int enable) {
+  if (!ws) return GS_ERR_ARG;
+  DeviceGuard g(ws->device);
+  if (enable && !ws->ev_created) {
+    for (int k = 0; k < GS_NUM_TIMERS; ++k)
+      for (int s = 0; s < kTimerRing; ++s) {
+        GS_TRY(cudaEventCreate(&ws->ev[k][s][0]));
+        GS_TRY(cudaEventCreate(&ws->ev[k][s][1]));
+      }
+    ws->ev_created = true;
+  }
+  ws->timing = enable != 0;
+  return GS_OK;
+}
+
+gs_status gs_timing_collect(gs_workspace* ws, double* ms_out, int64_t* count_out) {
+  if (!ws || !ms_out) return GS_ERR_ARG;
+  DeviceGuard g(ws->device);
+  for (int k = 0; k < GS_NUM_TIMERS; ++k) {
+    double tot = 0.0;
+    for (int s = 0; s < ws->ev_count[k]; ++s) {
+      GS_TRY(cudaEventSynchronize(ws->ev[k][s][1]));
+      float ms = 0.f;
+      GS_TRY(cudaEventElapsedTime(&ms, ws->ev[k][s][0], ws->ev[k][s][1]));
+      tot += ms;
+    }
+    ms_out[k] = tot;
+    if (count_out) count_out[k] = ws->ev_count[k];
+    ws->ev_count[k] = 0;
+  }
+  return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,361 @@
+// a4: backward of the tile rasterizer (X-GS App. B: the rasterizer is differentiable;
+// Eq. 2 tracking and Eq. 3 mapping need dL/dTheta and dL/dT).
+//
+// Per pixel, with w_i = a_i T_i and T_i = prod_{j<i}(1 - a_j):
+//   dL/dc_i = w_i g_C,  dL/dd_i = w_i g_D,  dL/df_i = w_i g_F
+//   dL/da_i = T_i (g.x_i - s_i) + g_A T_final / (1 - a_i),   x_i = (c_i, d_i, f_i)
+//   s_{i-1} = a_i (g.x_i) + (1 - a_i) s_i   (scalar running sum behind i, s_last = 0)
+// and a_i = o_i exp(-sigma_i) gives dL/do_i and dL/dsigma_i, from which the conic and
+// 2D-mean gradients follow.
+//
+// One 256-thread CTA per tile walks the tile's list backwards from the longest pixel
+// prefix (max n_contrib), recovering T_i = T_{i+1} / (1 - a_i) from T_final, in batches
+// of B Gaussians.  Phase 1 (one thread per pixel) writes w, dL/dsigma and dL/do of each
+// (pixel, Gaussian) pair to shared memory.  Phase 2 reduces over the 256 pixels of the
+// tile: the feature gradient is the contraction W^T g_F done with 4x4 register blocks,
+// colour/depth/opacity sums and the pixel moments sum_p dL/dsigma * (1, x, y, xx, xy, yy)
+// (from which the conic and mean gradients are formed exactly) are warp reductions.
+// Each Gaussian then receives one 16-byte vector atomic per 4 quantities per tile.
+#include "gs_blend.cuh"
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kT = 256;        // threads = pixels per tile
+constexpr int kWS = kT + 4;    // row stride of the j-major pair arrays (floats)
+
+template <int DP>
+struct BwdCfg {
+  static constexpr int B = DP >= 64 ? 8 : 16;          // Gaussians per batch
+  static constexpr int ES = DP + 4;                     // row stride of s_E (floats)
+  static constexpr int JB = B / 4, CB = DP / 4;         // 4x4 blocks of the contraction
+  static constexpr int TASKS = JB * CB;
+  static constexpr int S = TASKS > 0 ? kT / TASKS : 1;  // pixel split per block
+  static constexpr int G = kT / B;                      // threads per Gaussian in phase 2b
+  static constexpr size_t smem_floats =
+      (size_t)kT * ES           // s_E: upstream feature gradient per pixel
+      + (size_t)3 * B * kWS     // s_W, s_GS, s_GO (j-major)
+      + (size_t)B * DP          // s_f: batch features
+      + (size_t)B * DP;         // s_outF: batch feature-gradient sums
+};
+
+template <int DP, bool BF16, int B>
+__device__ __forceinline__ void stage_batch_features(const void* __restrict__ feats, int D,
+                                                     const uint32_t* __restrict__ s_id, int cnt,
+                                                     float* __restrict__ s_f) {
+  for (int e = threadIdx.x; e < B * DP; e += kT) {
+    const int j = e / DP, c = e - j * DP;
+    float v = 0.f;
+    if (j < cnt && c < D) {
+      const int64_t idx = (int64_t)s_id[j] * D + c;
+      if constexpr (BF16)
+        v = __bfloat162float(static_cast<const __nv_bfloat16*>(feats)[idx]);
+      else
+        v = __ldg(static_cast<const float*>(feats) + idx);
+    }
+    s_f[e] = v;
+  }
+}
+
+__device__ __forceinline__ void red_add4(float* dst, float a, float b, float c, float d) {
+  atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a, b, c, d));
+}
+
+template <int DP, bool BF16>
+__global__ void __launch_bounds__(kT, 2)
+k_raster_bwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restrict__ feats, int D,
+             const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_id,
+             const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+             const float* __restrict__ g_rgb, const float* __restrict__ g_depth,
+             const float* __restrict__ g_alpha, const float* __restrict__ g_feat,
+             float* __restrict__ g2d, float* __restrict__ g_feats) {
+  using Cfg = BwdCfg<DP>;
+  constexpr int B = Cfg::B;
+  __shared__ float4 s_r0[B], s_r1[B], s_r2[B];
+  __shared__ uint32_t s_id[B];
+  __shared__ float4 s_E4[kT];                 // (g_r, g_g, g_b, g_depth) per pixel
+  __shared__ uint32_t s_maxn;
+  extern __shared__ __align__(16) float smem[];
+  float* s_E = smem;                          // [kT][ES]
+  float* s_W = s_E + kT * Cfg::ES;            // [B][kWS]
+  float* s_GS = s_W + B * kWS;
+  float* s_GO = s_GS + B * kWS;
+  float* s_f = s_GO + B * kWS;                // [B][DP]
+  float* s_outF = s_f + B * DP;               // [B][DP]
+
+  const int t = threadIdx.x;
+  const int tile = blockIdx.x;
+  const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
+  const int px = tx0 + (t & 15), py = ty0 + (t >> 4);
+  const bool inside = px < cam.W && py < cam.H;
+  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const int64_t HW = (int64_t)cam.W * cam.H;
+  const int64_t p = (int64_t)py * cam.W + px;
+  const uint2 rg = ranges[tile];
+  const int start = (int)rg.x;
+
+  // upstream gradients of this pixel
+  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, Tf = 1.f;
+  int nc = 0;
+  float gF[DP > 0 ? DP : 1];
+#pragma unroll
+  for (int c = 0; c < (DP > 0 ? DP : 1); ++c) gF[c] = 0.f;
+  if (inside) {
+    if (g_rgb) {
+      gC0 = g_rgb[p];
+      gC1 = g_rgb[HW + p];
+      gC2 = g_rgb[2 * HW + p];
+    }
+    if (g_depth) gD = g_depth[p];
+    if (g_alpha) gA = g_alpha[p];
+    Tf = T_final[p];
+    nc = (int)n_contrib[p];
+    if constexpr (DP > 0) {
+#pragma unroll
+      for (int c = 0; c < DP; ++c) gF[c] = c < D ? g_feat[c * HW + p] : 0.f;
+    }
+  }
+  if constexpr (DP > 0) {
+#pragma unroll
+    for (int c = 0; c < DP; c += 4)
+      *reinterpret_cast<float4*>(s_E + t * Cfg::ES + c) = make_float4(gF[c], gF[c + 1], gF[c + 2], gF[c + 3]);
+  }
+  s_E4[t] = make_float4(gC0, gC1, gC2, gD);
+  if (t == 0) s_maxn = 0;
+  __syncthreads();
+  if (nc > 0) atomicMax(&s_maxn, (uint32_t)nc);
+  __syncthreads();
+  const int maxn = (int)s_maxn;
+  if (rg.x + (uint32_t)maxn > rg.y) return;   // cannot happen for consistent inputs
+
+  float T = Tf, s_run = 0.f;
+  const float gAT = gA * Tf;
+
+  for (int b_end = maxn; b_end > 0; b_end -= B) {
+    const int b_start = max(0, b_end - B);
+    const int cnt = b_end - b_start;
+    if (t < cnt) {
+      const uint32_t id = inst_id[start + b_start + t];
+      const GaussRec g = rec[id];
+      s_r0[t] = g.r0;
+      s_r1[t] = g.r1;
+      s_r2[t] = g.r2;
+      s_id[t] = id;
+    }
+    if constexpr (DP > 0) {
+      for (int e = t; e < B * DP; e += kT) s_outF[e] = 0.f;
+    }
+    __syncthreads();
+    if constexpr (DP > 0) stage_batch_features<DP, BF16, B>(feats, D, s_id, cnt, s_f);
+    __syncthreads();
+
+    // ---- phase 1: per pixel, reverse over the batch
+    for (int j = B - 1; j >= 0; --j) {
+      float w = 0.f, gs = 0.f, go = 0.f;
+      if (j < cnt && b_start + j < nc) {
+        const float4 r0 = s_r0[j];
+        const float4 r1 = s_r1[j];
+        const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+        if (sigma >= 0.f) {
+          const float G = blend_gauss(sigma);
+          const float oG = __fmul_rn(r1.y, G);
+          const float a = fminf(kAlphaMax, oG);
+          if (a >= kAlphaMin) {
+            const float inv = __fdividef(1.f, 1.f - a);
+            T = T * inv;                        // T_i
+            w = a * T;
+            const float4 r2 = s_r2[j];
+            float dot = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r1.z;
+            if constexpr (DP > 0) {
+              const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
+#pragma unroll
+              for (int q = 0; q < DP / 4; ++q) {
+                const float4 f = f4[q];
+                dot = fmaf(gF[4 * q], f.x, dot);
+                dot = fmaf(gF[4 * q + 1], f.y, dot);
+                dot = fmaf(gF[4 * q + 2], f.z, dot);
+                dot = fmaf(gF[4 * q + 3], f.w, dot);
+              }
+            }
+            const float galpha = T * (dot - s_run) + gAT * inv;
+            s_run = a * dot + (1.f - a) * s_run;
+            if (oG <= kAlphaMax) {
+              go = galpha * G;
+              gs = -galpha * a;
+            }
+          }
+        }
+      }
+      s_W[j * kWS + t] = w;
+      s_GS[j * kWS + t] = gs;
+      s_GO[j * kWS + t] = go;
+    }
+    __syncthreads();
+
+    // ---- phase 2a: feature gradients, out[j][c] = sum_p W[j][p] g_F[p][c]
+    if constexpr (DP > 0) {
+      if (g_feats && t < Cfg::TASKS * Cfg::S) {
+        const int cb = t % Cfg::CB;
+        const int jb = (t / Cfg::CB) % Cfg::JB;
+        const int part = t / Cfg::TASKS;
+        constexpr int PP = kT / Cfg::S;     // pixels per part
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        const int p0 = part * PP;
+#pragma unroll 2
+        for (int q = p0; q < p0 + PP; q += 4) {
+          float4 wv[4], ev[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) wv[a] = *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) ev[b] = *reinterpret_cast<const float4*>(s_E + (q + b) * Cfg::ES + 4 * cb);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float wa[4] = {wv[a].x, wv[a].y, wv[a].z, wv[a].w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              acc[a][0] = fmaf(wa[b], ev[b].x, acc[a][0]);
+              acc[a][1] = fmaf(wa[b], ev[b].y, acc[a][1]);
+              acc[a][2] = fmaf(wa[b], ev[b].z, acc[a][2]);
+              acc[a][3] = fmaf(wa[b], ev[b].w, acc[a][3]);
+            }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            if (Cfg::S > 1)
+              atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
+            else
+              s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
+          }
+      }
+    }
+
+    // ---- phase 2b: per Gaussian sums over pixels (G threads per Gaussian, consecutive lanes)
+    {
+      constexpr int G = Cfg::G;
+      const int j = t / G, pg = t % G;
+      float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+      float so = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sz = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < kT / G; ++k) {
+        const int q = pg + k * G;
+        const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
+        const float4 e = s_E4[q];
+        const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;
+        m1 += gs;
+        mx = fmaf(gs, x, mx);
+        my = fmaf(gs, y, my);
+        mxx = fmaf(gs * x, x, mxx);
+        mxy = fmaf(gs * x, y, mxy);
+        myy = fmaf(gs * y, y, myy);
+        so += go;
+        sr = fmaf(w, e.x, sr);
+        sg = fmaf(w, e.y, sg);
+        sb = fmaf(w, e.z, sb);
+        sz = fmaf(w, e.w, sz);
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+        mx += __shfl_xor_sync(0xffffffffu, mx, o);
+        my += __shfl_xor_sync(0xffffffffu, my, o);
+        mxx += __shfl_xor_sync(0xffffffffu, mxx, o);
+        mxy += __shfl_xor_sync(0xffffffffu, mxy, o);
+        myy += __shfl_xor_sync(0xffffffffu, myy, o);
+        so += __shfl_xor_sync(0xffffffffu, so, o);
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+      }
+      if (pg == 0 && j < cnt) {
+        const float4 r0 = s_r0[j];
+        const float4 r1 = s_r1[j];
+        // moments are about the tile centre: pixel offset dx = x - uc with uc = u - centre
+        const float uc = r0.x - ((float)tx0 + 8.f), vc = r0.y - ((float)ty0 + 8.f);
+        const float A = r0.z, Bq = r0.w, C = r1.x;
+        const float sdx = mx - uc * m1, sdy = my - vc * m1;            // sum gs dx, sum gs dy
+        const float sdxx = mxx - 2.f * uc * mx + uc * uc * m1;         // sum gs dx^2
+        const float sdyy = myy - 2.f * vc * my + vc * vc * m1;
+        const float sdxy = mxy - uc * my - vc * mx + uc * vc * m1;
+        const float gAq = 0.5f * sdxx, gBq = sdxy, gCq = 0.5f * sdyy;
+        const float gu = -(A * sdx + Bq * sdy), gv = -(C * sdy + Bq * sdx);
+        float* dst = g2d + (int64_t)s_id[j] * kG2D;
+        red_add4(dst, gu, gv, gAq, gBq);
+        red_add4(dst + 4, gCq, so, sr, sg);
+        red_add4(dst + 8, sb, sz, 0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    // ---- flush feature gradients of the batch
+    if constexpr (DP > 0) {
+      if (g_feats) {
+        if (D == DP) {
+          for (int e = t; e < cnt * (DP / 4); e += kT) {
+            const int j = e / (DP / 4), q = e - j * (DP / 4);
+            const float4 v = *reinterpret_cast<const float4*>(s_outF + j * DP + 4 * q);
+            atomicAdd(reinterpret_cast<float4*>(g_feats + (int64_t)s_id[j] * D + 4 * q), v);
+          }
+        } else {
+          for (int e = t; e < cnt * DP; e += kT) {
+            const int j = e / DP, c = e - j * DP;
+            if (c < D) atomicAdd(g_feats + (int64_t)s_id[j] * D + c, s_outF[e]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int DP, bool BF16>
+void launch_t(const CamDev& cam, const GaussRec* rec, const void* feats, int D, const uint2* ranges,
+              const uint32_t* inst_id, const float* T_final, const uint32_t* n_contrib,
+              const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
+              float* g2d, float* g_feats, cudaStream_t st) {
+  const size_t smem = sizeof(float) * BwdCfg<DP>::smem_floats;
+  auto kern = k_raster_bwd<DP, BF16>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static uint64_t configured = 0;   // one bit per device
+  if (smem > 48 * 1024 && !(configured >> (dev & 63) & 1)) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured |= 1ull << (dev & 63);
+  }
+  kern<<<cam.TX * cam.TY, kT, smem, st>>>(cam, rec, feats, D, ranges, inst_id, T_final, n_contrib,
+                                          g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats);
+}
+
+}  // namespace
+
+void launch_raster_bwd(const CamDev& cam, const GaussRec* rec, const void* feats, int feat_dtype,
+                       int D, const uint2* ranges, const uint32_t* inst_id, const float* T_final,
+                       const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
+                       const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,
+                       cudaStream_t st) {
+  if (cam.TX * cam.TY == 0) return;
+  const bool bf = feat_dtype == GS_BF16;
+  const int DP = g_feat ? padded_feat(D) : 0;
+#define GS_BWD(dp)                                                                           \
+  (bf ? launch_t<dp, true>(cam, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,  \
+                           g_depth, g_alpha, g_feat, g2d, g_feats, st)                      \
+      : launch_t<dp, false>(cam, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb, \
+                            g_depth, g_alpha, g_feat, g2d, g_feats, st))
+  switch (DP) {
+    case 0: GS_BWD(0); break;
+    case 8: GS_BWD(8); break;
+    case 16: GS_BWD(16); break;
+    case 32: GS_BWD(32); break;
+    default: GS_BWD(64); break;
+  }
+#undef GS_BWD
+}
+
+}  // namespace gs

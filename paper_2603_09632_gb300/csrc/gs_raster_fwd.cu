@@ -1,0 +1,214 @@
+// a3: forward rendering, X-GS Eq. 1 (front-to-back alpha blending over depth-sorted
+// Gaussians), depth by substituting c_i -> d_i (App. B) and features by c_i -> f_i
+// (Sec. 3.1).  One 256-thread CTA per 16x16 tile, one thread per pixel.
+//
+// The tile's sorted list is consumed in batches of 256 Gaussians staged in shared
+// memory (records gathered by id; features converted to fp32 once per batch, so bf16
+// storage costs no per-pixel conversion).  A warp skips the colour/feature update of a
+// Gaussian when none of its 32 pixels blends it (ballot), a warp stops when all its
+// pixels have terminated, and the CTA stops when all 256 pixels have.
+#include "gs_blend.cuh"
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kB = 256;   // batch = threads = pixels per tile
+
+template <int DP, bool BF16>
+__device__ __forceinline__ void stage_features(const void* __restrict__ feats, int D,
+                                               const uint32_t* __restrict__ s_id, int cnt,
+                                               float* __restrict__ s_feat) {
+  if constexpr (DP > 0) {
+    if (D == DP) {
+      // 16-byte chunks: 8 bf16 or 4 f32 values
+      constexpr int VPC = BF16 ? 8 : 4;
+      constexpr int CPR = DP / VPC;
+      for (int c = threadIdx.x; c < cnt * CPR; c += kB) {
+        const int j = c / CPR, part = c - j * CPR;
+        const int64_t row = (int64_t)s_id[j] * DP;
+        float* dst = s_feat + j * DP + part * VPC;
+        if constexpr (BF16) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(
+              static_cast<const __nv_bfloat16*>(feats) + row) + part);
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            dst[2 * k] = __uint_as_float(w[k] << 16);
+            dst[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+          }
+        } else {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(
+              static_cast<const float*>(feats) + row) + part);
+          *reinterpret_cast<float4*>(dst) = v;
+        }
+      }
+    } else {
+      for (int e = threadIdx.x; e < cnt * DP; e += kB) {
+        const int j = e / DP, c = e - j * DP;
+        float v = 0.f;
+        if (c < D) {
+          const int64_t idx = (int64_t)s_id[j] * D + c;
+          if constexpr (BF16)
+            v = __bfloat162float(static_cast<const __nv_bfloat16*>(feats)[idx]);
+          else
+            v = __ldg(static_cast<const float*>(feats) + idx);
+        }
+        s_feat[e] = v;
+      }
+    }
+  }
+}
+
+template <int DP, bool BF16>
+__global__ void __launch_bounds__(kB)
+k_raster_fwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restrict__ feats, int D,
+             const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_id,
+             float* __restrict__ rgb, float* __restrict__ depth, float* __restrict__ alpha,
+             float* __restrict__ feat, float* __restrict__ T_final,
+             uint32_t* __restrict__ n_contrib) {
+  __shared__ float4 s_r0[kB], s_r1[kB], s_r2[kB];
+  __shared__ uint32_t s_id[kB];
+  extern __shared__ __align__(16) float s_feat[];   // [kB][DP]
+
+  const int tile = blockIdx.x;
+  const int px = (tile % cam.TX) * kTile + (threadIdx.x & 15);
+  const int py = (tile / cam.TX) * kTile + (threadIdx.x >> 4);
+  const bool inside = px < cam.W && py < cam.H;
+  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const uint2 rg = ranges[tile];
+  const int start = (int)rg.x, end = (int)rg.y;
+
+  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
+  float acc[DP > 0 ? DP : 1];
+#pragma unroll
+  for (int c = 0; c < (DP > 0 ? DP : 1); ++c) acc[c] = 0.f;
+  int last = 0;
+  bool done = !inside;
+
+  for (int b0 = start; b0 < end; b0 += kB) {
+    if (__syncthreads_count(done) == kB) break;
+    const int cnt = min(kB, end - b0);
+    if ((int)threadIdx.x < cnt) {
+      const uint32_t id = inst_id[b0 + threadIdx.x];
+      const GaussRec g = rec[id];
+      s_r0[threadIdx.x] = g.r0;
+      s_r1[threadIdx.x] = g.r1;
+      s_r2[threadIdx.x] = g.r2;
+      s_id[threadIdx.x] = id;
+    }
+    __syncthreads();
+    stage_features<DP, BF16>(feats, D, s_id, cnt, s_feat);
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      if (__all_sync(0xffffffffu, done)) break;
+      const float4 r0 = s_r0[j];
+      const float4 r1 = s_r1[j];
+      float w = 0.f;
+      if (!done) {
+        const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+        if (sigma >= 0.f) {
+          const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
+          if (a >= kAlphaMin) {
+            const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+            if (Tn < kTMin) {
+              done = true;
+            } else {
+              w = __fmul_rn(a, T);
+              T = Tn;
+              last = b0 + j - start + 1;
+            }
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, w != 0.f)) {
+        const float4 r2 = s_r2[j];
+        c0 = fmaf(w, r2.x, c0);
+        c1 = fmaf(w, r2.y, c1);
+        c2 = fmaf(w, r2.z, c2);
+        dep = fmaf(w, r1.z, dep);
+        if constexpr (DP > 0) {
+          const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * DP);
+#pragma unroll
+          for (int q = 0; q < DP / 4; ++q) {
+            const float4 f = f4[q];
+            acc[4 * q] = fmaf(w, f.x, acc[4 * q]);
+            acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
+            acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
+            acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
+          }
+        }
+      }
+    }
+  }
+  if (!inside) return;
+  const int64_t HW = (int64_t)cam.W * cam.H;
+  const int64_t p = (int64_t)py * cam.W + px;
+  if (rgb) {
+    rgb[p] = c0;
+    rgb[HW + p] = c1;
+    rgb[2 * HW + p] = c2;
+  }
+  if (depth) depth[p] = dep;
+  if (alpha) alpha[p] = 1.f - T;
+  if constexpr (DP > 0) {
+    if (feat) {
+#pragma unroll
+      for (int c = 0; c < DP; ++c)
+        if (c < D) feat[c * HW + p] = acc[c];
+    }
+  }
+  T_final[p] = T;
+  n_contrib[p] = (uint32_t)last;
+}
+
+template <int DP, bool BF16>
+void launch_t(const CamDev& cam, const GaussRec* rec, const void* feats, int D, const uint2* ranges,
+              const uint32_t* inst_id, float* rgb, float* depth, float* alpha, float* feat,
+              float* T_final, uint32_t* n_contrib, cudaStream_t st) {
+  const size_t smem = sizeof(float) * kB * DP;
+  auto kern = k_raster_fwd<DP, BF16>;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static uint64_t configured = 0;   // one bit per device
+  if (smem > 48 * 1024 && !(configured >> (dev & 63) & 1)) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured |= 1ull << (dev & 63);
+  }
+  kern<<<cam.TX * cam.TY, kB, smem, st>>>(cam, rec, feats, D, ranges, inst_id, rgb, depth, alpha,
+                                          feat, T_final, n_contrib);
+}
+
+}  // namespace
+
+int padded_feat(int D) {
+  if (D <= 0) return 0;
+  if (D <= 8) return 8;
+  if (D <= 16) return 16;
+  if (D <= 32) return 32;
+  return 64;
+}
+
+void launch_raster_fwd(const CamDev& cam, const GaussRec* rec, const void* feats, int feat_dtype,
+                       int D, const uint2* ranges, const uint32_t* inst_id, float* rgb,
+                       float* depth, float* alpha, float* feat, float* T_final,
+                       uint32_t* n_contrib, cudaStream_t st) {
+  if (cam.TX * cam.TY == 0) return;
+  const bool bf = feat_dtype == GS_BF16;
+  const int DP = feat ? padded_feat(D) : 0;   // no feature output: skip feature blending
+#define GS_FWD(dp)                                                                             \
+  (bf ? launch_t<dp, true>(cam, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat, T_final, \
+                           n_contrib, st)                                                       \
+      : launch_t<dp, false>(cam, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,       \
+                            T_final, n_contrib, st))
+  switch (DP) {
+    case 0: GS_FWD(0); break;
+    case 8: GS_FWD(8); break;
+    case 16: GS_FWD(16); break;
+    case 32: GS_FWD(32); break;
+    default: GS_FWD(64); break;
+  }
+#undef GS_FWD
+}
+
+}  // namespace gs

@@ -1,0 +1,241 @@
+"""GPU (C ABI) vs CPU oracle parity.
+
+Tolerances: tile keys, sorted ids and ranges bit-exact; FP32 rgb/depth/alpha/features
+max-abs 1e-4 on pixels the oracle does not flag as within rounding distance of a blend
+threshold; BF16-stored features relative 1e-2 against the FP32-feature render; gradients
+relative (Frobenius) 1e-3 per tensor against the FP32 oracle's analytic backward.
+"""
+import numpy as np
+import pytest
+
+from synth import scenes as S
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+TOL_FWD = 1e-4
+TOL_BWD = 1e-3
+GRAD_KEYS = ("means", "scales", "quats", "opacities", "sh", "feats", "pose")
+
+
+def small_room(n=30_000, W=200, H=136, D=16, deg=3, pose=3):
+    sc = S.room_scene(n, n_feat=D, sh_degree=deg, seed=7)
+    cams = S.room_trajectory(8, W, H, 0.9 * W)
+    return sc, cams[pose]
+
+
+CASES = {
+    "tiny": lambda: (S.config_tiny()[0], S.config_tiny()[1][0]),
+    "room_ragged": small_room,
+    "room_sh1_d8": lambda: small_room(n=20_000, W=97, H=61, D=8, deg=1, pose=5),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request, oracle):
+    sc, cam = CASES[request.param]()
+    g = S.upstream_grads(cam.H, cam.W, sc.n_feat)
+    gpu = U.run(sc, cam, g)
+    return request.param, sc, cam, g, gpu
+
+
+def test_projection_bit_exact(oracle, case):
+    from paper_2603_09632_gb300 import _lib as L
+    name, sc, cam, g, gpu = case
+    ref = oracle.project(sc, cam, "f32")
+    got = L.gs_get_projection(gpu["rast"].ws, sc.n)
+    v = ref["valid"]
+    np.testing.assert_array_equal(got["rect"][v], ref["rect"][v])
+    assert np.all(got["rect"][~v] == 0)
+    for k in ("depth", "mean2d", "conic"):
+        np.testing.assert_array_equal(got[k][v].view(np.uint32), ref[k][v].view(np.uint32), err_msg=k)
+    np.testing.assert_allclose(got["rgb"][v], ref["rgb"][v], atol=1e-6)
+
+
+def test_tile_lists_bit_exact(oracle, case):
+    from paper_2603_09632_gb300 import _lib as L
+    name, sc, cam, g, gpu = case
+    TX, TY = oracle.tiles(cam)
+    keys, ids, ranges = oracle.tile_lists(sc, cam)
+    tiles_g, ids_g, ranges_g = L.gs_get_instances(gpu["rast"].ws, TX * TY)
+    assert gpu["instances"] == len(keys)
+    depth_g = L.gs_get_projection(gpu["rast"].ws, sc.n)["depth"].view(np.uint32)
+    keys_g = (tiles_g.astype(np.uint64) << np.uint64(32)) | depth_g[ids_g].astype(np.uint64)
+    np.testing.assert_array_equal(keys_g, keys)
+    np.testing.assert_array_equal(ids_g, ids)
+    np.testing.assert_array_equal(ranges_g, ranges)
+
+
+def test_forward_parity(oracle, case):
+    from paper_2603_09632_gb300 import _lib as L
+    name, sc, cam, g, gpu = case
+    ref = oracle.render(sc, cam, "f32")
+    flags = ref["flags"]
+    assert (flags != 0).mean() < 0.01, "too many near-threshold pixels to be meaningful"
+    for k in ("rgb", "depth", "alpha", "feat"):
+        err = U.max_abs_unflagged(gpu[k], ref[k], flags)
+        assert err <= TOL_FWD, (k, err)
+    T, nc = L.gs_get_pixel_state(gpu["rast"].ws, cam.H, cam.W)
+    ok = flags == 0
+    np.testing.assert_array_equal(nc[ok], ref["n_contrib"][ok])
+    assert np.abs(T - ref["T_final"])[ok].max() <= TOL_FWD
+
+
+def test_backward_parity(oracle, case):
+    name, sc, cam, g, gpu = case
+    ref = oracle.backward(sc, cam, g, "f32")
+    for k in GRAD_KEYS:
+        r = U.rel_err(gpu["grads"][k], ref[k])
+        assert r <= TOL_BWD, (k, r)
+
+
+def test_bf16_features(oracle):
+    sc, cam = small_room(n=30_000, D=64, deg=3)
+    gpu = U.run(sc, cam, bf16=True)
+    flags = oracle.render(sc, cam, "f32")["flags"]
+    # same bf16 values in FP32 arithmetic: FP32 tolerance
+    ref_b = oracle.render(sc, cam, "f32", feats=U.bf16_round(sc.feats))
+    assert U.max_abs_unflagged(gpu["feat"], ref_b["feat"], flags) <= TOL_FWD
+    # against the FP32-feature render: relative 1e-2 per channel map
+    ref = oracle.render(sc, cam, "f32")
+    ok = flags == 0
+    for c in range(sc.n_feat):
+        a, b = gpu["feat"][c][ok], ref["feat"][c][ok]
+        assert U.rel_err(a, b) <= 1e-2, c
+    assert np.abs(gpu["feat"] - ref["feat"])[:, ok].max() / np.abs(ref["feat"]).max() <= 1e-2
+
+
+def test_bf16_backward(oracle):
+    sc, cam = small_room(n=20_000, D=64, deg=0)
+    g = S.upstream_grads(cam.H, cam.W, sc.n_feat)
+    gpu = U.run(sc, cam, g, bf16=True)
+    scb = S.Scene(**{k: getattr(sc, k) for k in ("means", "scales", "quats", "opacities", "sh")},
+                  feats=U.bf16_round(sc.feats), sh_degree=sc.sh_degree)
+    ref = oracle.backward(scb, cam, g, "f32")
+    for k in GRAD_KEYS:
+        assert U.rel_err(gpu["grads"][k], ref[k]) <= TOL_BWD, k
+
+
+def test_determinism():
+    sc, cam = small_room()
+    a = U.run(sc, cam)
+    b = U.run(sc, cam, rast=a["rast"])
+    for k in ("rgb", "depth", "alpha", "feat"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_full_size_slam_frame_sampled(oracle):
+    """640x480, 200k room Gaussians, 16 f32 features, the bench's launch configuration:
+    forward on 3000 sampled pixels, backward of a loss restricted to those pixels."""
+    sc, cams = S.config_slam(n_poses=100)
+    cam = cams[0]
+    rng = np.random.default_rng(12)
+    pix = rng.choice(cam.W * cam.H, size=3000, replace=False)
+    g = S.upstream_grads(cam.H, cam.W, sc.n_feat)
+    mask = np.zeros(cam.W * cam.H, bool)
+    mask[pix] = True
+    gm = {k: (v.reshape(v.shape[:-2] + (-1,)) * mask).reshape(v.shape) for k, v in g.items()}
+    gpu = U.run(sc, cam, gm)
+    ref = oracle.render(sc, cam, "f32", pixels=pix)
+    flags = ref["flags"]
+    H, W = cam.H, cam.W
+    for k in ("rgb", "depth", "alpha", "feat"):
+        v = gpu[k].reshape(gpu[k].shape[:-2] + (H * W,))[..., pix]
+        assert U.max_abs_unflagged(v, ref[k], flags) <= TOL_FWD, k
+    gs = {k: v.reshape(v.shape[:-2] + (-1,))[..., pix] for k, v in g.items()}
+    rb = oracle.backward(sc, cam, gs, "f32", pixels=pix)
+    for k in GRAD_KEYS:
+        assert U.rel_err(gpu["grads"][k], rb[k]) <= TOL_BWD, k
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_scene():
+    sc = S.cube_scene(0, n_feat=4)
+    cam = S.pinhole(40, 30, 40.0, 40.0, np.eye(3), np.array([0, 0, 2.0]))
+    g = S.upstream_grads(cam.H, cam.W, 4)
+    r = U.run(sc, cam, g)
+    assert r["instances"] == 0
+    assert np.all(r["rgb"] == 0) and np.all(r["alpha"] == 0) and np.all(r["feat"] == 0)
+    np.testing.assert_array_equal(r["grads"]["pose"], np.zeros(6))
+
+
+def test_all_culled():
+    sc = S.cube_scene(500, n_feat=4)
+    cam = S.pinhole(64, 48, 50.0, 50.0, np.eye(3), np.array([0, 0, -3.0]))   # scene behind
+    g = S.upstream_grads(cam.H, cam.W, 4)
+    r = U.run(sc, cam, g)
+    assert r["instances"] == 0 and np.all(r["alpha"] == 0)
+    for k in GRAD_KEYS:
+        assert np.all(r["grads"][k] == 0), k
+
+
+def test_one_huge_gaussian_and_odd_channels(oracle):
+    # one Gaussian covering every tile, D = 3 (padded inside the kernels), SH 2
+    sc = S.cube_scene(3, n_feat=3, sh_degree=2, seed=2, log_scale_mu=0.0, log_scale_sd=0.01)
+    sc.means[:] = [[0.0, 0.0, 0.0], [0.1, 0.0, 0.3], [-0.2, 0.1, -0.2]]
+    cam = S.pinhole(150, 90, 80.0, 80.0, np.eye(3), np.array([0, 0, 2.5]))
+    g = S.upstream_grads(cam.H, cam.W, 3)
+    r = U.run(sc, cam, g)
+    ref = oracle.render(sc, cam, "f32")
+    for k in ("rgb", "depth", "alpha", "feat"):
+        assert U.max_abs_unflagged(r[k], ref[k], ref["flags"]) <= TOL_FWD, k
+    rb = oracle.backward(sc, cam, g, "f32")
+    for k in GRAD_KEYS:
+        assert U.rel_err(r["grads"][k], rb[k]) <= TOL_BWD, k
+
+
+def test_no_features():
+    sc = S.cube_scene(800, n_feat=0, seed=3)
+    cam = S.config_tiny()[1][0]
+    g = S.upstream_grads(cam.H, cam.W, 0)
+    r = U.run(sc, cam, {k: v for k, v in g.items() if k != "feat"})
+    assert r["feat"] is None and r["grads"]["feats"] is None
+    assert r["alpha"].max() > 0.5
+
+
+def test_no_sync_binning_and_overflow():
+    from paper_2603_09632_gb300 import _lib as L
+    from paper_2603_09632_gb300.render import Rasterizer
+    sc, (cam,) = S.config_tiny()
+    ref = U.run(sc, cam)
+    rast = Rasterizer(U.device())
+    rast.reserve(sc.n, ref["instances"], cam.W * cam.H)
+    out = U.run(sc, cam, rast=rast, sync=False)
+    for k in ("rgb", "alpha", "feat"):
+        np.testing.assert_array_equal(out[k], ref[k])
+    assert L.gs_workspace_status(rast.ws) == L.GS_OK
+    # a workspace reserved too small: the excess is dropped and reported, nothing faults
+    small = Rasterizer(U.device())
+    small.reserve(sc.n, ref["instances"] // 2, cam.W * cam.H)
+    U.run(sc, cam, rast=small, sync=False)
+    assert L.gs_workspace_status(small.ws) == L.GS_ERR_DEVICE
+    assert L.gs_workspace_status(small.ws) == L.GS_OK      # cleared by the read
+
+
+def test_l1_grad_matches_sign():
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    a = torch.randn(1000, device=U.device())
+    b = torch.randn(1000, device=U.device())
+    b[:10] = a[:10]
+    out = torch.empty_like(a)
+    L.gs_l1_grad(a, b, 0.5, out)
+    ref = 0.5 * np.sign(a.cpu().numpy() - b.cpu().numpy())
+    np.testing.assert_array_equal(out.cpu().numpy(), ref.astype(np.float32))
+
+
+def test_argument_errors():
+    from paper_2603_09632_gb300 import _lib as L
+    from paper_2603_09632_gb300.render import Rasterizer
+    sc, (cam,) = S.config_tiny()
+    scene = U.upload(sc)
+    rast = Rasterizer(U.device())
+    c = L.make_camera(cam.W, cam.H, cam.fx, cam.fy, cam.cx, cam.cy, cam.R, cam.t)
+    with pytest.raises(L.GSError) as e:
+        L.gs_render_fwd(scene, c, rast.ws)            # before project/bin
+    assert e.value.status == L.GS_ERR_STATE
+    bad = L.make_camera(cam.W, cam.H, -1.0, cam.fy, cam.cx, cam.cy, cam.R, cam.t)
+    with pytest.raises(L.GSError) as e:
+        L.gs_project(scene, bad, rast.ws)
+    assert e.value.status == L.GS_ERR_ARG
