@@ -1,0 +1,422 @@
+"""Benchmark: Mpix/s of forward + backward (RGB + depth + alpha + features) on one GB300.
+
+One step = one camera pose of the workload through the whole path: gs_project ->
+gs_bin_tiles -> gs_render_fwd -> gs_render_bwd (gradients to every Gaussian parameter and
+the 6-DoF pose), inputs resident in HBM.  The default workload is the SLAM frame: 200k
+room Gaussians, SH 0, 16 fp32 feature channels, 640x480, fx = fy = 600, cycling over a
+100-pose trajectory.  L2 is flushed (a 256 MiB write) between timed steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead (the
+reference arm: there is no runnable reference implementation of this path).
+Multi-GPU (torchrun, N > 1): poses are independent, so each rank renders its own poses
+with no data-path collective (weak scaling); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import scenes as S  # noqa: E402
+
+WORKLOADS = {
+    "slam_640x480_200k": dict(make=lambda: S.config_slam(n_poses=100), bf16=False, l1=False,
+                              desc="room 200k Gaussians, SH0, 16 fp32 feats, 640x480, fx=600"),
+    "semantic_1200x680_1m": dict(make=lambda: S.config_semantic(n_poses=100), bf16=True, l1=True,
+                                 desc="room 1M Gaussians, SH3, 64 bf16 feats, 1200x680, fx=600, L1 loss"),
+    "tiny_128x96_2k": dict(make=S.config_tiny, bf16=False, l1=False,
+                           desc="cube 2k Gaussians, SH0, 8 fp32 feats, 128x96, fx=100"),
+    "memory_3840x2160_3m": dict(make=lambda: S.config_memory(n_poses=10), bf16=False, l1=False,
+                                desc="room 3M Gaussians, SH0, 32 fp32 feats, 3840x2160, fx=3600"),
+}
+DEFAULT_WORKLOAD = "slam_640x480_200k"
+METRIC = "Mpix/s fwd+bwd (RGB+D+feat) at 1 GB300"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- algorithmic model
+
+def stage_bytes(st, D, bf, K):
+    """Algorithmic bytes per launch of each stage (the byte model of the design notes)."""
+    N, V, I, Ie, P = st["n"], st["visible"], st["instances"], st["inst_eff"], st["pixels"]
+    pix_io = P * (20 + 4 * D + 8)
+    return {
+        "project": N * 44 + V * (12 * K + 48),
+        "bin": I * 36,
+        "fwd": Ie * (44 + D * bf) + pix_io,
+        "bwd_raster": pix_io + Ie * (44 + D * bf) + V * (40 + 4 * D),
+        "bwd_project": V * (40 + 44 + 12 * K) + V * (44 + 12 * K) + 24,
+    }
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    from paper_2603_09632_gb300.render import as_camera
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl = WORKLOADS[args.workload]
+    scene_np, cams = wl["make"]()
+    D, K = scene_np.n_feat, (scene_np.sh_degree + 1) ** 2
+    bf = 2 if wl["bf16"] else 4
+    H, W = cams[0].H, cams[0].W
+    P = H * W
+
+    def dev_t(a, dtype=torch.float32):
+        return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev).to(dtype)
+
+    fdt = torch.bfloat16 if wl["bf16"] else torch.float32
+    scene = L.Scene(dev_t(scene_np.means), dev_t(scene_np.scales), dev_t(scene_np.quats),
+                    dev_t(scene_np.opacities), dev_t(scene_np.sh), dev_t(scene_np.feats, fdt))
+    g = S.upstream_grads(H, W, D)
+    gr, gd, ga, gf = (dev_t(g[k]) for k in ("rgb", "depth", "alpha", "feat"))
+    target = dev_t(S.feature_target(H, W, D)) if wl["l1"] else None
+    out = dict(rgb=torch.empty((3, H, W), device=dev), depth=torch.empty((H, W), device=dev),
+               alpha=torch.empty((H, W), device=dev), feat=torch.empty((D, H, W), device=dev))
+    grads = dict(means=torch.empty((scene.n, 3), device=dev), scales=torch.empty((scene.n, 3), device=dev),
+                 quats=torch.empty((scene.n, 4), device=dev), opac=torch.empty(scene.n, device=dev),
+                 sh=torch.empty((scene.n, K, 3), device=dev), feats=torch.empty((scene.n, D), device=dev),
+                 pose=torch.empty(6, device=dev))
+    gcams = [as_camera(c) for c in cams]
+    ws = L.Workspace(local)
+    stream = torch.cuda.current_stream()
+
+    # size the workspace once (max instance count over the trajectory, +25 %), so that the
+    # timed steps never synchronise or allocate
+    max_inst = 0
+    for c in gcams:
+        L.gs_project(scene, c, ws)
+        max_inst = max(max_inst, L.gs_bin_tiles(ws, sync=True))
+    L.gs_workspace_reserve(ws, scene.n, int(max_inst * 1.25) + 1024, P)
+
+    def step(c, gfeat):
+        L.gs_project(scene, c, ws, stream)
+        L.gs_bin_tiles(ws, sync=False, stream=stream)
+        L.gs_render_fwd(scene, c, ws, out["rgb"], out["depth"], out["alpha"], out["feat"], stream)
+        if target is not None:
+            L.gs_l1_grad(out["feat"], target, 1.0 / out["feat"].numel(), gf, stream)
+        L.gs_render_bwd(scene, c, ws, gr, gd, ga, gfeat, grads["means"], grads["scales"],
+                        grads["quats"], grads["opac"], grads["sh"], grads["feats"], grads["pose"],
+                        stream)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    poses = [(rank * 37 + k) % len(gcams) for k in range(args.warmup + args.steps)]
+    for k in range(args.warmup):
+        step(gcams[poses[k]], gf)
+        flush.fill_(float(k))
+    torch.cuda.synchronize()
+    if L.gs_workspace_status(ws) != L.GS_OK:
+        raise RuntimeError("instance capacity overflow during warm-up")
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    L.gs_timing_enable(ws, True)
+    L.gs_timing_collect(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = L.gs_launch_count()
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step(gcams[poses[args.warmup + k]], gf)
+        evs[k][1].record(stream)
+        flush.fill_(float(k))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = L.gs_launch_count() - n0
+    clk = clocks.stop()
+    stage = L.gs_timing_collect(ws)
+    L.gs_timing_enable(ws, False)
+    status = L.gs_workspace_status(ws)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * args.steps * P / (ms * 1e-3) / 1e6
+
+    # algorithmic bytes per stage, averaged over the timed poses (untimed recount)
+    sb_tot = {}
+    for k in range(args.steps):
+        c = gcams[poses[args.warmup + k]]
+        L.gs_project(scene, c, ws)
+        L.gs_bin_tiles(ws, sync=True)
+        L.gs_render_fwd(scene, c, ws, out["rgb"], out["depth"], out["alpha"], out["feat"])
+        st = L.gs_get_stats(ws)
+        for name, b in stage_bytes(st, D, bf, K).items():
+            sb_tot[name] = sb_tot.get(name, 0.0) + b
+    stage_ms = {name: stage[name][0] / max(stage[name][1], 1) for name in stage}
+    dom = max(stage_ms, key=stage_ms.get)
+    peaks, src = load_peaks()
+    alg = sb_tot[dom] / args.steps
+    achieved = alg / (stage_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": None, "peak_source": src,
+                "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+                "stage_alg_mb": {k: round(v / args.steps / 1e6, 3) for k, v in sb_tot.items()}}
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(args, L, scene_np, gcams, poses, wl, dev, stream, ws, K, D, fdt, H, W)
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "gaussians": scene.n,
+                   "pixels_per_step": P, "poses": len(gcams), "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
+        "device_status": L.status_string(status),
+    }
+    if rank == 0 and not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, scene_np, cams, target_budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, L, scene_np, gcams, poses, wl, dev, stream, ws, K, D, fdt, H, W):
+    """Same metric through the C ABI with HOST inputs/outputs: every step copies the scene
+    parameters and upstream gradients from pinned host memory, runs the path and copies
+    the rendered images and all gradients back to pinned host memory."""
+    import torch
+    n = scene_np.n
+    pin = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dt).pin_memory()
+    h_in = [pin(scene_np.means), pin(scene_np.scales), pin(scene_np.quats), pin(scene_np.opacities),
+            pin(scene_np.sh), pin(scene_np.feats, fdt)]
+    g = S.upstream_grads(H, W, D)
+    h_g = [pin(g[k]) for k in ("rgb", "depth", "alpha", "feat")]
+    d_in = [torch.empty_like(t, device=dev) for t in h_in]
+    d_g = [torch.empty_like(t, device=dev) for t in h_g]
+    scene = L.Scene(*d_in)
+    outs = [torch.empty((3, H, W), device=dev), torch.empty((H, W), device=dev),
+            torch.empty((H, W), device=dev), torch.empty((D, H, W), device=dev)]
+    grads = [torch.empty((n, 3), device=dev), torch.empty((n, 3), device=dev),
+             torch.empty((n, 4), device=dev), torch.empty(n, device=dev),
+             torch.empty((n, K, 3), device=dev), torch.empty((n, D), device=dev),
+             torch.empty(6, device=dev)]
+    h_out = [torch.empty_like(t, device="cpu").pin_memory() for t in outs + grads]
+    bi = sum(t.numel() * t.element_size() for t in h_in + h_g)
+    bo = sum(t.numel() * t.element_size() for t in h_out)
+
+    def step(c):
+        for d, h in zip(d_in + d_g, h_in + h_g):
+            d.copy_(h, non_blocking=True)
+        L.gs_project(scene, c, ws, stream)
+        L.gs_bin_tiles(ws, sync=False, stream=stream)
+        L.gs_render_fwd(scene, c, ws, *outs, stream)
+        L.gs_render_bwd(scene, c, ws, *d_g, *grads, stream)
+        for h, d in zip(h_out, outs + grads):
+            h.copy_(d, non_blocking=True)
+
+    for k in range(min(3, args.warmup)):
+        step(gcams[poses[k]])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(args.steps):
+        step(gcams[poses[args.warmup + k]])
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return {"value": round(args.steps * H * W / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
+            "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+            "ms_per_step": round(ms / args.steps, 4)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_step(O, scene_np, cam, pixels):
+    """One bounded sample of the workload through the CPU oracle (FP32): forward and
+    backward of a loss restricted to ``pixels`` (flat indices)."""
+    g = S.upstream_grads(cam.H, cam.W, scene_np.n_feat)
+    gs = {k: v.reshape(v.shape[:-2] + (-1,))[..., pixels] for k, v in g.items()}
+    O.render(scene_np, cam, "f32", pixels=pixels)
+    O.backward(scene_np, cam, gs, "f32", pixels=pixels)
+
+
+def sample_pixels(cam, n_tiles, rng):
+    TX, TY = (cam.W + 15) // 16, (cam.H + 15) // 16
+    tiles = rng.choice(TX * TY, size=min(n_tiles, TX * TY), replace=False)
+    pix = []
+    for t in tiles:
+        x0, y0 = (t % TX) * 16, (t // TX) * 16
+        ys, xs = np.mgrid[y0:min(y0 + 16, cam.H), x0:min(x0 + 16, cam.W)]
+        pix.append((ys * cam.W + xs).ravel())
+    return np.concatenate(pix)
+
+
+def cpu_baseline(args, scene_np, cams, target_budget_s=15.0):
+    from oracle import oracle as O
+    O.build()
+    cores = O.set_threads(os.cpu_count() or 1)
+    rng = np.random.default_rng(5)
+    n_tiles = args.cpu_tiles
+    t_tot, px_tot, k = 0.0, 0, 0
+    while t_tot < target_budget_s and k < len(cams):
+        cam = cams[k]
+        pix = sample_pixels(cam, n_tiles, rng)
+        t0 = time.perf_counter()
+        oracle_step(O, scene_np, cam, pix)
+        t_tot += time.perf_counter() - t0
+        px_tot += pix.size
+        k += 1
+    return {"value": round(px_tot / t_tot / 1e6, 5), "unit": "Mpix/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{k} poses x {n_tiles} random 16x16 tiles, FP32 oracle forward + backward "
+                      f"(projection and tile lists of the full scene each pose), {t_tot:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    cores = O.set_threads(os.cpu_count() or 1)
+    wl = WORKLOADS[args.workload]
+    scene_np, cams = wl["make"]()
+    rng = np.random.default_rng(5)
+    times, px = [], 0
+    for k in range(args.warmup + args.steps):
+        cam = cams[k % len(cams)]
+        pix = sample_pixels(cam, args.cpu_tiles, rng)
+        t0 = time.perf_counter()
+        oracle_step(O, scene_np, cam, pix)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            px += pix.size
+    tot = sum(times)
+    value = px / tot / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Mpix/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * tot / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "gaussians": scene_np.n,
+                       "pixels_per_step": int(px / args.steps), "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "Mpix/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{args.cpu_tiles} random 16x16 tiles per step, FP32 oracle "
+                                       "forward + backward on the host cores"},
+            "e2e": {"value": round(value, 5), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-tiles", type=int, default=300)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -196,6 +196,10 @@ gs_status gs_timing_enable(gs_workspace* ws, int enable);
  * NULL) the number of timed launches of each stage. */
 gs_status gs_timing_collect(gs_workspace* ws, double* ms_out, int64_t* count_out);
 
+/* Number of CUDA kernels this library has launched in the process so far (all
+ * workspaces, all devices).  Host-side counter; no synchronisation. */
+int64_t gs_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,7 @@ def _load():
         "gs_get_pixel_state": ([P, P, P, P], st),
         "gs_timing_enable": ([P, i32], st),
         "gs_timing_collect": ([P, P, P], st),
+        "gs_launch_count": ([], i64),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -269,6 +270,10 @@ def gs_get_pixel_state(ws, H, W, stream=None):
     _check(lib.gs_get_pixel_state(ws.h, P(T.ctypes.data), P(nc.ctypes.data), _stream(stream)),
            "gs_get_pixel_state")
     return T, nc
+
+
+def gs_launch_count() -> int:
+    return int(lib.gs_launch_count())
 
 
 def gs_timing_enable(ws, enable=True):

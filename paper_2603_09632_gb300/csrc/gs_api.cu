@@ -1,5 +1,6 @@
 // C ABI of libgs: workspace management and the entry points declared in include/gs.h.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -7,11 +8,12 @@
 
 #include "gs_internal.cuh"
 
-namespace gs {
-int padded_feat(int D);
-}
-
 using namespace gs;
+
+namespace gs {
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace gs
 
 namespace {
 
@@ -490,6 +492,8 @@ gs_status gs_get_pixel_state(gs_workspace* ws, float* T_final, uint32_t* n_contr
   GS_TRY(cudaStreamSynchronize(st));
   return GS_OK;
 }
+
+int64_t gs_launch_count(void) { return gs::g_launches.load(std::memory_order_relaxed); }
 
 gs_status gs_timing_enable(gs_workspace* ws, int enable) {
   if (!ws) return GS_ERR_ARG;

@@ -21,4 +21,45 @@ __device__ __forceinline__ float blend_sigma(float dx, float dy, float A, float 
 // G = exp(-sigma) and o*G; the caller applies the cap and thresholds.
 __device__ __forceinline__ float blend_gauss(float sigma) { return __expf(-sigma); }
 
+// sigma at offset dx (fixed) minimised over dy in [lo, hi] (convex quadratic in dy).
+__device__ __forceinline__ float edge_min_sigma(float dx, float lo, float hi, float a, float b,
+                                                float c) {
+  const float dy = fminf(fmaxf(-b * dx / c, lo), hi);
+  return 0.5f * (a * dx * dx + c * dy * dy) + b * dx * dy;
+}
+
+// Conservative per-tile test: true when no pixel centre of the 16x16 tile with origin
+// (x0, y0) can reach alpha >= 1/255 for this Gaussian, so the tile can skip it without
+// changing any output.  sigma is convex, so its minimum over the box of pixel centres is
+// 0 when the mean lies inside the box and otherwise lies on one of the four edges.  The
+// test keeps a margin of 1e-3 in sigma (0.1 % in alpha), far above rounding.
+__device__ __forceinline__ bool tile_culled(float x0, float y0, float u, float v, float A, float B,
+                                            float C, float o) {
+  const float lx = x0 + 0.5f - u, hx = x0 + 15.5f - u;
+  const float ly = y0 + 0.5f - v, hy = y0 + 15.5f - v;
+  if (lx <= 0.f && hx >= 0.f && ly <= 0.f && hy >= 0.f) return false;
+  const float s = fminf(fminf(edge_min_sigma(lx, ly, hy, A, B, C), edge_min_sigma(hx, ly, hy, A, B, C)),
+                        fminf(edge_min_sigma(ly, lx, hx, C, B, A), edge_min_sigma(hy, lx, hx, C, B, A)));
+  return s > __logf(255.f * o) + 1e-3f;
+}
+
+// Ordered compaction of one flag per thread over a 256-thread block.  Returns the
+// position of a kept item (-1 otherwise) and the number kept.  Contains one barrier;
+// s_wc (8 ints) must not be reused before the next barrier.
+__device__ __forceinline__ int block_compact_index(bool keep, int* s_wc, int* total) {
+  const unsigned b = __ballot_sync(0xffffffffu, keep);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s_wc[w] = __popc(b);
+  __syncthreads();
+  int off = 0, tot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int c = s_wc[k];
+    off += k < w ? c : 0;
+    tot += c;
+  }
+  *total = tot;
+  return keep ? off + __popc(b & ((1u << lane) - 1u)) : -1;
+}
+
 }  // namespace gs

@@ -108,6 +108,9 @@ void launch_l1_grad(const float* pred, const float* target, int64_t n, float sca
 
 int padded_feat(int D);
 
+// Count kernels launched by the library (process-wide; read with gs_launch_count()).
+void note_launch(int k = 1);
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ inline int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ inline int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }

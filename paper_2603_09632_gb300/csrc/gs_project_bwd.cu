@@ -340,10 +340,14 @@ void launch_project_bwd(const gs_scene& sc, const CamDev& cam, const GaussRec* r
       default: GS_PB(3); break;
     }
 #undef GS_PB
+    note_launch();
   }
   if (g_pose6) {
     if (sc.n > 0)
+    {
       k_pose_reduce<<<1, 256, 0, st>>>(pose_partials, nb, g_pose6);
+      note_launch();
+    }
     else
       cudaMemsetAsync(g_pose6, 0, 6 * sizeof(float), st);
   }
@@ -353,6 +357,7 @@ void launch_l1_grad(const float* pred, const float* target, int64_t n, float sca
                     cudaStream_t st) {
   if (n <= 0) return;
   k_l1_grad<<<(int)ceil_div(n, 256), 256, 0, st>>>(pred, target, n, scale, grad);
+  note_launch();
 }
 
 }  // namespace gs

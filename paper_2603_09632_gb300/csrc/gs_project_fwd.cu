@@ -232,6 +232,7 @@ void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32
     case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect); break;
     default: k_project<3><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect); break;
   }
+  note_launch();
 }
 
 }  // namespace gs

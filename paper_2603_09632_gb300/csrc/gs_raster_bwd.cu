@@ -9,54 +9,112 @@
 // 2D-mean gradients follow.
 //
 // One 256-thread CTA per tile walks the tile's list backwards from the longest pixel
-// prefix (max n_contrib), recovering T_i = T_{i+1} / (1 - a_i) from T_final, in batches
-// of B Gaussians.  Phase 1 (one thread per pixel) writes w, dL/dsigma and dL/do of each
+// prefix (max n_contrib), recovering T_i = T_{i+1} / (1 - a_i) from T_final.  The list is
+// taken in chunks of 256 entries; each chunk is gathered once, entries that no pixel of
+// the tile can blend are dropped (conservative test, outputs unchanged) and the rest are
+// compacted into shared memory.  The compacted chunk is processed in batches of B
+// Gaussians.  Phase 1 (one thread per pixel) writes w, dL/dsigma and dL/do of each
 // (pixel, Gaussian) pair to shared memory.  Phase 2 reduces over the 256 pixels of the
-// tile: the feature gradient is the contraction W^T g_F done with 4x4 register blocks,
+// tile: the feature gradient is the contraction W^T g_F with 4x4 register blocks, and
 // colour/depth/opacity sums and the pixel moments sum_p dL/dsigma * (1, x, y, xx, xy, yy)
 // (from which the conic and mean gradients are formed exactly) are warp reductions.
-// Each Gaussian then receives one 16-byte vector atomic per 4 quantities per tile.
+// The next batch's features are fetched into registers during phase 2.  Two barriers
+// per batch.  Each Gaussian receives one 16-byte vector atomic per 4 quantities per tile.
 #include "gs_blend.cuh"
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kT = 256;        // threads = pixels per tile
+constexpr int kT = 256;        // threads = pixels per tile = entries per chunk
 constexpr int kWS = kT + 4;    // row stride of the j-major pair arrays (floats)
 
 template <int DP>
 struct BwdCfg {
   static constexpr int B = DP >= 64 ? 8 : 16;          // Gaussians per batch
   static constexpr int ES = DP + 4;                     // row stride of s_E (floats)
-  static constexpr int JB = B / 4, CB = DP / 4;         // 4x4 blocks of the contraction
+  static constexpr int JB = B / 4;                      // 4x4 blocks of the contraction
+  static constexpr int CB = DP / 4;
   static constexpr int TASKS = JB * CB;
   static constexpr int S = TASKS > 0 ? kT / TASKS : 1;  // pixel split per block
   static constexpr int G = kT / B;                      // threads per Gaussian in phase 2b
   static constexpr size_t smem_floats =
       (size_t)kT * ES           // s_E: upstream feature gradient per pixel
       + (size_t)3 * B * kWS     // s_W, s_GS, s_GO (j-major)
-      + (size_t)B * DP          // s_f: batch features
+      + (size_t)2 * B * DP      // s_f: batch features, double buffered
       + (size_t)B * DP;         // s_outF: batch feature-gradient sums
 };
 
+// Features of one batch: fetched into registers, stored to shared memory later.
 template <int DP, bool BF16, int B>
-__device__ __forceinline__ void stage_batch_features(const void* __restrict__ feats, int D,
-                                                     const uint32_t* __restrict__ s_id, int cnt,
-                                                     float* __restrict__ s_f) {
-  for (int e = threadIdx.x; e < B * DP; e += kT) {
-    const int j = e / DP, c = e - j * DP;
-    float v = 0.f;
-    if (j < cnt && c < D) {
-      const int64_t idx = (int64_t)s_id[j] * D + c;
-      if constexpr (BF16)
-        v = __bfloat162float(static_cast<const __nv_bfloat16*>(feats)[idx]);
-      else
-        v = __ldg(static_cast<const float*>(feats) + idx);
+struct FeatBatch {
+  static constexpr int VPC = BF16 ? 8 : 4;                 // values per 16-byte chunk
+  static constexpr int CPR = DP / VPC > 0 ? DP / VPC : 1;  // chunks per row
+  static constexpr int NS = (B * DP + kT - 1) / kT;        // scalar path values per thread
+  uint4 v;
+  float s[NS > 0 ? NS : 1];
+
+  __device__ __forceinline__ void fetch(const void* __restrict__ feats, int D,
+                                        const uint32_t* __restrict__ s_id, int jb0, int bc) {
+    const int t = threadIdx.x;
+    if (D == DP) {
+      v = make_uint4(0u, 0u, 0u, 0u);
+      if (t < B * CPR) {
+        const int j = t / CPR, part = t - j * CPR;
+        if (j < bc) {
+          const int64_t row = (int64_t)s_id[jb0 + j] * DP;
+          if constexpr (BF16)
+            v = __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(feats) + row) + part);
+          else
+            v = __ldg(reinterpret_cast<const uint4*>(static_cast<const float*>(feats) + row) + part);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const int e = t + k * kT;
+        float x = 0.f;
+        if (e < B * DP) {
+          const int j = e / DP, c = e - j * DP;
+          if (j < bc && c < D) {
+            const int64_t idx = (int64_t)s_id[jb0 + j] * D + c;
+            if constexpr (BF16)
+              x = __bfloat162float(static_cast<const __nv_bfloat16*>(feats)[idx]);
+            else
+              x = __ldg(static_cast<const float*>(feats) + idx);
+          }
+        }
+        s[k] = x;
+      }
     }
-    s_f[e] = v;
   }
-}
+
+  __device__ __forceinline__ void store(int D, float* __restrict__ s_f) const {
+    const int t = threadIdx.x;
+    if (D == DP) {
+      if (t < B * CPR) {
+        const int j = t / CPR, part = t - j * CPR;
+        float* dst = s_f + j * DP + part * VPC;
+        if constexpr (BF16) {
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            dst[2 * k] = __uint_as_float(w[k] << 16);
+            dst[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+          }
+        } else {
+          *reinterpret_cast<uint4*>(dst) = v;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const int e = t + k * kT;
+        if (e < B * DP) s_f[e] = s[k];
+      }
+    }
+  }
+};
 
 __device__ __forceinline__ void red_add4(float* dst, float a, float b, float c, float d) {
   atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a, b, c, d));
@@ -72,17 +130,19 @@ k_raster_bwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restric
              float* __restrict__ g2d, float* __restrict__ g_feats) {
   using Cfg = BwdCfg<DP>;
   constexpr int B = Cfg::B;
-  __shared__ float4 s_r0[B], s_r1[B], s_r2[B];
-  __shared__ uint32_t s_id[B];
-  __shared__ float4 s_E4[kT];                 // (g_r, g_g, g_b, g_depth) per pixel
+  __shared__ float4 s_r0[kT], s_r1[kT], s_r2[kT];   // compacted records of the chunk
+  __shared__ uint32_t s_id[kT];
+  __shared__ int s_orig[kT];                        // list position of each compacted entry
+  __shared__ float4 s_E4[kT];                       // (g_r, g_g, g_b, g_depth) per pixel
+  __shared__ int s_wc[8];
   __shared__ uint32_t s_maxn;
   extern __shared__ __align__(16) float smem[];
   float* s_E = smem;                          // [kT][ES]
   float* s_W = s_E + kT * Cfg::ES;            // [B][kWS]
   float* s_GS = s_W + B * kWS;
   float* s_GO = s_GS + B * kWS;
-  float* s_f = s_GO + B * kWS;                // [B][DP]
-  float* s_outF = s_f + B * DP;               // [B][DP]
+  float* s_fb = s_GO + B * kWS;               // [2][B][DP]
+  float* s_outF = s_fb + 2 * B * DP;          // [B][DP]
 
   const int t = threadIdx.x;
   const int tile = blockIdx.x;
@@ -120,6 +180,7 @@ k_raster_bwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restric
 #pragma unroll
     for (int c = 0; c < DP; c += 4)
       *reinterpret_cast<float4*>(s_E + t * Cfg::ES + c) = make_float4(gF[c], gF[c + 1], gF[c + 2], gF[c + 3]);
+    for (int e = t; e < B * DP; e += kT) s_outF[e] = 0.f;
   }
   s_E4[t] = make_float4(gC0, gC1, gC2, gD);
   if (t == 0) s_maxn = 0;
@@ -132,186 +193,214 @@ k_raster_bwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restric
   float T = Tf, s_run = 0.f;
   const float gAT = gA * Tf;
 
-  for (int b_end = maxn; b_end > 0; b_end -= B) {
-    const int b_start = max(0, b_end - B);
-    const int cnt = b_end - b_start;
-    if (t < cnt) {
-      const uint32_t id = inst_id[start + b_start + t];
-      const GaussRec g = rec[id];
-      s_r0[t] = g.r0;
-      s_r1[t] = g.r1;
-      s_r2[t] = g.r2;
-      s_id[t] = id;
+  for (int c1 = maxn; c1 > 0; c1 -= kT) {
+    const int c0 = max(0, c1 - kT);
+    // ---- gather the chunk [c0, c1) of the list, drop entries the tile cannot blend
+    __syncthreads();                          // previous chunk fully consumed
+    bool keep = false;
+    uint32_t id = 0;
+    GaussRec g;
+    if (t < c1 - c0) {
+      id = inst_id[start + c0 + t];
+      g = rec[id];
+      keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
     }
+    int nk;
+    const int pos = block_compact_index(keep, s_wc, &nk);
+    if (keep) {
+      s_r0[pos] = g.r0;
+      s_r1[pos] = g.r1;
+      s_r2[pos] = g.r2;
+      s_id[pos] = id;
+      s_orig[pos] = c0 + t;
+    }
+    __syncthreads();
+    FeatBatch<DP, BF16, B> fb;
     if constexpr (DP > 0) {
-      for (int e = t; e < B * DP; e += kT) s_outF[e] = 0.f;
+      fb.fetch(feats, D, s_id, max(0, nk - B), min(B, nk));
+      fb.store(D, s_fb);
+      __syncthreads();
     }
-    __syncthreads();
-    if constexpr (DP > 0) stage_batch_features<DP, BF16, B>(feats, D, s_id, cnt, s_f);
-    __syncthreads();
 
-    // ---- phase 1: per pixel, reverse over the batch
-    for (int j = B - 1; j >= 0; --j) {
-      float w = 0.f, gs = 0.f, go = 0.f;
-      if (j < cnt && b_start + j < nc) {
-        const float4 r0 = s_r0[j];
-        const float4 r1 = s_r1[j];
-        const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-        if (sigma >= 0.f) {
-          const float G = blend_gauss(sigma);
-          const float oG = __fmul_rn(r1.y, G);
-          const float a = fminf(kAlphaMax, oG);
-          if (a >= kAlphaMin) {
-            const float inv = __fdividef(1.f, 1.f - a);
-            T = T * inv;                        // T_i
-            w = a * T;
-            const float4 r2 = s_r2[j];
-            float dot = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r1.z;
-            if constexpr (DP > 0) {
-              const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
+    // ---- batches of the compacted chunk, last entries first
+    for (int jb1 = nk, bi = 0; jb1 > 0; jb1 -= B, ++bi) {
+      const int jb0 = max(0, jb1 - B), bc = jb1 - jb0;
+      const float* s_f = s_fb + (bi & 1) * B * DP;
+
+      // phase 1: per pixel, reverse over the batch
+      for (int j = B - 1; j >= 0; --j) {
+        float w = 0.f, gs = 0.f, go = 0.f;
+        if (j < bc && s_orig[jb0 + j] < nc) {
+          const float4 r0 = s_r0[jb0 + j];
+          const float4 r1 = s_r1[jb0 + j];
+          const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+          if (sigma >= 0.f) {
+            const float G = blend_gauss(sigma);
+            const float oG = __fmul_rn(r1.y, G);
+            const float a = fminf(kAlphaMax, oG);
+            if (a >= kAlphaMin) {
+              const float inv = __fdividef(1.f, 1.f - a);
+              T = T * inv;                        // T_i
+              w = a * T;
+              const float4 r2 = s_r2[jb0 + j];
+              float dot = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r1.z;
+              if constexpr (DP > 0) {
+                const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
 #pragma unroll
-              for (int q = 0; q < DP / 4; ++q) {
-                const float4 f = f4[q];
-                dot = fmaf(gF[4 * q], f.x, dot);
-                dot = fmaf(gF[4 * q + 1], f.y, dot);
-                dot = fmaf(gF[4 * q + 2], f.z, dot);
-                dot = fmaf(gF[4 * q + 3], f.w, dot);
+                for (int q = 0; q < DP / 4; ++q) {
+                  const float4 f = f4[q];
+                  dot = fmaf(gF[4 * q], f.x, dot);
+                  dot = fmaf(gF[4 * q + 1], f.y, dot);
+                  dot = fmaf(gF[4 * q + 2], f.z, dot);
+                  dot = fmaf(gF[4 * q + 3], f.w, dot);
+                }
+              }
+              const float galpha = T * (dot - s_run) + gAT * inv;
+              s_run = a * dot + (1.f - a) * s_run;
+              if (oG <= kAlphaMax) {
+                go = galpha * G;
+                gs = -galpha * a;
               }
             }
-            const float galpha = T * (dot - s_run) + gAT * inv;
-            s_run = a * dot + (1.f - a) * s_run;
-            if (oG <= kAlphaMax) {
-              go = galpha * G;
-              gs = -galpha * a;
-            }
           }
         }
+        s_W[j * kWS + t] = w;
+        s_GS[j * kWS + t] = gs;
+        s_GO[j * kWS + t] = go;
       }
-      s_W[j * kWS + t] = w;
-      s_GS[j * kWS + t] = gs;
-      s_GO[j * kWS + t] = go;
-    }
-    __syncthreads();
+      __syncthreads();
 
-    // ---- phase 2a: feature gradients, out[j][c] = sum_p W[j][p] g_F[p][c]
-    if constexpr (DP > 0) {
-      if (g_feats && t < Cfg::TASKS * Cfg::S) {
-        const int cb = t % Cfg::CB;
-        const int jb = (t / Cfg::CB) % Cfg::JB;
-        const int part = t / Cfg::TASKS;
-        constexpr int PP = kT / Cfg::S;     // pixels per part
-        float acc[4][4];
+      // next batch's features: fetch now, store after phase 2
+      const bool more = jb0 > 0;
+      if constexpr (DP > 0) {
+        if (more) fb.fetch(feats, D, s_id, max(0, jb0 - B), min(B, jb0));
+      }
+
+      // phase 2a: feature gradients, out[j][c] = sum_p W[j][p] g_F[p][c]
+      if constexpr (DP > 0) {
+        if (g_feats) {
+          const int cb = t % Cfg::CB;
+          const int jb = (t / Cfg::CB) % Cfg::JB;
+          const int part = t / Cfg::TASKS;
+          constexpr int PP = kT / Cfg::S;     // pixels per part
+          float acc[4][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+          for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-        const int p0 = part * PP;
+            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+          const int p0 = part * PP;
 #pragma unroll 2
-        for (int q = p0; q < p0 + PP; q += 4) {
-          float4 wv[4], ev[4];
+          for (int q = p0; q < p0 + PP; q += 4) {
+            float4 wv[4], ev[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) wv[a] = *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q);
+            for (int a = 0; a < 4; ++a) wv[a] = *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q);
 #pragma unroll
-          for (int b = 0; b < 4; ++b) ev[b] = *reinterpret_cast<const float4*>(s_E + (q + b) * Cfg::ES + 4 * cb);
+            for (int b = 0; b < 4; ++b) ev[b] = *reinterpret_cast<const float4*>(s_E + (q + b) * Cfg::ES + 4 * cb);
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const float wa[4] = {wv[a].x, wv[a].y, wv[a].z, wv[a].w};
+            for (int a = 0; a < 4; ++a) {
+              const float wa[4] = {wv[a].x, wv[a].y, wv[a].z, wv[a].w};
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                acc[a][0] = fmaf(wa[b], ev[b].x, acc[a][0]);
+                acc[a][1] = fmaf(wa[b], ev[b].y, acc[a][1]);
+                acc[a][2] = fmaf(wa[b], ev[b].z, acc[a][2]);
+                acc[a][3] = fmaf(wa[b], ev[b].w, acc[a][3]);
+              }
+            }
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-              acc[a][0] = fmaf(wa[b], ev[b].x, acc[a][0]);
-              acc[a][1] = fmaf(wa[b], ev[b].y, acc[a][1]);
-              acc[a][2] = fmaf(wa[b], ev[b].z, acc[a][2]);
-              acc[a][3] = fmaf(wa[b], ev[b].w, acc[a][3]);
+              if (Cfg::S > 1)
+                atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
+              else
+                s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
+            }
+        }
+      }
+
+      // phase 2b: per Gaussian sums over pixels (G threads per Gaussian, consecutive lanes)
+      {
+        constexpr int G = Cfg::G;
+        const int j = t / G, pg = t % G;
+        float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+        float so = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sz = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < kT / G; ++k) {
+          const int q = pg + k * G;
+          const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
+          const float4 e = s_E4[q];
+          const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;
+          m1 += gs;
+          mx = fmaf(gs, x, mx);
+          my = fmaf(gs, y, my);
+          mxx = fmaf(gs * x, x, mxx);
+          mxy = fmaf(gs * x, y, mxy);
+          myy = fmaf(gs * y, y, myy);
+          so += go;
+          sr = fmaf(w, e.x, sr);
+          sg = fmaf(w, e.y, sg);
+          sb = fmaf(w, e.z, sb);
+          sz = fmaf(w, e.w, sz);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+          m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+          mx += __shfl_xor_sync(0xffffffffu, mx, o);
+          my += __shfl_xor_sync(0xffffffffu, my, o);
+          mxx += __shfl_xor_sync(0xffffffffu, mxx, o);
+          mxy += __shfl_xor_sync(0xffffffffu, mxy, o);
+          myy += __shfl_xor_sync(0xffffffffu, myy, o);
+          so += __shfl_xor_sync(0xffffffffu, so, o);
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          sg += __shfl_xor_sync(0xffffffffu, sg, o);
+          sb += __shfl_xor_sync(0xffffffffu, sb, o);
+          sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        if (pg == 0 && j < bc) {
+          const float4 r0 = s_r0[jb0 + j];
+          const float4 r1 = s_r1[jb0 + j];
+          // moments are about the tile centre: pixel offset dx = x - uc with uc = u - centre
+          const float uc = r0.x - ((float)tx0 + 8.f), vc = r0.y - ((float)ty0 + 8.f);
+          const float A = r0.z, Bq = r0.w, C = r1.x;
+          const float sdx = mx - uc * m1, sdy = my - vc * m1;            // sum gs dx, sum gs dy
+          const float sdxx = mxx - 2.f * uc * mx + uc * uc * m1;         // sum gs dx^2
+          const float sdyy = myy - 2.f * vc * my + vc * vc * m1;
+          const float sdxy = mxy - uc * my - vc * mx + uc * vc * m1;
+          const float gAq = 0.5f * sdxx, gBq = sdxy, gCq = 0.5f * sdyy;
+          const float gu = -(A * sdx + Bq * sdy), gv = -(C * sdy + Bq * sdx);
+          float* dst = g2d + (int64_t)s_id[jb0 + j] * kG2D;
+          red_add4(dst, gu, gv, gAq, gBq);
+          red_add4(dst + 4, gCq, so, sr, sg);
+          red_add4(dst + 8, sb, sz, 0.f, 0.f);
+        }
+      }
+      if constexpr (DP > 0) {
+        if (more) fb.store(D, s_fb + ((bi + 1) & 1) * B * DP);
+      }
+      __syncthreads();
+
+      // flush and clear the batch's feature-gradient sums
+      if constexpr (DP > 0) {
+        if (g_feats) {
+          if (D == DP) {
+            for (int e = t; e < bc * (DP / 4); e += kT) {
+              const int j = e / (DP / 4), q = e - j * (DP / 4);
+              float4* so = reinterpret_cast<float4*>(s_outF + j * DP + 4 * q);
+              atomicAdd(reinterpret_cast<float4*>(g_feats + (int64_t)s_id[jb0 + j] * D + 4 * q), *so);
+              *so = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          } else {
+            for (int e = t; e < bc * DP; e += kT) {
+              const int j = e / DP, c = e - j * DP;
+              if (c < D) atomicAdd(g_feats + (int64_t)s_id[jb0 + j] * D + c, s_outF[e]);
+              s_outF[e] = 0.f;
             }
           }
         }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            if (Cfg::S > 1)
-              atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
-            else
-              s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
-          }
       }
     }
-
-    // ---- phase 2b: per Gaussian sums over pixels (G threads per Gaussian, consecutive lanes)
-    {
-      constexpr int G = Cfg::G;
-      const int j = t / G, pg = t % G;
-      float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
-      float so = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sz = 0.f;
-#pragma unroll 4
-      for (int k = 0; k < kT / G; ++k) {
-        const int q = pg + k * G;
-        const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
-        const float4 e = s_E4[q];
-        const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;
-        m1 += gs;
-        mx = fmaf(gs, x, mx);
-        my = fmaf(gs, y, my);
-        mxx = fmaf(gs * x, x, mxx);
-        mxy = fmaf(gs * x, y, mxy);
-        myy = fmaf(gs * y, y, myy);
-        so += go;
-        sr = fmaf(w, e.x, sr);
-        sg = fmaf(w, e.y, sg);
-        sb = fmaf(w, e.z, sb);
-        sz = fmaf(w, e.w, sz);
-      }
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) {
-        m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-        mx += __shfl_xor_sync(0xffffffffu, mx, o);
-        my += __shfl_xor_sync(0xffffffffu, my, o);
-        mxx += __shfl_xor_sync(0xffffffffu, mxx, o);
-        mxy += __shfl_xor_sync(0xffffffffu, mxy, o);
-        myy += __shfl_xor_sync(0xffffffffu, myy, o);
-        so += __shfl_xor_sync(0xffffffffu, so, o);
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        sg += __shfl_xor_sync(0xffffffffu, sg, o);
-        sb += __shfl_xor_sync(0xffffffffu, sb, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-      }
-      if (pg == 0 && j < cnt) {
-        const float4 r0 = s_r0[j];
-        const float4 r1 = s_r1[j];
-        // moments are about the tile centre: pixel offset dx = x - uc with uc = u - centre
-        const float uc = r0.x - ((float)tx0 + 8.f), vc = r0.y - ((float)ty0 + 8.f);
-        const float A = r0.z, Bq = r0.w, C = r1.x;
-        const float sdx = mx - uc * m1, sdy = my - vc * m1;            // sum gs dx, sum gs dy
-        const float sdxx = mxx - 2.f * uc * mx + uc * uc * m1;         // sum gs dx^2
-        const float sdyy = myy - 2.f * vc * my + vc * vc * m1;
-        const float sdxy = mxy - uc * my - vc * mx + uc * vc * m1;
-        const float gAq = 0.5f * sdxx, gBq = sdxy, gCq = 0.5f * sdyy;
-        const float gu = -(A * sdx + Bq * sdy), gv = -(C * sdy + Bq * sdx);
-        float* dst = g2d + (int64_t)s_id[j] * kG2D;
-        red_add4(dst, gu, gv, gAq, gBq);
-        red_add4(dst + 4, gCq, so, sr, sg);
-        red_add4(dst + 8, sb, sz, 0.f, 0.f);
-      }
-    }
-    __syncthreads();
-    // ---- flush feature gradients of the batch
-    if constexpr (DP > 0) {
-      if (g_feats) {
-        if (D == DP) {
-          for (int e = t; e < cnt * (DP / 4); e += kT) {
-            const int j = e / (DP / 4), q = e - j * (DP / 4);
-            const float4 v = *reinterpret_cast<const float4*>(s_outF + j * DP + 4 * q);
-            atomicAdd(reinterpret_cast<float4*>(g_feats + (int64_t)s_id[j] * D + 4 * q), v);
-          }
-        } else {
-          for (int e = t; e < cnt * DP; e += kT) {
-            const int j = e / DP, c = e - j * DP;
-            if (c < D) atomicAdd(g_feats + (int64_t)s_id[j] * D + c, s_outF[e]);
-          }
-        }
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -331,6 +420,7 @@ void launch_t(const CamDev& cam, const GaussRec* rec, const void* feats, int D, 
   }
   kern<<<cam.TX * cam.TY, kT, smem, st>>>(cam, rec, feats, D, ranges, inst_id, T_final, n_contrib,
                                           g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats);
+  note_launch();
 }
 
 }  // namespace

@@ -69,11 +69,14 @@ k_raster_fwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restric
              uint32_t* __restrict__ n_contrib) {
   __shared__ float4 s_r0[kB], s_r1[kB], s_r2[kB];
   __shared__ uint32_t s_id[kB];
+  __shared__ int s_orig[kB];
+  __shared__ int s_wc[8];
   extern __shared__ __align__(16) float s_feat[];   // [kB][DP]
 
   const int tile = blockIdx.x;
-  const int px = (tile % cam.TX) * kTile + (threadIdx.x & 15);
-  const int py = (tile / cam.TX) * kTile + (threadIdx.x >> 4);
+  const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
+  const int px = tx0 + (threadIdx.x & 15);
+  const int py = ty0 + (threadIdx.x >> 4);
   const bool inside = px < cam.W && py < cam.H;
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
   const uint2 rg = ranges[tile];
@@ -89,18 +92,28 @@ k_raster_fwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restric
   for (int b0 = start; b0 < end; b0 += kB) {
     if (__syncthreads_count(done) == kB) break;
     const int cnt = min(kB, end - b0);
+    // gather the batch and drop entries that no pixel of this tile can blend
+    bool keep = false;
+    uint32_t id = 0;
+    GaussRec g;
     if ((int)threadIdx.x < cnt) {
-      const uint32_t id = inst_id[b0 + threadIdx.x];
-      const GaussRec g = rec[id];
-      s_r0[threadIdx.x] = g.r0;
-      s_r1[threadIdx.x] = g.r1;
-      s_r2[threadIdx.x] = g.r2;
-      s_id[threadIdx.x] = id;
+      id = inst_id[b0 + threadIdx.x];
+      g = rec[id];
+      keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
+    }
+    int nk;
+    const int pos = block_compact_index(keep, s_wc, &nk);
+    if (keep) {
+      s_r0[pos] = g.r0;
+      s_r1[pos] = g.r1;
+      s_r2[pos] = g.r2;
+      s_id[pos] = id;
+      s_orig[pos] = b0 + (int)threadIdx.x - start;
     }
     __syncthreads();
-    stage_features<DP, BF16>(feats, D, s_id, cnt, s_feat);
+    stage_features<DP, BF16>(feats, D, s_id, nk, s_feat);
     __syncthreads();
-    for (int j = 0; j < cnt; ++j) {
+    for (int j = 0; j < nk; ++j) {
       if (__all_sync(0xffffffffu, done)) break;
       const float4 r0 = s_r0[j];
       const float4 r1 = s_r1[j];
@@ -116,7 +129,7 @@ k_raster_fwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restric
             } else {
               w = __fmul_rn(a, T);
               T = Tn;
-              last = b0 + j - start + 1;
+              last = s_orig[j] + 1;
             }
           }
         }
@@ -177,6 +190,7 @@ void launch_t(const CamDev& cam, const GaussRec* rec, const void* feats, int D, 
   }
   kern<<<cam.TX * cam.TY, kB, smem, st>>>(cam, rec, feats, D, ranges, inst_id, rgb, depth, alpha,
                                           feat, T_final, n_contrib);
+  note_launch();
 }
 
 }  // namespace

@@ -57,17 +57,36 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
 // ---------------------------------------------------------------- device-wide scan
 // Each block owns kChunk consecutive elements.
 
+// The kItems consecutive elements [i0, i0 + kItems) of a thread, zero past n; 16-byte
+// loads when the whole run is in range (buffers are 16-byte aligned, i0 is a multiple of 16).
+__device__ __forceinline__ void load_run(const uint32_t* in, int64_t i0, int64_t n, uint32_t* v) {
+  if (i0 + kItems <= n) {
+    const uint4* p = reinterpret_cast<const uint4*>(in + i0);
+#pragma unroll
+    for (int k = 0; k < kItems / 4; ++k) {
+      const uint4 q = p[k];
+      v[4 * k] = q.x;
+      v[4 * k + 1] = q.y;
+      v[4 * k + 2] = q.z;
+      v[4 * k + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) v[k] = i0 + k < n ? in[i0 + k] : 0u;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_scan_reduce(const uint32_t* __restrict__ in, const uint32_t* d_n, int64_t bound,
               uint32_t* __restrict__ partial) {
   __shared__ uint32_t s_warp[kWarps];
   const int64_t n = dev_count(d_n, bound);
-  const int64_t base = (int64_t)blockIdx.x * kChunk;
+  const int64_t i0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kItems;
+  uint32_t v[kItems];
+  load_run(in, i0, n, v);
   uint32_t sum = 0;
-  for (int k = 0; k < kItems; ++k) {
-    const int64_t i = base + k * kThreads + threadIdx.x;
-    if (i < n) sum += in[i];
-  }
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) sum += v[k];
   uint32_t total;
   block_exclusive_scan(sum, s_warp, &total);
   if (threadIdx.x == 0) partial[blockIdx.x] = total;
@@ -96,14 +115,28 @@ k_scan_down(const uint32_t* in, uint32_t* out, const uint32_t* d_n, int64_t boun
   const int64_t n = dev_count(d_n, bound);
   const int64_t base = (int64_t)blockIdx.x * kChunk;
   if (base >= n) return;
-  uint32_t carry = partial[blockIdx.x];
+  const int64_t i0 = base + (int64_t)threadIdx.x * kItems;
+  uint32_t v[kItems];
+  load_run(in, i0, n, v);
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kItems; ++k) sum += v[k];
+  uint32_t tot;
+  uint32_t run = partial[blockIdx.x] + block_exclusive_scan(sum, s_warp, &tot);
+#pragma unroll
   for (int k = 0; k < kItems; ++k) {
-    const int64_t i = base + k * kThreads + threadIdx.x;
-    const uint32_t v = i < n ? in[i] : 0;
-    uint32_t tot;
-    const uint32_t ex = block_exclusive_scan(v, s_warp, &tot);
-    if (i < n) out[i] = carry + ex;
-    carry += tot;
+    const uint32_t x = v[k];
+    v[k] = run;
+    run += x;
+  }
+  if (i0 + kItems <= n) {
+    uint4* q = reinterpret_cast<uint4*>(out + i0);
+#pragma unroll
+    for (int k = 0; k < kItems / 4; ++k) q[k] = make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kItems; ++k)
+      if (i0 + k < n) out[i0 + k] = v[k];
   }
 }
 
@@ -117,6 +150,7 @@ void scan_impl(const uint32_t* in, uint32_t* out, const uint32_t* d_n, int64_t b
   k_scan_reduce<<<nb, kThreads, 0, st>>>(in, d_n, bound, temp);
   k_scan_partials<<<1, kThreads, 0, st>>>(temp, nb, total_out);
   k_scan_down<<<nb, kThreads, 0, st>>>(in, out, d_n, bound, temp);
+  note_launch(3);
 }
 
 // ---------------------------------------------------------------- radix sort passes
@@ -314,6 +348,7 @@ int radix_sort_pairs(const uint32_t* d_n, int64_t bound, uint32_t* k0, uint32_t*
     k_radix_hist<<<nchunks, kThreads, 0, st>>>(ki, d_n, bound, shift, nchunks, hist);
     scan_impl(hist, hist, nullptr, hwords, scan_temp, nullptr, st);
     k_radix_scatter<<<nchunks, kThreads, 0, st>>>(ki, vi, ko, vo, d_n, bound, shift, nchunks, hist);
+    note_launch(2);
     cur ^= 1;
   }
   return cur;
@@ -330,6 +365,7 @@ void launch_compact_visible(const uint32_t* ntiles, const uint32_t* depth_key, i
   k_visible_flags<<<g, 256, 0, st>>>(ntiles, n, flags_scan);
   scan_impl(flags_scan, flags_scan, nullptr, n, scan_temp, counters + kCntVisible, st);
   k_compact<<<g, 256, 0, st>>>(ntiles, depth_key, flags_scan, n, out_keys, out_ids);
+  note_launch(2);
 }
 
 void launch_tile_offsets(const uint32_t* sorted_ids, const uint32_t* ntiles, int64_t bound_v,
@@ -342,6 +378,7 @@ void launch_tile_offsets(const uint32_t* sorted_ids, const uint32_t* ntiles, int
   k_gather_counts<<<(int)ceil_div(bound_v, 256), 256, 0, st>>>(sorted_ids, ntiles,
                                                                counters + kCntVisible, bound_v,
                                                                offsets);
+  note_launch();
   scan_impl(offsets, offsets, counters + kCntVisible, bound_v, scan_temp, counters + kCntInst, st);
 }
 
@@ -352,6 +389,7 @@ void launch_emit_instances(const uint32_t* sorted_ids, const uint2* rect, const 
   k_emit<<<(int)ceil_div(bound_v, 256), 256, 0, st>>>(sorted_ids, rect, offsets,
                                                       counters + kCntVisible, bound_v, TX,
                                                       counters, cap, inst_tile, inst_id);
+  note_launch();
 }
 
 void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int64_t bound_i,
@@ -360,13 +398,17 @@ void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int
   const int64_t b = min64(bound_i, cap);
   if (b <= 0) return;
   k_ranges<<<(int)ceil_div(b, 256), 256, 0, st>>>(inst_tile, counters, bound_i, cap, ranges);
+  note_launch();
 }
 
 void launch_inst_eff(const uint2* ranges, const uint32_t* n_contrib, int TX, int TY, int W, int H,
                      uint32_t* counters, cudaStream_t st) {
   (void)ranges;
   cudaMemsetAsync(counters + kCntInstEff, 0, 4, st);
-  if (TX * TY > 0) k_inst_eff<<<TX * TY, kThreads, 0, st>>>(n_contrib, TX, W, H, counters);
+  if (TX * TY > 0) {
+    k_inst_eff<<<TX * TY, kThreads, 0, st>>>(n_contrib, TX, W, H, counters);
+    note_launch();
+  }
 }
 
 }  // namespace gs
