@@ -207,11 +207,13 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     n0 = L.gs_launch_count()
+    torch.cuda.nvtx.range_push("timed")   # lets a profiler capture exactly these steps
     for k in range(args.steps):
         evs[k][0].record(stream)
         step(gcams[poses[args.warmup + k]], gf)
         evs[k][1].record(stream)
         flush.fill_(float(k))
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

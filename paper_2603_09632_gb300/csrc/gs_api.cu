@@ -46,7 +46,7 @@ struct gs_workspace {
   int device = 0;
   // per Gaussian
   DevBuf<GaussRec> rec;
-  DevBuf<uint32_t> depth_key, ntiles, flags, vis_keys, vis_ids, alt_keys, alt_vals, offsets;
+  DevBuf<uint32_t> depth_key, ntiles, sort_k0, sort_v0, sort_k1, sort_v1;
   DevBuf<uint2> rect;
   DevBuf<float> g2d;
   DevBuf<float> pose_partials;
@@ -57,7 +57,9 @@ struct gs_workspace {
   DevBuf<float> T_final;
   DevBuf<uint32_t> n_contrib;
   // scratch
-  DevBuf<uint32_t> hist, scan_temp, counters;
+  DevBuf<uint32_t> bin_zero, counters;   // bin_zero: digit histograms + chunk tickets
+  DevBuf<unsigned long long> bin_status;  // look-back status words
+  uint32_t epoch = 0;
   uint32_t* h_counters = nullptr;   // pinned mirror
   // state
   int64_t n = 0;
@@ -123,6 +125,8 @@ gs_status make_cam(const gs_camera* c, CamDev* out) {
   if (!c) return GS_ERR_ARG;
   if (c->W <= 0 || c->H <= 0 || c->W > 65535 * kTile || c->H > 65535 * kTile) return GS_ERR_ARG;
   if (c->tile != kTile) return GS_ERR_ARG;
+  if ((int64_t)((c->W + kTile - 1) / kTile) * ((c->H + kTile - 1) / kTile) > (int64_t(1) << 24))
+    return GS_ERR_ARG;
   if (!(c->fx > 0.f) || !(c->fy > 0.f) || !(c->near_z > 0.f)) return GS_ERR_ARG;
   if (c->stride != 1 || c->off_x != 0 || c->off_y != 0) return GS_ERR_ARG;
   out->W = c->W;
@@ -161,18 +165,25 @@ struct StageTimer {
   }
 };
 
+// Look-back status words: zeroed once when (re)allocated, epoch-tagged afterwards.
+cudaError_t ensure_status(gs_workspace* ws, int64_t elems) {
+  const size_t need = bin_status_words(elems);
+  if (need <= ws->bin_status.cap) return cudaSuccess;
+  cudaError_t e = ws->bin_status.ensure(need);
+  if (e != cudaSuccess) return e;
+  return cudaMemset(ws->bin_status.p, 0, ws->bin_status.cap * sizeof(unsigned long long));
+}
+
 cudaError_t ensure_gauss(gs_workspace* ws, int64_t n) {
   const size_t m = (size_t)std::max<int64_t>(n, 1);
   cudaError_t e;
   if ((e = ws->rec.ensure(m)) || (e = ws->depth_key.ensure(m)) || (e = ws->ntiles.ensure(m)) ||
-      (e = ws->flags.ensure(m)) || (e = ws->vis_keys.ensure(m)) || (e = ws->vis_ids.ensure(m)) ||
-      (e = ws->alt_keys.ensure(m)) || (e = ws->alt_vals.ensure(m)) ||
-      (e = ws->offsets.ensure(m)) || (e = ws->rect.ensure(m)) ||
+      (e = ws->sort_k0.ensure(m)) || (e = ws->sort_v0.ensure(m)) ||
+      (e = ws->sort_k1.ensure(m)) || (e = ws->sort_v1.ensure(m)) || (e = ws->rect.ensure(m)) ||
       (e = ws->g2d.ensure(m * kG2D)) ||
       (e = ws->pose_partials.ensure((size_t)project_bwd_blocks(n) * 8)))
     return e;
-  if ((e = ws->hist.ensure(radix_hist_words(n))) || (e = ws->scan_temp.ensure(scan_temp_words(n)))) return e;
-  return ws->scan_temp.ensure(scan_temp_words((int64_t)radix_hist_words(n)));
+  return ensure_status(ws, n);
 }
 
 cudaError_t ensure_inst(gs_workspace* ws, int64_t cap) {
@@ -181,8 +192,7 @@ cudaError_t ensure_inst(gs_workspace* ws, int64_t cap) {
   if ((e = ws->inst_tile.ensure(m)) || (e = ws->inst_id.ensure(m)) ||
       (e = ws->inst_tile2.ensure(m)) || (e = ws->inst_id2.ensure(m)))
     return e;
-  if ((e = ws->hist.ensure(radix_hist_words(cap)))) return e;
-  return ws->scan_temp.ensure(scan_temp_words((int64_t)radix_hist_words(cap)));
+  return ensure_status(ws, cap);
 }
 
 cudaError_t ensure_pix(gs_workspace* ws, int64_t npix, int64_t ntiles) {
@@ -221,7 +231,8 @@ gs_status gs_workspace_create(gs_workspace** out, int device) {
   if (!ws) return GS_ERR_OOM;
   ws->device = device;
   DeviceGuard g(device);
-  if (ws->counters.ensure(kCntNum) != cudaSuccess ||
+  if (ws->counters.ensure(kCntNum) != cudaSuccess || ws->bin_zero.ensure(kBinZeroWords) != cudaSuccess ||
+      cudaMemset(ws->bin_zero.p, 0, kBinZeroWords * sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(ws->counters.p, 0, kCntNum * sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ws->h_counters, kCntNum * sizeof(uint32_t)) != cudaSuccess) {
     gs_workspace_destroy(ws);
@@ -236,12 +247,12 @@ void gs_workspace_destroy(gs_workspace* ws) {
   {
     DeviceGuard g(ws->device);
     cudaDeviceSynchronize();
-    ws->rec.release(); ws->depth_key.release(); ws->ntiles.release(); ws->flags.release();
-    ws->vis_keys.release(); ws->vis_ids.release(); ws->alt_keys.release(); ws->alt_vals.release();
-    ws->offsets.release(); ws->rect.release(); ws->g2d.release(); ws->pose_partials.release();
+    ws->rec.release(); ws->depth_key.release(); ws->ntiles.release();
+    ws->sort_k0.release(); ws->sort_v0.release(); ws->sort_k1.release(); ws->sort_v1.release();
+    ws->rect.release(); ws->g2d.release(); ws->pose_partials.release();
     ws->inst_tile.release(); ws->inst_id.release(); ws->inst_tile2.release(); ws->inst_id2.release();
     ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
-    ws->hist.release(); ws->scan_temp.release(); ws->counters.release();
+    ws->bin_zero.release(); ws->bin_status.release(); ws->counters.release();
     if (ws->h_counters) cudaFreeHost(ws->h_counters);
     if (ws->ev_created)
       for (int k = 0; k < GS_NUM_TIMERS; ++k)
@@ -286,12 +297,15 @@ gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
   if (s != GS_OK) return s;
   CamDev cd;
   if ((s = make_cam(cam, &cd)) != GS_OK) return s;
+  cd.n_gauss = (int)scene->n;
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
   GS_TRY(ensure_gauss(ws, scene->n));
   GS_TRY(ensure_pix(ws, (int64_t)cd.W * cd.H, (int64_t)cd.TX * cd.TY));
   StageTimer tm(ws, GS_TIMER_PROJECT, st);
-  launch_project(*scene, cd, ws->rec.p, ws->depth_key.p, ws->ntiles.p, ws->rect.p, st);
+  GS_TRY(cudaMemsetAsync(ws->counters.p + kCntVisible, 0, 2 * sizeof(uint32_t), st));
+  launch_project(*scene, cd, ws->rec.p, ws->depth_key.p, ws->ntiles.p, ws->rect.p, ws->counters.p,
+                 st);
   GS_TRY(cudaGetLastError());
   ws->n = scene->n;
   ws->W = cd.W;
@@ -311,36 +325,40 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   const int ntl = ws->TX * ws->TY;
   StageTimer tm(ws, GS_TIMER_BIN, st);
   uint32_t* cnt = ws->counters.p;
-  // 1. visible compaction (id order), 2. depth sort
-  launch_compact_visible(ws->ntiles.p, ws->depth_key.p, n, ws->flags.p, ws->vis_keys.p,
-                         ws->vis_ids.p, cnt, ws->scan_temp.p, st);
-  const int which = radix_sort_pairs(cnt + kCntVisible, n, ws->vis_keys.p, ws->vis_ids.p,
-                                     ws->alt_keys.p, ws->alt_vals.p, 32, ws->hist.p,
-                                     ws->scan_temp.p, st);
-  const uint32_t* sorted_ids = which ? ws->alt_vals.p : ws->vis_ids.p;
-  // 3. tile counts in depth order -> offsets, I
-  launch_tile_offsets(sorted_ids, ws->ntiles.p, n, cnt, ws->offsets.p, ws->scan_temp.p, st);
+  BinScratch bs;
+  bs.ghist = ws->bin_zero.p;
+  bs.tickets = ws->bin_zero.p + 7 * 256;
+  bs.status = ws->bin_status.p;
+  bs.counters = cnt;
+  bs.epoch = &ws->epoch;
+  GS_TRY(cudaMemsetAsync(ws->bin_zero.p, 0, kBinZeroWords * sizeof(uint32_t), st));
   int64_t bound;
   if (n_instances_out) {
+    // I was counted by the projection: one synchronisation, then size the instance buffers
     GS_TRY(cudaMemcpyAsync(ws->h_counters, cnt, kCntNum * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     GS_TRY(cudaStreamSynchronize(st));
     bound = (int64_t)ws->h_counters[kCntInst];
     GS_TRY(ensure_inst(ws, bound));
+    bs.status = ws->bin_status.p;
     *n_instances_out = bound;
   } else {
     bound = (int64_t)ws->inst_tile.cap;
   }
   const int64_t cap = (int64_t)ws->inst_tile.cap;
-  // 4. emit instances, 5. stable sort by tile, 6. ranges
-  launch_emit_instances(sorted_ids, ws->rect.p, ws->offsets.p, n, ws->TX, cnt, cap,
-                        ws->inst_tile.p, ws->inst_id.p, st);
-  const int w2 = radix_sort_pairs(cnt + kCntInst, std::min(bound, cap), ws->inst_tile.p,
-                                  ws->inst_id.p, ws->inst_tile2.p, ws->inst_id2.p, bits_for(ntl),
-                                  ws->hist.p, ws->scan_temp.p, st);
+  // 1. depth sort of all Gaussians (culled ones last), 2. emit instances in depth order,
+  // 3. stable sort of the instances by tile, 4. tile ranges
+  launch_depth_sort(ws->depth_key.p, n, ws->sort_k1.p, ws->sort_v1.p, ws->sort_k0.p, ws->sort_v0.p,
+                    bs, st);
+  const uint32_t* sorted_ids = ws->sort_v0.p;
+  // the depth sort's ping-pong key buffer is free now: it holds the tile-count offsets
+  launch_emit_instances(sorted_ids, ws->ntiles.p, ws->rect.p, n, ws->TX, cap, ws->sort_k1.p,
+                        ws->inst_tile.p, ws->inst_id.p, bs, st);
+  const int w2 = launch_tile_sort(min64(bound, cap), bits_for(ntl), ws->inst_tile.p, ws->inst_id.p,
+                                  ws->inst_tile2.p, ws->inst_id2.p, bs, st);
   ws->tile_sorted = w2 ? ws->inst_tile2.p : ws->inst_tile.p;
   ws->id_sorted = w2 ? ws->inst_id2.p : ws->inst_id.p;
   ws->sorted_ids = sorted_ids;
-  launch_tile_ranges(ws->tile_sorted, cnt, std::min(bound, cap), cap, ntl, ws->ranges.p, st);
+  launch_tile_ranges(ws->tile_sorted, cnt, min64(bound, cap), cap, ntl, ws->ranges.p, st);
   GS_TRY(cudaGetLastError());
   ws->inst_bound = std::min(bound, cap);
   ws->stage = 2;
@@ -354,6 +372,7 @@ gs_status gs_render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
   if (s != GS_OK) return s;
   CamDev cd;
   if ((s = make_cam(cam, &cd)) != GS_OK) return s;
+  cd.n_gauss = (int)scene->n;
   if (ws->stage < 2 || scene->n != ws->n || cd.W != ws->W || cd.H != ws->H) return GS_ERR_STATE;
   if (feat && scene->n_feat > 0 && !aligned16(feat)) return GS_ERR_ARG;
   DeviceGuard g(ws->device);
@@ -376,6 +395,7 @@ gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
   if (s != GS_OK) return s;
   CamDev cd;
   if ((s = make_cam(cam, &cd)) != GS_OK) return s;
+  cd.n_gauss = (int)scene->n;
   if (ws->stage < 3 || scene->n != ws->n || cd.W != ws->W || cd.H != ws->H) return GS_ERR_STATE;
   if (g_feats && !aligned16(g_feats)) return GS_ERR_ARG;
   if (g_quats && !aligned16(g_quats)) return GS_ERR_ARG;
@@ -415,7 +435,7 @@ gs_status gs_get_stats(gs_workspace* ws, gs_stats* out, void* stream) {
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
   if (ws->stage >= 3)
-    launch_inst_eff(ws->ranges.p, ws->n_contrib.p, ws->TX, ws->TY, ws->W, ws->H, ws->counters.p, st);
+    launch_inst_eff(ws->n_contrib.p, ws->TX, ws->TY, ws->W, ws->H, ws->counters.p, st);
   GS_TRY(cudaMemcpyAsync(ws->h_counters, ws->counters.p, kCntNum * sizeof(uint32_t),
                          cudaMemcpyDeviceToHost, st));
   GS_TRY(cudaStreamSynchronize(st));

@@ -23,6 +23,7 @@ struct __align__(16) GaussRec {
 // Camera as the kernels see it.
 struct CamDev {
   int W, H, TX, TY;
+  int n_gauss;   // number of Gaussians (bounds check of gathered ids)
   float fx, fy, cx, cy;
   float R[9];
   float t[3];
@@ -33,6 +34,7 @@ struct CamDev {
 enum : uint32_t {
   kErrInstOverflow = 1u,   // instance count above reserved capacity (no-sync binning)
   kErrBadRange = 2u,       // a tile range outside the instance array (guard)
+  kErrLookback = 4u,       // a sort/scan look-back wait ran out (bounded spin)
 };
 
 // Device counters (one small array in the workspace).
@@ -47,40 +49,47 @@ enum : int {
 // ---- launchers (each .cu file defines its own) --------------------------------------
 
 // gs_project_fwd.cu
+// Also adds V (visible Gaussians) and I (tile instances) to counters[kCntVisible/kCntInst].
 void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32_t* depth_key,
-                    uint32_t* ntiles, uint2* rect, cudaStream_t st);
+                    uint32_t* ntiles, uint2* rect, uint32_t* counters, cudaStream_t st);
 
 // gs_sort.cu
-size_t scan_temp_words(int64_t n);
-// exclusive scan of n u32 (n known on the host); in may equal out
-void device_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* temp,
-                           cudaStream_t st);
-// number of histogram words the radix sort needs for `bound` elements
-size_t radix_hist_words(int64_t bound);
-// Stable LSD radix sort of (key, val) pairs over key bits [0, end_bit).  The element count
-// is *d_n (device), at most `bound` (host).  Ping-pongs between (k0,v0) and (k1,v1);
-// returns 0 if the result is in (k0, v0), 1 if in (k1, v1).
-int radix_sort_pairs(const uint32_t* d_n, int64_t bound, uint32_t* k0, uint32_t* v0,
-                     uint32_t* k1, uint32_t* v1, int end_bit, uint32_t* hist,
-                     uint32_t* scan_temp, cudaStream_t st);
-// visible compaction: ids and depth keys of Gaussians with ntiles > 0, in id order;
-// writes V to counters[kCntVisible].
-void launch_compact_visible(const uint32_t* ntiles, const uint32_t* depth_key, int64_t n,
-                            uint32_t* flags_scan, uint32_t* out_keys, uint32_t* out_ids,
-                            uint32_t* counters, uint32_t* scan_temp, cudaStream_t st);
-// per visible Gaussian in depth order: tile count -> exclusive offsets; I -> counters.
-void launch_tile_offsets(const uint32_t* sorted_ids, const uint32_t* ntiles, int64_t bound_v,
-                         uint32_t* counters, uint32_t* offsets, uint32_t* scan_temp,
-                         cudaStream_t st);
-// emit (tile, id) instances in depth order, at most cap (overflow flagged)
-void launch_emit_instances(const uint32_t* sorted_ids, const uint2* rect, const uint32_t* offsets,
-                           int64_t bound_v, int TX, uint32_t* counters, int64_t cap,
-                           uint32_t* inst_tile, uint32_t* inst_id, cudaStream_t st);
+// Scratch of the binning kernels.  ghist (7 x 256 words) and tickets (4 words) are one
+// contiguous block zeroed at the start of every binning; status holds the look-back words
+// (tagged with a launch epoch, so it never needs clearing after allocation).
+constexpr int kBinZeroWords = 7 * 256 + 4;
+struct BinScratch {
+  uint32_t* ghist;              // [7][256]: 4 depth-key digits, 3 tile-key digits
+  uint32_t* tickets;            // [4] chunk tickets (right after ghist)
+  unsigned long long* status;   // look-back status words
+  uint32_t* counters;           // workspace counters (status word for errors)
+  uint32_t* epoch;              // host-side launch epoch, 1 .. 2^30 - 1
+  uint32_t next_epoch() const {
+    *epoch = (*epoch % 0x3FFFFFFFu) + 1u;
+    return *epoch;
+  }
+};
+// look-back status words needed for sorts of up to max_elems elements
+size_t bin_status_words(int64_t max_elems);
+// Stable sort of all n Gaussians by depth key (4 onesweep passes; values = ids).  Result
+// in (k0, v0); (k1, v1) is the ping-pong buffer.
+void launch_depth_sort(const uint32_t* depth_key, int64_t n, uint32_t* k1, uint32_t* v1,
+                       uint32_t* k0, uint32_t* v0, const BinScratch& s, cudaStream_t st);
+// Emit (tile, id) instances of the depth-sorted Gaussians: tile-count prefix sum into
+// `offsets` (n words), then emission balanced over output slots, at most cap (overflow
+// flagged), with the tile-key digit histograms.
+void launch_emit_instances(const uint32_t* sorted_ids, const uint32_t* ntiles, const uint2* rect,
+                           int64_t n, int TX, int64_t cap, uint32_t* offsets, uint32_t* inst_tile,
+                           uint32_t* inst_id, const BinScratch& s, cudaStream_t st);
+// Stable sort of min(I, bound) instances by tile id (tile_bits <= 24).  Returns 0 if the
+// result is in (k0, v0), 1 if in (k1, v1).
+int launch_tile_sort(int64_t bound, int tile_bits, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                     uint32_t* v1, const BinScratch& s, cudaStream_t st);
 // tile ranges [start, end) from tile-sorted instances
 void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int64_t bound_i,
                         int64_t cap, int n_tiles, uint2* ranges, cudaStream_t st);
-void launch_inst_eff(const uint2* ranges, const uint32_t* n_contrib, int TX, int TY, int W, int H,
-                     uint32_t* counters, cudaStream_t st);
+void launch_inst_eff(const uint32_t* n_contrib, int TX, int TY, int W, int H, uint32_t* counters,
+                     cudaStream_t st);
 
 // gs_raster_fwd.cu
 void launch_raster_fwd(const CamDev& cam, const GaussRec* rec, const void* feats, int feat_dtype,

@@ -53,7 +53,7 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
           const float* __restrict__ quats, const float* __restrict__ opac,
           const float* __restrict__ sh, GaussRec* __restrict__ rec,
           uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ntiles,
-          uint2* __restrict__ rect) {
+          uint2* __restrict__ rect, uint32_t* __restrict__ counters) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ __align__(16) float s_mu[kProjThreads * 3];
   __shared__ __align__(16) float s_sc[kProjThreads * 3];
@@ -67,170 +67,189 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
   stage_rows(sh, row0, rows, K * 3, s_sh);
   __syncthreads();
   const int l = threadIdx.x;
-  if (l >= rows) return;
-  const int64_t i = row0 + l;
+  uint32_t cnt_v = 0, cnt_i = 0;
+  if (l < rows) {
+    const int64_t i = row0 + l;
 
-  const float* R = cam.R;
-  const float mx = s_mu[3 * l], my = s_mu[3 * l + 1], mz = s_mu[3 * l + 2];
-  // p = W mu + t
-  const float x = ((R[0] * mx + R[1] * my) + R[2] * mz) + cam.t[0];
-  const float y = ((R[3] * mx + R[4] * my) + R[5] * mz) + cam.t[1];
-  const float z = ((R[6] * mx + R[7] * my) + R[8] * mz) + cam.t[2];
+    const float* R = cam.R;
+    const float mx = s_mu[3 * l], my = s_mu[3 * l + 1], mz = s_mu[3 * l + 2];
+    // p = W mu + t
+    const float x = ((R[0] * mx + R[1] * my) + R[2] * mz) + cam.t[0];
+    const float y = ((R[3] * mx + R[4] * my) + R[5] * mz) + cam.t[1];
+    const float z = ((R[6] * mx + R[7] * my) + R[8] * mz) + cam.t[2];
 
-  uint32_t nt = 0;
-  uint2 rc = make_uint2(0, 0);
-  GaussRec g;
-  g.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
-  g.r1 = g.r0;
-  g.r2 = g.r0;
-  bool valid = z > cam.near_z;
-  float a = 0.f, b = 0.f, c = 0.f, det = 0.f, u = 0.f, v = 0.f;
-  if (valid) {
-    // unit quaternion (w, x, y, z) -> rotation
-    const float q0 = s_q[4 * l], q1 = s_q[4 * l + 1], q2 = s_q[4 * l + 2], q3 = s_q[4 * l + 3];
-    const float ql = sqrtf(((q0 * q0 + q1 * q1) + q2 * q2) + q3 * q3);
-    const float w = q0 / ql, qx = q1 / ql, qy = q2 / ql, qz = q3 / ql;
-    float Rq[9];
-    Rq[0] = 1.f - 2.f * (qy * qy + qz * qz);
-    Rq[1] = 2.f * (qx * qy - w * qz);
-    Rq[2] = 2.f * (qx * qz + w * qy);
-    Rq[3] = 2.f * (qx * qy + w * qz);
-    Rq[4] = 1.f - 2.f * (qx * qx + qz * qz);
-    Rq[5] = 2.f * (qy * qz - w * qx);
-    Rq[6] = 2.f * (qx * qz - w * qy);
-    Rq[7] = 2.f * (qy * qz + w * qx);
-    Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
-    const float s0 = s_sc[3 * l], s1 = s_sc[3 * l + 1], s2 = s_sc[3 * l + 2];
-    float M[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      M[r * 3 + 0] = Rq[r * 3 + 0] * s0;
-      M[r * 3 + 1] = Rq[r * 3 + 1] * s1;
-      M[r * 3 + 2] = Rq[r * 3 + 2] * s2;
-    }
-    // Sigma = M M^T (upper triangle, mirrored)
-    float Sig[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int s = r; s < 3; ++s) {
-        const float e = (M[r * 3] * M[s * 3] + M[r * 3 + 1] * M[s * 3 + 1]) + M[r * 3 + 2] * M[s * 3 + 2];
-        Sig[r * 3 + s] = e;
-        Sig[s * 3 + r] = e;
-      }
-    // Sc = W Sigma W^T (A = W Sigma full, then upper triangle of A W^T)
-    float A[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
-        A[r * 3 + s] = (R[r * 3] * Sig[s] + R[r * 3 + 1] * Sig[3 + s]) + R[r * 3 + 2] * Sig[6 + s];
-    float Sc[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int s = r; s < 3; ++s) {
-        const float e = (A[r * 3] * R[s * 3] + A[r * 3 + 1] * R[s * 3 + 1]) + A[r * 3 + 2] * R[s * 3 + 2];
-        Sc[r * 3 + s] = e;
-        Sc[s * 3 + r] = e;
-      }
-    // J with the 1.3 x half-FOV guard band
-    const float tanx = (0.5f * (float)cam.W) / cam.fx, tany = (0.5f * (float)cam.H) / cam.fy;
-    const float limx = 1.3f * tanx, limy = 1.3f * tany;
-    const float tx = x / z, ty = y / z;
-    const float txc = fminf(limx, fmaxf(-limx, tx)), tyc = fminf(limy, fmaxf(-limy, ty));
-    const float j00 = cam.fx / z, j02 = -((cam.fx * txc) / z);
-    const float j11 = cam.fy / z, j12 = -((cam.fy * tyc) / z);
-    const float T00 = j00 * Sc[0] + j02 * Sc[2];
-    const float T01 = j00 * Sc[1] + j02 * Sc[5];
-    const float T02 = j00 * Sc[2] + j02 * Sc[8];
-    const float T11 = j11 * Sc[4] + j12 * Sc[5];
-    const float T12 = j11 * Sc[5] + j12 * Sc[8];
-    a = (T00 * j00 + T02 * j02) + 0.3f;
-    b = T01 * j11 + T02 * j12;
-    c = (T11 * j11 + T12 * j12) + 0.3f;
-    det = a * c - b * b;
-    valid = det > 0.f;
+    uint32_t nt = 0;
+    uint2 rc = make_uint2(0, 0);
+    GaussRec g;
+    g.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    g.r1 = g.r0;
+    g.r2 = g.r0;
+    bool valid = z > cam.near_z;
+    float a = 0.f, b = 0.f, c = 0.f, det = 0.f, u = 0.f, v = 0.f;
     if (valid) {
-      const float mid = 0.5f * (a + c);
-      const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
-      const float r = ceilf(3.f * sqrtf(lam));
-      u = cam.fx * tx + cam.cx;
-      v = cam.fy * ty + cam.cy;
-      const int x0 = (int)clamp_tile(floorf((u - r) / 16.f), cam.TX);
-      const int x1 = (int)clamp_tile(floorf((u + r) / 16.f) + 1.f, cam.TX);
-      const int y0 = (int)clamp_tile(floorf((v - r) / 16.f), cam.TY);
-      const int y1 = (int)clamp_tile(floorf((v + r) / 16.f) + 1.f, cam.TY);
-      valid = x1 > x0 && y1 > y0;
+      // unit quaternion (w, x, y, z) -> rotation
+      const float q0 = s_q[4 * l], q1 = s_q[4 * l + 1], q2 = s_q[4 * l + 2], q3 = s_q[4 * l + 3];
+      const float ql = sqrtf(((q0 * q0 + q1 * q1) + q2 * q2) + q3 * q3);
+      const float w = q0 / ql, qx = q1 / ql, qy = q2 / ql, qz = q3 / ql;
+      float Rq[9];
+      Rq[0] = 1.f - 2.f * (qy * qy + qz * qz);
+      Rq[1] = 2.f * (qx * qy - w * qz);
+      Rq[2] = 2.f * (qx * qz + w * qy);
+      Rq[3] = 2.f * (qx * qy + w * qz);
+      Rq[4] = 1.f - 2.f * (qx * qx + qz * qz);
+      Rq[5] = 2.f * (qy * qz - w * qx);
+      Rq[6] = 2.f * (qx * qz - w * qy);
+      Rq[7] = 2.f * (qy * qz + w * qx);
+      Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
+      const float s0 = s_sc[3 * l], s1 = s_sc[3 * l + 1], s2 = s_sc[3 * l + 2];
+      float M[9];
+  #pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        M[r * 3 + 0] = Rq[r * 3 + 0] * s0;
+        M[r * 3 + 1] = Rq[r * 3 + 1] * s1;
+        M[r * 3 + 2] = Rq[r * 3 + 2] * s2;
+      }
+      // Sigma = M M^T (upper triangle, mirrored)
+      float Sig[9];
+  #pragma unroll
+      for (int r = 0; r < 3; ++r)
+  #pragma unroll
+        for (int s = r; s < 3; ++s) {
+          const float e = (M[r * 3] * M[s * 3] + M[r * 3 + 1] * M[s * 3 + 1]) + M[r * 3 + 2] * M[s * 3 + 2];
+          Sig[r * 3 + s] = e;
+          Sig[s * 3 + r] = e;
+        }
+      // Sc = W Sigma W^T (A = W Sigma full, then upper triangle of A W^T)
+      float A[9];
+  #pragma unroll
+      for (int r = 0; r < 3; ++r)
+  #pragma unroll
+        for (int s = 0; s < 3; ++s)
+          A[r * 3 + s] = (R[r * 3] * Sig[s] + R[r * 3 + 1] * Sig[3 + s]) + R[r * 3 + 2] * Sig[6 + s];
+      float Sc[9];
+  #pragma unroll
+      for (int r = 0; r < 3; ++r)
+  #pragma unroll
+        for (int s = r; s < 3; ++s) {
+          const float e = (A[r * 3] * R[s * 3] + A[r * 3 + 1] * R[s * 3 + 1]) + A[r * 3 + 2] * R[s * 3 + 2];
+          Sc[r * 3 + s] = e;
+          Sc[s * 3 + r] = e;
+        }
+      // J with the 1.3 x half-FOV guard band
+      const float tanx = (0.5f * (float)cam.W) / cam.fx, tany = (0.5f * (float)cam.H) / cam.fy;
+      const float limx = 1.3f * tanx, limy = 1.3f * tany;
+      const float tx = x / z, ty = y / z;
+      const float txc = fminf(limx, fmaxf(-limx, tx)), tyc = fminf(limy, fmaxf(-limy, ty));
+      const float j00 = cam.fx / z, j02 = -((cam.fx * txc) / z);
+      const float j11 = cam.fy / z, j12 = -((cam.fy * tyc) / z);
+      const float T00 = j00 * Sc[0] + j02 * Sc[2];
+      const float T01 = j00 * Sc[1] + j02 * Sc[5];
+      const float T02 = j00 * Sc[2] + j02 * Sc[8];
+      const float T11 = j11 * Sc[4] + j12 * Sc[5];
+      const float T12 = j11 * Sc[5] + j12 * Sc[8];
+      a = (T00 * j00 + T02 * j02) + 0.3f;
+      b = T01 * j11 + T02 * j12;
+      c = (T11 * j11 + T12 * j12) + 0.3f;
+      det = a * c - b * b;
+      valid = det > 0.f;
       if (valid) {
-        nt = (uint32_t)((x1 - x0) * (y1 - y0));
-        rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+        const float mid = 0.5f * (a + c);
+        const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+        const float r = ceilf(3.f * sqrtf(lam));
+        u = cam.fx * tx + cam.cx;
+        v = cam.fy * ty + cam.cy;
+        const int x0 = (int)clamp_tile(floorf((u - r) / 16.f), cam.TX);
+        const int x1 = (int)clamp_tile(floorf((u + r) / 16.f) + 1.f, cam.TX);
+        const int y0 = (int)clamp_tile(floorf((v - r) / 16.f), cam.TY);
+        const int y1 = (int)clamp_tile(floorf((v + r) / 16.f) + 1.f, cam.TY);
+        valid = x1 > x0 && y1 > y0;
+        if (valid) {
+          nt = (uint32_t)((x1 - x0) * (y1 - y0));
+          rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+        }
       }
     }
+    if (valid) {
+      // colour: real SH along dir = normalize(mu - camera centre), camera centre = -W^T t
+      float cp[3];
+  #pragma unroll
+      for (int k = 0; k < 3; ++k)
+        cp[k] = -((R[k] * cam.t[0] + R[3 + k] * cam.t[1]) + R[6 + k] * cam.t[2]);
+      const float d0 = mx - cp[0], d1 = my - cp[1], d2 = mz - cp[2];
+      const float dl = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      const float dx = d0 / dl, dy = d1 / dl, dz = d2 / dl;
+      float Y[K];
+      Y[0] = kC0;
+      if (DEG >= 1) {
+        Y[1] = kC1 * dy;
+        Y[2] = kC1 * dz;
+        Y[3] = kC1 * dx;
+      }
+      if (DEG >= 2) {
+        Y[4] = kC2a * dx * dy;
+        Y[5] = kC2a * dy * dz;
+        Y[6] = kC2b * (2.f * dz * dz - dx * dx - dy * dy);
+        Y[7] = kC2a * dx * dz;
+        Y[8] = kC2c * (dx * dx - dy * dy);
+      }
+      if (DEG >= 3) {
+        Y[9] = kC3a * dy * (3.f * dx * dx - dy * dy);
+        Y[10] = kC3b * dx * dy * dz;
+        Y[11] = kC3c * dy * (4.f * dz * dz - dx * dx - dy * dy);
+        Y[12] = kC3d * dz * (2.f * dz * dz - 3.f * dx * dx - 3.f * dy * dy);
+        Y[13] = kC3c * dx * (4.f * dz * dz - dx * dx - dy * dy);
+        Y[14] = kC3e * dz * (dx * dx - dy * dy);
+        Y[15] = kC3a * dx * (dx * dx - 3.f * dy * dy);
+      }
+      const float* shl = s_sh + l * K * 3;
+      float col[3];
+  #pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.f;
+  #pragma unroll
+        for (int k = 0; k < K; ++k) acc += shl[k * 3 + ch] * Y[k];
+        acc += 0.5f;
+        col[ch] = acc > 0.f ? acc : 0.f;
+      }
+      g.r0 = make_float4(u, v, c / det, -b / det);
+      g.r1 = make_float4(a / det, __ldg(opac + i), z, 0.f);
+      g.r2 = make_float4(col[0], col[1], col[2], 0.f);
+    }
+    rec[i] = g;
+    depth_key[i] = valid ? __float_as_uint(z) : 0xFFFFFFFFu;
+    ntiles[i] = nt;
+    rect[i] = rc;
+    cnt_v = valid ? 1u : 0u;
+    cnt_i = nt;
   }
-  if (valid) {
-    // colour: real SH along dir = normalize(mu - camera centre), camera centre = -W^T t
-    float cp[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      cp[k] = -((R[k] * cam.t[0] + R[3 + k] * cam.t[1]) + R[6 + k] * cam.t[2]);
-    const float d0 = mx - cp[0], d1 = my - cp[1], d2 = mz - cp[2];
-    const float dl = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-    const float dx = d0 / dl, dy = d1 / dl, dz = d2 / dl;
-    float Y[K];
-    Y[0] = kC0;
-    if (DEG >= 1) {
-      Y[1] = kC1 * dy;
-      Y[2] = kC1 * dz;
-      Y[3] = kC1 * dx;
-    }
-    if (DEG >= 2) {
-      Y[4] = kC2a * dx * dy;
-      Y[5] = kC2a * dy * dz;
-      Y[6] = kC2b * (2.f * dz * dz - dx * dx - dy * dy);
-      Y[7] = kC2a * dx * dz;
-      Y[8] = kC2c * (dx * dx - dy * dy);
-    }
-    if (DEG >= 3) {
-      Y[9] = kC3a * dy * (3.f * dx * dx - dy * dy);
-      Y[10] = kC3b * dx * dy * dz;
-      Y[11] = kC3c * dy * (4.f * dz * dz - dx * dx - dy * dy);
-      Y[12] = kC3d * dz * (2.f * dz * dz - 3.f * dx * dx - 3.f * dy * dy);
-      Y[13] = kC3c * dx * (4.f * dz * dz - dx * dx - dy * dy);
-      Y[14] = kC3e * dz * (dx * dx - dy * dy);
-      Y[15] = kC3a * dx * (dx * dx - 3.f * dy * dy);
-    }
-    const float* shl = s_sh + l * K * 3;
-    float col[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float acc = 0.f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) acc += shl[k * 3 + ch] * Y[k];
-      acc += 0.5f;
-      col[ch] = acc > 0.f ? acc : 0.f;
-    }
-    g.r0 = make_float4(u, v, c / det, -b / det);
-    g.r1 = make_float4(a / det, __ldg(opac + i), z, 0.f);
-    g.r2 = make_float4(col[0], col[1], col[2], 0.f);
+  // V and I for the workspace counters: warp sums, then one atomic per block
+  __shared__ uint32_t s_cnt[2];
+  if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0u;
+  __syncthreads();
+  cnt_v = __reduce_add_sync(0xffffffffu, cnt_v);
+  cnt_i = __reduce_add_sync(0xffffffffu, cnt_i);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_cnt[0], cnt_v);
+    atomicAdd(&s_cnt[1], cnt_i);
   }
-  rec[i] = g;
-  depth_key[i] = valid ? __float_as_uint(z) : 0xFFFFFFFFu;
-  ntiles[i] = nt;
-  rect[i] = rc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_cnt[0]) atomicAdd(&counters[kCntVisible], s_cnt[0]);
+    if (s_cnt[1]) atomicAdd(&counters[kCntInst], s_cnt[1]);
+  }
 }
 
 }  // namespace
 
 void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32_t* depth_key,
-                    uint32_t* ntiles, uint2* rect, cudaStream_t st) {
+                    uint32_t* ntiles, uint2* rect, uint32_t* counters, cudaStream_t st) {
   if (sc.n <= 0) return;
   const int grid = (int)ceil_div(sc.n, kProjThreads);
   switch (sc.sh_degree) {
-    case 0: k_project<0><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect); break;
-    case 1: k_project<1><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect); break;
-    case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect); break;
-    default: k_project<3><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect); break;
+    case 0: k_project<0><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
+    case 1: k_project<1><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
+    case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
+    default: k_project<3><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
   }
   note_launch();
 }

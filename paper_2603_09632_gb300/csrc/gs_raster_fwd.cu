@@ -96,8 +96,8 @@ k_raster_fwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restric
     bool keep = false;
     uint32_t id = 0;
     GaussRec g;
-    if ((int)threadIdx.x < cnt) {
-      id = inst_id[b0 + threadIdx.x];
+    if ((int)threadIdx.x < cnt) id = inst_id[b0 + threadIdx.x];
+    if ((int)threadIdx.x < cnt && id < (uint32_t)cam.n_gauss) {
       g = rec[id];
       keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
     }

@@ -2,25 +2,34 @@
 //
 // Eq. 1 blends "depth-sorted" Gaussians; with 16x16 tiles each tile needs the Gaussians
 // covering it in (depth, id) order.  Instead of sorting all I (tile, depth) instances by
-// a 64-bit key, the path sorts the V visible Gaussians once by depth (32-bit keys, four
-// 8-bit passes), emits their tile instances in that order, and stable-sorts the I
-// instances by tile id only (ceil(log2 T) bits, one or two passes).  Stability makes the
-// result identical to a stable sort by (tile, depth) of instances emitted in id order.
+// a 64-bit key, the path sorts the N Gaussians once by depth (32-bit keys: culled ones
+// carry 0xFFFFFFFF and sort last), emits the tile instances in that order, and
+// stable-sorts the I instances by tile id only (ceil(log2 T) bits, one or two passes).
+// Stability makes the result identical to a stable sort by (tile, depth) of instances
+// emitted in id order.
 //
-// Radix pass = reduce-then-scan: (1) per 4096-element chunk digit histograms, (2) one
-// device-wide exclusive scan over the digit-major histogram, (3) a stable scatter that
-// ranks elements with warp match/ballot, sorts the chunk locally in shared memory and
-// writes each digit's run contiguously.  No kernel waits on another block.
+// Each radix pass is a single kernel ("onesweep"): a block takes the next 4096-element
+// chunk from a ticket counter, ranks its keys with warp match, publishes per-digit
+// counts, and finds its per-digit output offset by decoupled look-back over the chunks
+// before it (each poll is bounded; a wait that runs out sets an error bit and the block
+// carries on with guarded writes).  Digit histograms of all passes are computed up front
+// (depth keys) or while emitting the instances (tile keys).  The tile-count prefix sum
+// is fused into the emission kernel with the same look-back.
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kChunk = kThreads * kItems;   // 4096 elements per block
+constexpr int kItemsBig = 16;               // elements per thread for large sorts
+constexpr int kItemsSmall = 8;              // ... and below kSmallSort elements
+constexpr int64_t kSmallSort = 1 << 21;
+constexpr int kEmitItems = 8;
+constexpr int kEmitChunk = kThreads * kEmitItems;   // 1024 Gaussians per emission block
 constexpr int kWarps = kThreads / 32;
 constexpr int kRadix = 256;
+constexpr uint32_t kFlagAgg = 1u, kFlagPre = 2u;
+constexpr int kSpinLimit = 1 << 22;
 
 __device__ __forceinline__ int64_t dev_count(const uint32_t* d_n, int64_t bound) {
   return d_n ? min64((int64_t)*d_n, bound) : bound;
@@ -54,137 +63,107 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
   return before + x - v;
 }
 
-// ---------------------------------------------------------------- device-wide scan
-// Each block owns kChunk consecutive elements.
+// Next chunk index from a ticket counter.  Chunks are handed out in launch order, so the
+// chunks before any running block have all started.  The last taker resets the counter
+// for the next launch (every other block has taken its ticket by then).
+__device__ __forceinline__ int acquire_chunk(uint32_t* ticket, int nblocks, uint32_t* s_chunk) {
+  if (threadIdx.x == 0) {
+    const uint32_t c = atomicAdd(ticket, 1u);
+    if (c == (uint32_t)nblocks - 1) atomicExch(ticket, 0u);
+    *s_chunk = c;
+  }
+  __syncthreads();
+  return (int)*s_chunk;
+}
 
-// The kItems consecutive elements [i0, i0 + kItems) of a thread, zero past n; 16-byte
-// loads when the whole run is in range (buffers are 16-byte aligned, i0 is a multiple of 16).
-__device__ __forceinline__ void load_run(const uint32_t* in, int64_t i0, int64_t n, uint32_t* v) {
-  if (i0 + kItems <= n) {
-    const uint4* p = reinterpret_cast<const uint4*>(in + i0);
+// Status word of the look-back: high 32 bits = epoch << 2 | flag, low 32 bits = value.
+// Words of older launches (other epochs) read as "not yet published".
+__device__ __forceinline__ void publish(unsigned long long* p, uint32_t epoch, uint32_t flag,
+                                        uint32_t v) {
+  atomicExch(p, ((unsigned long long)((epoch << 2) | flag) << 32) | v);
+}
+
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__device__ __forceinline__ bool status_ready(unsigned long long w, uint32_t epoch) {
+  const uint32_t hi = (uint32_t)(w >> 32);
+  return (hi >> 2) == epoch && (hi & 3u) != 0u;
+}
+
+// Sum of the published values of the chunks before `chunk` in column `col`, walking back
+// until an inclusive prefix is found.  The words of up to kLB predecessors are requested
+// together, so a walk over many chunks costs a few memory round trips.  Each wait for a
+// word not yet published is bounded.
+constexpr int kLB = 8;
+__device__ uint32_t look_back(const unsigned long long* status, int chunk, int col, int stride,
+                              uint32_t epoch, uint32_t* err) {
+  uint32_t excl = 0;
+  for (int k = chunk - 1; k >= 0; k -= kLB) {
+    unsigned long long w[kLB];
 #pragma unroll
-    for (int k = 0; k < kItems / 4; ++k) {
-      const uint4 q = p[k];
-      v[4 * k] = q.x;
-      v[4 * k + 1] = q.y;
-      v[4 * k + 2] = q.z;
-      v[4 * k + 3] = q.w;
+    for (int j = 0; j < kLB; ++j)
+      w[j] = k - j >= 0 ? ld_status(status + (size_t)(k - j) * stride + col) : 0ull;
+#pragma unroll
+    for (int j = 0; j < kLB; ++j) {
+      if (k - j < 0) break;
+      int spins = 0;
+      while (!status_ready(w[j], epoch)) {
+        if (++spins > kSpinLimit) {
+          atomicOr(err, kErrLookback);
+          return excl;
+        }
+        if (spins > 32) __nanosleep(100);
+        w[j] = ld_status(status + (size_t)(k - j) * stride + col);
+      }
+      excl += (uint32_t)w[j];
+      if ((uint32_t)(w[j] >> 32 & 3u) == kFlagPre) return excl;
     }
-  } else {
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) v[k] = i0 + k < n ? in[i0 + k] : 0u;
   }
+  return excl;
 }
 
+// ---------------------------------------------------------------- radix sort
+
+// Digit histograms of all four 8-bit digits of the depth keys (grid-stride).
 __global__ void __launch_bounds__(kThreads)
-k_scan_reduce(const uint32_t* __restrict__ in, const uint32_t* d_n, int64_t bound,
-              uint32_t* __restrict__ partial) {
-  __shared__ uint32_t s_warp[kWarps];
-  const int64_t n = dev_count(d_n, bound);
-  const int64_t i0 = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kItems;
-  uint32_t v[kItems];
-  load_run(in, i0, n, v);
-  uint32_t sum = 0;
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) sum += v[k];
-  uint32_t total;
-  block_exclusive_scan(sum, s_warp, &total);
-  if (threadIdx.x == 0) partial[blockIdx.x] = total;
-}
-
-// Single block: exclusive scan of nblocks partial sums in place; grand total to *total_out.
-__global__ void __launch_bounds__(kThreads)
-k_scan_partials(uint32_t* __restrict__ partial, int nblocks, uint32_t* total_out) {
-  __shared__ uint32_t s_warp[kWarps];
-  uint32_t carry = 0;
-  for (int b0 = 0; b0 < nblocks; b0 += kThreads) {
-    const int i = b0 + threadIdx.x;
-    const uint32_t v = i < nblocks ? partial[i] : 0;
-    uint32_t tot;
-    const uint32_t ex = block_exclusive_scan(v, s_warp, &tot);
-    if (i < nblocks) partial[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0 && total_out) *total_out = carry;
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_scan_down(const uint32_t* in, uint32_t* out, const uint32_t* d_n, int64_t bound,
-            const uint32_t* __restrict__ partial) {
-  __shared__ uint32_t s_warp[kWarps];
-  const int64_t n = dev_count(d_n, bound);
-  const int64_t base = (int64_t)blockIdx.x * kChunk;
-  if (base >= n) return;
-  const int64_t i0 = base + (int64_t)threadIdx.x * kItems;
-  uint32_t v[kItems];
-  load_run(in, i0, n, v);
-  uint32_t sum = 0;
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) sum += v[k];
-  uint32_t tot;
-  uint32_t run = partial[blockIdx.x] + block_exclusive_scan(sum, s_warp, &tot);
-#pragma unroll
-  for (int k = 0; k < kItems; ++k) {
-    const uint32_t x = v[k];
-    v[k] = run;
-    run += x;
-  }
-  if (i0 + kItems <= n) {
-    uint4* q = reinterpret_cast<uint4*>(out + i0);
-#pragma unroll
-    for (int k = 0; k < kItems / 4; ++k) q[k] = make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < kItems; ++k)
-      if (i0 + k < n) out[i0 + k] = v[k];
-  }
-}
-
-void scan_impl(const uint32_t* in, uint32_t* out, const uint32_t* d_n, int64_t bound,
-               uint32_t* temp, uint32_t* total_out, cudaStream_t st) {
-  if (bound <= 0) {
-    if (total_out) cudaMemsetAsync(total_out, 0, 4, st);
-    return;
-  }
-  const int nb = (int)ceil_div(bound, kChunk);
-  k_scan_reduce<<<nb, kThreads, 0, st>>>(in, d_n, bound, temp);
-  k_scan_partials<<<1, kThreads, 0, st>>>(temp, nb, total_out);
-  k_scan_down<<<nb, kThreads, 0, st>>>(in, out, d_n, bound, temp);
-  note_launch(3);
-}
-
-// ---------------------------------------------------------------- radix sort passes
-
-__global__ void __launch_bounds__(kThreads)
-k_radix_hist(const uint32_t* __restrict__ keys, const uint32_t* d_n, int64_t bound, int shift,
-             int nchunks, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_h[kRadix];
-  s_h[threadIdx.x] = 0;
+k_hist4(const uint32_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t s_h[4 * kRadix];
+  for (int e = threadIdx.x; e < 4 * kRadix; e += kThreads) s_h[e] = 0;
   __syncthreads();
-  const int64_t n = dev_count(d_n, bound);
-  const int64_t base = (int64_t)blockIdx.x * kChunk;
-  for (int k = 0; k < kItems; ++k) {
-    const int64_t i = base + k * kThreads + threadIdx.x;
-    if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & 0xFFu], 1u);
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const uint32_t k = keys[i];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p * kRadix + ((k >> (8 * p)) & 0xFFu)], 1u);
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * nchunks + blockIdx.x] = s_h[threadIdx.x];
+  for (int e = threadIdx.x; e < 4 * kRadix; e += kThreads)
+    if (s_h[e]) atomicAdd(&ghist[e], s_h[e]);
 }
 
-// Stable scatter of one chunk.  Warp w owns elements [w*512, w*512+512) of the chunk, in
-// rounds of 32; within a round lanes with equal digits are ranked with __match_any_sync.
+// One stable LSD pass over 8 bits at `shift`.  Warp w owns elements [w*512, w*512+512) of
+// the chunk in rounds of 32; lanes with equal digits are ranked with __match_any_sync.
+// vin == nullptr means the values are the element indices.
+template <int kItems>
 __global__ void __launch_bounds__(kThreads)
-k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* d_n,
-                int64_t bound, int shift, int nchunks, const uint32_t* __restrict__ hist_scan) {
+k_onesweep(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+           uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* d_n,
+           int64_t bound, int nblocks, int shift, const uint32_t* __restrict__ ghist,
+           unsigned long long* __restrict__ status, uint32_t* ticket, uint32_t epoch,
+           uint32_t* err) {
   __shared__ uint32_t s_wcnt[kWarps][kRadix];     // per-warp digit counts -> offsets
   __shared__ uint32_t s_dstart[kRadix];           // digit start inside the chunk
   __shared__ uint32_t s_gbase[kRadix];            // digit start in the output
   __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_chunk;
+  constexpr int kChunk = kThreads * kItems;
   __shared__ uint32_t s_keys[kChunk];
   __shared__ uint32_t s_vals[kChunk];
+  const int chunk = acquire_chunk(ticket, nblocks, &s_chunk);
   const int64_t n = dev_count(d_n, bound);
-  const int64_t base = (int64_t)blockIdx.x * kChunk;
+  const int64_t base = (int64_t)chunk * kChunk;
   if (base >= n) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = threadIdx.x; d < kWarps * kRadix; d += kThreads) (&s_wcnt[0][0])[d] = 0;
@@ -192,12 +171,17 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
 
   uint32_t key[kItems], val[kItems], rank[kItems];
   const uint32_t lt_mask = (1u << lane) - 1u;
+  // all loads first (in flight together), then the ranking rounds
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    const int64_t i = base + warp * (kItems * 32) + r * 32 + lane;
+    key[r] = i < n ? kin[i] : 0u;
+    val[r] = i < n ? (vin ? vin[i] : (uint32_t)i) : 0u;
+  }
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t i = base + warp * (kItems * 32) + r * 32 + lane;
     const bool valid = i < n;
-    key[r] = valid ? kin[i] : 0u;
-    val[r] = valid ? vin[i] : 0u;
     const uint32_t d = valid ? ((key[r] >> shift) & 0xFFu) : 0x100u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t before = valid ? s_wcnt[warp][d] : 0u;
@@ -207,20 +191,27 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive scan over warps, digit totals, chunk-local digit starts
   {
     const int d = threadIdx.x;
-    uint32_t sum = 0;
+    uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
       const uint32_t c = s_wcnt[w][d];
-      s_wcnt[w][d] = sum;
-      sum += c;
+      s_wcnt[w][d] = cnt;
+      cnt += c;
     }
+    unsigned long long* st = status + (size_t)chunk * kRadix + d;
+    publish(st, epoch, chunk == 0 ? kFlagPre : kFlagAgg, cnt);
     uint32_t tot;
-    const uint32_t start = block_exclusive_scan(sum, s_warp, &tot);
-    s_dstart[d] = start;
-    s_gbase[d] = hist_scan[(int64_t)d * nchunks + blockIdx.x];
+    const uint32_t dstart = block_exclusive_scan(cnt, s_warp, &tot);
+    const uint32_t gpre = block_exclusive_scan(ghist[d], s_warp, &tot);
+    uint32_t excl = 0;
+    if (chunk > 0) {
+      excl = look_back(status, chunk, d, kRadix, epoch, err);
+      publish(st, epoch, kFlagPre, excl + cnt);
+    }
+    s_dstart[d] = dstart;
+    s_gbase[d] = gpre + excl;
   }
   __syncthreads();
 #pragma unroll
@@ -238,67 +229,123 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
   for (int j = threadIdx.x; j < cnt; j += kThreads) {
     const uint32_t k = s_keys[j];
     const uint32_t d = (k >> shift) & 0xFFu;
-    const uint32_t o = s_gbase[d] + (uint32_t)j - s_dstart[d];
-    kout[o] = k;
-    vout[o] = s_vals[j];
-  }
-}
-
-// ---------------------------------------------------------------- binning kernels
-
-__global__ void k_visible_flags(const uint32_t* __restrict__ ntiles, int64_t n,
-                                uint32_t* __restrict__ flags) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) flags[i] = ntiles[i] > 0 ? 1u : 0u;
-}
-
-__global__ void k_compact(const uint32_t* __restrict__ ntiles, const uint32_t* __restrict__ depth_key,
-                          const uint32_t* __restrict__ pos, int64_t n, uint32_t* __restrict__ okeys,
-                          uint32_t* __restrict__ oids) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && ntiles[i] > 0) {
-    const uint32_t p = pos[i];
-    okeys[p] = depth_key[i];
-    oids[p] = (uint32_t)i;
-  }
-}
-
-__global__ void k_gather_counts(const uint32_t* __restrict__ sorted_ids,
-                                const uint32_t* __restrict__ ntiles, const uint32_t* d_v,
-                                int64_t bound, uint32_t* __restrict__ cnt) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < dev_count(d_v, bound)) cnt[r] = ntiles[sorted_ids[r]];
-}
-
-__global__ void k_emit(const uint32_t* __restrict__ sorted_ids, const uint2* __restrict__ rect,
-                       const uint32_t* __restrict__ offsets, const uint32_t* d_v, int64_t bound,
-                       int TX, uint32_t* counters, int64_t cap, uint32_t* __restrict__ inst_tile,
-                       uint32_t* __restrict__ inst_id) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= dev_count(d_v, bound)) return;
-  const uint32_t id = sorted_ids[r];
-  const uint2 rc = rect[id];
-  const int x0 = rc.x & 0xFFFF, y0 = rc.x >> 16, x1 = rc.y & 0xFFFF, y1 = rc.y >> 16;
-  int64_t o = offsets[r];
-  bool overflow = false;
-  for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx, ++o) {
-      if (o < cap) {
-        inst_tile[o] = (uint32_t)(ty * TX + tx);
-        inst_id[o] = id;
-      } else {
-        overflow = true;
-      }
+    const int64_t o = (int64_t)s_gbase[d] + j - s_dstart[d];
+    if (o < n) {               // always true unless a look-back timed out
+      kout[o] = k;
+      vout[o] = s_vals[j];
     }
-  if (overflow) atomicOr(&counters[kCntStatus], kErrInstOverflow);
+  }
+}
+
+// ---------------------------------------------------------------- instance emission
+
+// Exclusive prefix of the tile counts of the depth-sorted Gaussians (decoupled look-back
+// over chunks of kEmitChunk): offsets[r] = first instance slot of sorted Gaussian r.
+__global__ void __launch_bounds__(kThreads)
+k_tile_offsets(const uint32_t* __restrict__ sorted_ids, const uint32_t* __restrict__ ntiles,
+               int64_t n, int nblocks, uint32_t* __restrict__ offsets,
+               unsigned long long* __restrict__ status, uint32_t* ticket, uint32_t epoch,
+               uint32_t* counters) {
+  constexpr int EI = kEmitItems;
+  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_chunk, s_base;
+  const int chunk = acquire_chunk(ticket, nblocks, &s_chunk);
+  const int64_t i0 = (int64_t)chunk * kEmitChunk + threadIdx.x * EI;
+  if ((int64_t)chunk * kEmitChunk >= n) return;
+  uint32_t cnt[EI];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < EI; ++k) {
+    const uint32_t id = i0 + k < n ? sorted_ids[i0 + k] : 0xFFFFFFFFu;
+    cnt[k] = id < (uint32_t)n ? ntiles[id] : 0u;
+    sum += cnt[k];
+  }
+  uint32_t total;
+  uint32_t off = block_exclusive_scan(sum, s_warp, &total);
+  if (threadIdx.x == 0) {
+    unsigned long long* st = status + chunk;
+    publish(st, epoch, chunk == 0 ? kFlagPre : kFlagAgg, total);
+    uint32_t excl = 0;
+    if (chunk > 0) {
+      excl = look_back(status, chunk, 0, 1, epoch, &counters[kCntStatus]);
+      publish(st, epoch, kFlagPre, excl + total);
+    }
+    s_base = excl;
+  }
+  __syncthreads();
+  off += s_base;
+#pragma unroll
+  for (int k = 0; k < EI; ++k) {
+    if (i0 + k < n) offsets[i0 + k] = off;
+    off += cnt[k];
+  }
+}
+
+// Instance emission balanced over output slots: thread t of block b writes slots
+// [b*kEmitChunk + t*kEmitItems, + kEmitItems).  The Gaussian owning a slot is the last r
+// with offsets[r] <= slot (binary search for the first slot, then a forward walk).  Each
+// Gaussian's slots hold its tiles in row-major order.  Also accumulates the three 8-bit
+// digit histograms of the tile ids for the tile sort.  Slots at or beyond min(I, cap)
+// are not written; I above cap is flagged.
+__global__ void __launch_bounds__(kThreads)
+k_emit(const uint32_t* __restrict__ sorted_ids, const uint32_t* __restrict__ offsets,
+       const uint2* __restrict__ rect, int64_t n, int TX, int64_t cap,
+       uint32_t* __restrict__ inst_tile, uint32_t* __restrict__ inst_id,
+       uint32_t* __restrict__ ghist_tile, uint32_t* counters) {
+  __shared__ uint32_t s_h[3 * kRadix];
+  for (int e = threadIdx.x; e < 3 * kRadix; e += kThreads) s_h[e] = 0;
+  __syncthreads();
+  const int64_t I = (int64_t)counters[kCntInst];
+  if (threadIdx.x == 0 && blockIdx.x == 0 && I > cap) atomicOr(&counters[kCntStatus], kErrInstOverflow);
+  const int64_t m = min64(I, cap);
+  const int64_t o0 = (int64_t)blockIdx.x * kEmitChunk + threadIdx.x * kEmitItems;
+  if (o0 < m && n > 0) {
+    // last r with offsets[r] <= o0
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (offsets[mid] <= (uint32_t)o0) lo = mid; else hi = mid - 1;
+    }
+    int64_t r = lo;
+    uint32_t id = sorted_ids[r];
+    uint2 rc = id < (uint32_t)n ? rect[id] : make_uint2(0u, 0u);
+    uint32_t start = offsets[r];
+#pragma unroll 1
+    for (int k = 0; k < kEmitItems; ++k) {
+      const int64_t o = o0 + k;
+      if (o >= m) break;
+      while (r + 1 < n && offsets[r + 1] <= (uint32_t)o) {
+        ++r;
+        id = sorted_ids[r];
+        rc = id < (uint32_t)n ? rect[id] : make_uint2(0u, 0u);
+        start = offsets[r];
+      }
+      const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, w = (rc.y & 0xFFFFu) - x0;
+      if (w == 0u) continue;    // inconsistent inputs only
+      const uint32_t q = (uint32_t)o - start;
+      const uint32_t t = (y0 + q / w) * (uint32_t)TX + x0 + q % w;
+      inst_tile[o] = t;
+      inst_id[o] = id;
+      atomicAdd(&s_h[t & 0xFFu], 1u);
+      atomicAdd(&s_h[kRadix + ((t >> 8) & 0xFFu)], 1u);
+      atomicAdd(&s_h[2 * kRadix + ((t >> 16) & 0xFFu)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 3 * kRadix; e += kThreads)
+    if (s_h[e]) atomicAdd(&ghist_tile[e], s_h[e]);
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ tile, const uint32_t* counters, int64_t bound,
-                         int64_t cap, uint2* __restrict__ ranges) {
+                         int64_t cap, int n_tiles, uint2* __restrict__ ranges) {
   const int64_t n = min64(min64((int64_t)counters[kCntInst], bound), cap);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t t = tile[i];
+  if (t >= (uint32_t)n_tiles) {
+    atomicOr((uint32_t*)&counters[kCntStatus], kErrBadRange);
+    return;
+  }
   if (i == 0 || tile[i - 1] != t) ranges[t].x = (uint32_t)i;
   if (i + 1 == n || tile[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
 }
@@ -320,76 +367,79 @@ k_inst_eff(const uint32_t* __restrict__ n_contrib, int TX, int W, int H, uint32_
   }
 }
 
+int sort_items(int64_t n) { return n >= kSmallSort ? kItemsBig : kItemsSmall; }
+int num_chunks(int64_t n, int items) { return (int)ceil_div(max64(n, 1), (int64_t)kThreads * items); }
+
+// One onesweep pass with the chunk size chosen for n.
+void onesweep(int items, int nb, cudaStream_t st, const uint32_t* kin, const uint32_t* vin,
+              uint32_t* kout, uint32_t* vout, const uint32_t* d_n, int64_t bound, int shift,
+              const uint32_t* ghist, const BinScratch& s, uint32_t* ticket) {
+  if (items == kItemsBig)
+    k_onesweep<kItemsBig><<<nb, kThreads, 0, st>>>(kin, vin, kout, vout, d_n, bound, nb, shift, ghist,
+                                                   s.status, ticket, s.next_epoch(),
+                                                   s.counters + kCntStatus);
+  else
+    k_onesweep<kItemsSmall><<<nb, kThreads, 0, st>>>(kin, vin, kout, vout, d_n, bound, nb, shift, ghist,
+                                                     s.status, ticket, s.next_epoch(),
+                                                     s.counters + kCntStatus);
+  note_launch();
+}
+
 }  // namespace
 
-size_t scan_temp_words(int64_t n) { return (size_t)ceil_div(max64(n, 1), kChunk) + 32; }
-
-void device_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* temp,
-                           cudaStream_t st) {
-  scan_impl(in, out, nullptr, n, temp, nullptr, st);
+// Enough for any n <= max_elems: the smallest chunk (kItemsSmall == kEmitItems) gives the
+// most chunks, each needing kRadix words.
+size_t bin_status_words(int64_t max_elems) {
+  static_assert(kEmitItems == kItemsSmall, "status sizing assumes the smallest chunk");
+  return (size_t)num_chunks(max_elems, kItemsSmall) * kRadix;
 }
 
-size_t radix_hist_words(int64_t bound) {
-  return (size_t)kRadix * (size_t)ceil_div(max64(bound, 1), kChunk);
-}
-
-int radix_sort_pairs(const uint32_t* d_n, int64_t bound, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                     uint32_t* v1, int end_bit, uint32_t* hist, uint32_t* scan_temp,
-                     cudaStream_t st) {
-  if (bound <= 0 || end_bit <= 0) return 0;
-  const int nchunks = (int)ceil_div(bound, kChunk);
-  const int64_t hwords = (int64_t)kRadix * nchunks;
-  int cur = 0;
-  for (int shift = 0; shift < end_bit; shift += 8) {
-    const uint32_t* ki = cur ? k1 : k0;
-    const uint32_t* vi = cur ? v1 : v0;
-    uint32_t* ko = cur ? k0 : k1;
-    uint32_t* vo = cur ? v0 : v1;
-    k_radix_hist<<<nchunks, kThreads, 0, st>>>(ki, d_n, bound, shift, nchunks, hist);
-    scan_impl(hist, hist, nullptr, hwords, scan_temp, nullptr, st);
-    k_radix_scatter<<<nchunks, kThreads, 0, st>>>(ki, vi, ko, vo, d_n, bound, shift, nchunks, hist);
-    note_launch(2);
-    cur ^= 1;
+void launch_depth_sort(const uint32_t* depth_key, int64_t n, uint32_t* k1, uint32_t* v1,
+                       uint32_t* k0, uint32_t* v0, const BinScratch& s, cudaStream_t st) {
+  if (n <= 0) return;
+  const int items = sort_items(n);
+  const int nb = num_chunks(n, items);
+  k_hist4<<<std::min(nb, 4 * 152), kThreads, 0, st>>>(depth_key, n, s.ghist);
+  note_launch();
+  // pass 0 reads the projection's keys and generates the ids; passes alternate 1 <-> 0
+  const uint32_t* ki = depth_key;
+  const uint32_t* vi = nullptr;
+  uint32_t* ko[4] = {k1, k0, k1, k0};
+  uint32_t* vo[4] = {v1, v0, v1, v0};
+  for (int p = 0; p < 4; ++p) {
+    onesweep(items, nb, st, ki, vi, ko[p], vo[p], nullptr, n, 8 * p, s.ghist + p * kRadix, s,
+             s.tickets);
+    ki = ko[p];
+    vi = vo[p];
   }
-  return cur;
 }
 
-void launch_compact_visible(const uint32_t* ntiles, const uint32_t* depth_key, int64_t n,
-                            uint32_t* flags_scan, uint32_t* out_keys, uint32_t* out_ids,
-                            uint32_t* counters, uint32_t* scan_temp, cudaStream_t st) {
-  if (n <= 0) {
-    cudaMemsetAsync(counters + kCntVisible, 0, 4, st);
-    return;
-  }
-  const int g = (int)ceil_div(n, 256);
-  k_visible_flags<<<g, 256, 0, st>>>(ntiles, n, flags_scan);
-  scan_impl(flags_scan, flags_scan, nullptr, n, scan_temp, counters + kCntVisible, st);
-  k_compact<<<g, 256, 0, st>>>(ntiles, depth_key, flags_scan, n, out_keys, out_ids);
+void launch_emit_instances(const uint32_t* sorted_ids, const uint32_t* ntiles, const uint2* rect,
+                           int64_t n, int TX, int64_t cap, uint32_t* offsets, uint32_t* inst_tile,
+                           uint32_t* inst_id, const BinScratch& s, cudaStream_t st) {
+  if (n <= 0) return;
+  const int nb = num_chunks(n, kEmitItems);
+  k_tile_offsets<<<nb, kThreads, 0, st>>>(sorted_ids, ntiles, n, nb, offsets, s.status,
+                                          s.tickets + 1, s.next_epoch(), s.counters);
+  const int64_t slots = cap > 0 ? cap : 1;
+  k_emit<<<num_chunks(slots, kEmitItems), kThreads, 0, st>>>(sorted_ids, offsets, rect, n, TX, cap,
+                                                             inst_tile, inst_id, s.ghist + 4 * kRadix,
+                                                             s.counters);
   note_launch(2);
 }
 
-void launch_tile_offsets(const uint32_t* sorted_ids, const uint32_t* ntiles, int64_t bound_v,
-                         uint32_t* counters, uint32_t* offsets, uint32_t* scan_temp,
-                         cudaStream_t st) {
-  if (bound_v <= 0) {
-    cudaMemsetAsync(counters + kCntInst, 0, 4, st);
-    return;
+int launch_tile_sort(int64_t bound, int tile_bits, uint32_t* k0, uint32_t* v0, uint32_t* k1,
+                     uint32_t* v1, const BinScratch& s, cudaStream_t st) {
+  if (bound <= 0 || tile_bits <= 0) return 0;
+  const int items = sort_items(bound);
+  const int nb = num_chunks(bound, items);
+  int cur = 0;
+  for (int p = 0; p * 8 < tile_bits && p < 3; ++p) {
+    onesweep(items, nb, st, cur ? k1 : k0, cur ? v1 : v0, cur ? k0 : k1, cur ? v0 : v1,
+             s.counters + kCntInst, bound, 8 * p, s.ghist + (4 + p) * kRadix, s, s.tickets + 2);
+    cur ^= 1;
   }
-  k_gather_counts<<<(int)ceil_div(bound_v, 256), 256, 0, st>>>(sorted_ids, ntiles,
-                                                               counters + kCntVisible, bound_v,
-                                                               offsets);
-  note_launch();
-  scan_impl(offsets, offsets, counters + kCntVisible, bound_v, scan_temp, counters + kCntInst, st);
-}
-
-void launch_emit_instances(const uint32_t* sorted_ids, const uint2* rect, const uint32_t* offsets,
-                           int64_t bound_v, int TX, uint32_t* counters, int64_t cap,
-                           uint32_t* inst_tile, uint32_t* inst_id, cudaStream_t st) {
-  if (bound_v <= 0) return;
-  k_emit<<<(int)ceil_div(bound_v, 256), 256, 0, st>>>(sorted_ids, rect, offsets,
-                                                      counters + kCntVisible, bound_v, TX,
-                                                      counters, cap, inst_tile, inst_id);
-  note_launch();
+  return cur;
 }
 
 void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int64_t bound_i,
@@ -397,13 +447,13 @@ void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, st);
   const int64_t b = min64(bound_i, cap);
   if (b <= 0) return;
-  k_ranges<<<(int)ceil_div(b, 256), 256, 0, st>>>(inst_tile, counters, bound_i, cap, ranges);
+  k_ranges<<<(int)ceil_div(b, 256), 256, 0, st>>>(inst_tile, counters, bound_i, cap, n_tiles,
+                                                   ranges);
   note_launch();
 }
 
-void launch_inst_eff(const uint2* ranges, const uint32_t* n_contrib, int TX, int TY, int W, int H,
-                     uint32_t* counters, cudaStream_t st) {
-  (void)ranges;
+void launch_inst_eff(const uint32_t* n_contrib, int TX, int TY, int W, int H, uint32_t* counters,
+                     cudaStream_t st) {
   cudaMemsetAsync(counters + kCntInstEff, 0, 4, st);
   if (TX * TY > 0) {
     k_inst_eff<<<TX * TY, kThreads, 0, st>>>(n_contrib, TX, W, H, counters);
