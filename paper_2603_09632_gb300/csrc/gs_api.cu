@@ -54,6 +54,8 @@ struct gs_workspace {
   DevBuf<uint32_t> inst_tile, inst_id, inst_tile2, inst_id2;
   // per tile / pixel
   DevBuf<uint2> ranges;
+  DevBuf<uint32_t> tile_order, queue;   // heavy-first tile order; persistent-kernel queue heads
+  bool ordered = false;
   DevBuf<float> T_final;
   DevBuf<uint32_t> n_contrib;
   // scratch
@@ -200,6 +202,7 @@ cudaError_t ensure_pix(gs_workspace* ws, int64_t npix, int64_t ntiles) {
   if ((e = ws->T_final.ensure((size_t)std::max<int64_t>(npix, 1))) ||
       (e = ws->n_contrib.ensure((size_t)std::max<int64_t>(npix, 1))))
     return e;
+  if ((e = ws->tile_order.ensure((size_t)std::max<int64_t>(ntiles, 1)))) return e;
   return ws->ranges.ensure((size_t)std::max<int64_t>(ntiles, 1));
 }
 
@@ -232,6 +235,7 @@ gs_status gs_workspace_create(gs_workspace** out, int device) {
   ws->device = device;
   DeviceGuard g(device);
   if (ws->counters.ensure(kCntNum) != cudaSuccess || ws->bin_zero.ensure(kBinZeroWords) != cudaSuccess ||
+      ws->queue.ensure(4) != cudaSuccess ||
       cudaMemset(ws->bin_zero.p, 0, kBinZeroWords * sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(ws->counters.p, 0, kCntNum * sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ws->h_counters, kCntNum * sizeof(uint32_t)) != cudaSuccess) {
@@ -252,6 +256,7 @@ void gs_workspace_destroy(gs_workspace* ws) {
     ws->rect.release(); ws->g2d.release(); ws->pose_partials.release();
     ws->inst_tile.release(); ws->inst_id.release(); ws->inst_tile2.release(); ws->inst_id2.release();
     ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
+    ws->tile_order.release(); ws->queue.release();
     ws->bin_zero.release(); ws->bin_status.release(); ws->counters.release();
     if (ws->h_counters) cudaFreeHost(ws->h_counters);
     if (ws->ev_created)
@@ -359,6 +364,7 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   ws->id_sorted = w2 ? ws->inst_id2.p : ws->inst_id.p;
   ws->sorted_ids = sorted_ids;
   launch_tile_ranges(ws->tile_sorted, cnt, min64(bound, cap), cap, ntl, ws->ranges.p, st);
+  ws->ordered = launch_tile_order(ws->ranges.p, ntl, ws->tile_order.p, st);
   GS_TRY(cudaGetLastError());
   ws->inst_bound = std::min(bound, cap);
   ws->stage = 2;
@@ -378,7 +384,9 @@ gs_status gs_render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
   StageTimer tm(ws, GS_TIMER_FWD, st);
-  launch_raster_fwd(cd, ws->rec.p, scene->feats, scene->feat_dtype, scene->n_feat, ws->ranges.p,
+  GS_TRY(cudaMemsetAsync(ws->queue.p, 0, sizeof(uint32_t), st));
+  const TileQueue tq{ws->queue.p, ws->ordered ? ws->tile_order.p : nullptr, cd.TX * cd.TY};
+  launch_raster_fwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, scene->n_feat, ws->ranges.p,
                     ws->id_sorted, rgb, depth, alpha, scene->n_feat > 0 ? feat : nullptr,
                     ws->T_final.p, ws->n_contrib.p, st);
   GS_TRY(cudaGetLastError());
@@ -408,7 +416,9 @@ gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
     if (n > 0) GS_TRY(cudaMemsetAsync(ws->g2d.p, 0, sizeof(float) * kG2D * (size_t)n, st));
     if (g_feats && n > 0 && D > 0)
       GS_TRY(cudaMemsetAsync(g_feats, 0, sizeof(float) * (size_t)n * D, st));
-    launch_raster_bwd(cd, ws->rec.p, scene->feats, scene->feat_dtype, D, ws->ranges.p,
+    GS_TRY(cudaMemsetAsync(ws->queue.p + 1, 0, sizeof(uint32_t), st));
+    const TileQueue tq{ws->queue.p + 1, ws->ordered ? ws->tile_order.p : nullptr, cd.TX * cd.TY};
+    launch_raster_bwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, D, ws->ranges.p,
                       ws->id_sorted, ws->T_final.p, ws->n_contrib.p, g_rgb, g_depth, g_alpha,
                       D > 0 ? g_feat : nullptr, ws->g2d.p, D > 0 ? g_feats : nullptr, st);
     GS_TRY(cudaGetLastError());

@@ -90,17 +90,45 @@ void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int
                         int64_t cap, int n_tiles, uint2* ranges, cudaStream_t st);
 void launch_inst_eff(const uint32_t* n_contrib, int TX, int TY, int W, int H, uint32_t* counters,
                      cudaStream_t st);
+// Heavy-first processing order of the tiles (longest lists first).  Returns false (and
+// launches nothing) above kMaxOrderedTiles tiles: the raster kernels then take tiles in
+// index order.
+constexpr int kMaxOrderedTiles = 1 << 18;
+bool launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t st);
+
+// Persistent raster scheduling: a CTA takes the next tile index from *queue (zeroed
+// before each launch) and maps it through `order` (identity when null).
+struct TileQueue {
+  uint32_t* head;
+  const uint32_t* order;
+  int n_tiles;
+};
+
+// Grid of a persistent kernel: as many CTAs as fit on the device at once (never more than
+// n_items).  Sets the dynamic shared-memory attribute when above the 48 KB default.
+template <class Kernel>
+inline int persistent_grid(Kernel kern, int threads, size_t smem, int n_items) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  const int g = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  return n_items < g ? (n_items > 0 ? n_items : 1) : g;
+}
 
 // gs_raster_fwd.cu
-void launch_raster_fwd(const CamDev& cam, const GaussRec* rec, const void* feats, int feat_dtype,
-                       int D, const uint2* ranges, const uint32_t* inst_id, float* rgb,
-                       float* depth, float* alpha, float* feat, float* T_final,
-                       uint32_t* n_contrib, cudaStream_t st);
+void launch_raster_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
+                       const void* feats, int feat_dtype, int D, const uint2* ranges,
+                       const uint32_t* inst_id, float* rgb, float* depth, float* alpha, float* feat,
+                       float* T_final, uint32_t* n_contrib, cudaStream_t st);
 
 // gs_raster_bwd.cu
 // Accumulators per Gaussian: g2d[12*i + k], k = u, v, A, B, C, o, r, g, b, z
 constexpr int kG2D = 12;
-void launch_raster_bwd(const CamDev& cam, const GaussRec* rec, const void* feats, int feat_dtype,
+void launch_raster_bwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
+                       const void* feats, int feat_dtype,
                        int D, const uint2* ranges, const uint32_t* inst_id, const float* T_final,
                        const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
                        const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,

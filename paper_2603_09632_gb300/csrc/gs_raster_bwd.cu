@@ -122,7 +122,8 @@ __device__ __forceinline__ void red_add4(float* dst, float a, float b, float c, 
 
 template <int DP, bool BF16>
 __global__ void __launch_bounds__(kT, 2)
-k_raster_bwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restrict__ feats, int D,
+k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
+             const void* __restrict__ feats, int D,
              const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_id,
              const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
              const float* __restrict__ g_rgb, const float* __restrict__ g_depth,
@@ -145,288 +146,295 @@ k_raster_bwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restric
   float* s_outF = s_fb + 2 * B * DP;          // [B][DP]
 
   const int t = threadIdx.x;
-  const int tile = blockIdx.x;
-  const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
-  const int px = tx0 + (t & 15), py = ty0 + (t >> 4);
-  const bool inside = px < cam.W && py < cam.H;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-  const int64_t HW = (int64_t)cam.W * cam.H;
-  const int64_t p = (int64_t)py * cam.W + px;
-  const uint2 rg = ranges[tile];
-  const int start = (int)rg.x;
-
-  // upstream gradients of this pixel
-  float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, Tf = 1.f;
-  int nc = 0;
-  float gF[DP > 0 ? DP : 1];
-#pragma unroll
-  for (int c = 0; c < (DP > 0 ? DP : 1); ++c) gF[c] = 0.f;
-  if (inside) {
-    if (g_rgb) {
-      gC0 = g_rgb[p];
-      gC1 = g_rgb[HW + p];
-      gC2 = g_rgb[2 * HW + p];
-    }
-    if (g_depth) gD = g_depth[p];
-    if (g_alpha) gA = g_alpha[p];
-    Tf = T_final[p];
-    nc = (int)n_contrib[p];
-    if constexpr (DP > 0) {
-#pragma unroll
-      for (int c = 0; c < DP; ++c) gF[c] = c < D ? g_feat[c * HW + p] : 0.f;
-    }
-  }
-  if constexpr (DP > 0) {
-#pragma unroll
-    for (int c = 0; c < DP; c += 4)
-      *reinterpret_cast<float4*>(s_E + t * Cfg::ES + c) = make_float4(gF[c], gF[c + 1], gF[c + 2], gF[c + 3]);
-    for (int e = t; e < B * DP; e += kT) s_outF[e] = 0.f;
-  }
-  s_E4[t] = make_float4(gC0, gC1, gC2, gD);
-  if (t == 0) s_maxn = 0;
-  __syncthreads();
-  if (nc > 0) atomicMax(&s_maxn, (uint32_t)nc);
-  __syncthreads();
-  const int maxn = (int)s_maxn;
-  if (rg.x + (uint32_t)maxn > rg.y) return;   // cannot happen for consistent inputs
-
-  float T = Tf, s_run = 0.f;
-  const float gAT = gA * Tf;
-
-  for (int c1 = maxn; c1 > 0; c1 -= kT) {
-    const int c0 = max(0, c1 - kT);
-    // ---- gather the chunk [c0, c1) of the list, drop entries the tile cannot blend
-    __syncthreads();                          // previous chunk fully consumed
-    bool keep = false;
-    uint32_t id = 0;
-    GaussRec g;
-    if (t < c1 - c0) id = inst_id[start + c0 + t];
-    if (t < c1 - c0 && id < (uint32_t)cam.n_gauss) {
-      g = rec[id];
-      keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
-    }
-    int nk;
-    const int pos = block_compact_index(keep, s_wc, &nk);
-    if (keep) {
-      s_r0[pos] = g.r0;
-      s_r1[pos] = g.r1;
-      s_r2[pos] = g.r2;
-      s_id[pos] = id;
-      s_orig[pos] = c0 + t;
+  __shared__ int s_tile;
+  // persistent CTA: tiles from the queue, heaviest first
+  for (;;) {
+    if (t == 0) {
+      const uint32_t q = atomicAdd(tq.head, 1u);
+      s_tile = q < (uint32_t)tq.n_tiles ? (int)(tq.order ? tq.order[q] : q) : -1;
     }
     __syncthreads();
-    FeatBatch<DP, BF16, B> fb;
-    if constexpr (DP > 0) {
-      fb.fetch(feats, D, s_id, max(0, nk - B), min(B, nk));
-      fb.store(D, s_fb);
-      __syncthreads();
+    const int tile = s_tile;
+    if (tile < 0) break;
+    const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
+    const int px = tx0 + (t & 15), py = ty0 + (t >> 4);
+    const bool inside = px < cam.W && py < cam.H;
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int64_t HW = (int64_t)cam.W * cam.H;
+    const int64_t p = (int64_t)py * cam.W + px;
+    const uint2 rg = ranges[tile];
+    const int start = (int)rg.x;
+
+    // upstream gradients of this pixel
+    float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, Tf = 1.f;
+    int nc = 0;
+    float gF[DP > 0 ? DP : 1];
+  #pragma unroll
+    for (int c = 0; c < (DP > 0 ? DP : 1); ++c) gF[c] = 0.f;
+    if (inside) {
+      if (g_rgb) {
+        gC0 = g_rgb[p];
+        gC1 = g_rgb[HW + p];
+        gC2 = g_rgb[2 * HW + p];
+      }
+      if (g_depth) gD = g_depth[p];
+      if (g_alpha) gA = g_alpha[p];
+      Tf = T_final[p];
+      nc = (int)n_contrib[p];
+      if constexpr (DP > 0) {
+  #pragma unroll
+        for (int c = 0; c < DP; ++c) gF[c] = c < D ? g_feat[c * HW + p] : 0.f;
+      }
     }
+    if constexpr (DP > 0) {
+  #pragma unroll
+      for (int c = 0; c < DP; c += 4)
+        *reinterpret_cast<float4*>(s_E + t * Cfg::ES + c) = make_float4(gF[c], gF[c + 1], gF[c + 2], gF[c + 3]);
+      for (int e = t; e < B * DP; e += kT) s_outF[e] = 0.f;
+    }
+    s_E4[t] = make_float4(gC0, gC1, gC2, gD);
+    if (t == 0) s_maxn = 0;
+    __syncthreads();
+    if (nc > 0) atomicMax(&s_maxn, (uint32_t)nc);
+    __syncthreads();
+    const int maxn = (int)s_maxn;
+    if (rg.x + (uint32_t)maxn <= rg.y) {          // always, for consistent inputs
 
-    // ---- batches of the compacted chunk, last entries first
-    for (int jb1 = nk, bi = 0; jb1 > 0; jb1 -= B, ++bi) {
-      const int jb0 = max(0, jb1 - B), bc = jb1 - jb0;
-      const float* s_f = s_fb + (bi & 1) * B * DP;
+    float T = Tf, s_run = 0.f;
+    const float gAT = gA * Tf;
 
-      // phase 1: per pixel, reverse over the batch
-      for (int j = B - 1; j >= 0; --j) {
-        float w = 0.f, gs = 0.f, go = 0.f;
-        if (j < bc && s_orig[jb0 + j] < nc) {
-          const float4 r0 = s_r0[jb0 + j];
-          const float4 r1 = s_r1[jb0 + j];
-          const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-          if (sigma >= 0.f) {
-            const float G = blend_gauss(sigma);
-            const float oG = __fmul_rn(r1.y, G);
-            const float a = fminf(kAlphaMax, oG);
-            if (a >= kAlphaMin) {
-              const float inv = __fdividef(1.f, 1.f - a);
-              T = T * inv;                        // T_i
-              w = a * T;
-              const float4 r2 = s_r2[jb0 + j];
-              float dot = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r1.z;
-              if constexpr (DP > 0) {
-                const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
-#pragma unroll
-                for (int q = 0; q < DP / 4; ++q) {
-                  const float4 f = f4[q];
-                  dot = fmaf(gF[4 * q], f.x, dot);
-                  dot = fmaf(gF[4 * q + 1], f.y, dot);
-                  dot = fmaf(gF[4 * q + 2], f.z, dot);
-                  dot = fmaf(gF[4 * q + 3], f.w, dot);
+    for (int c1 = maxn; c1 > 0; c1 -= kT) {
+      const int c0 = max(0, c1 - kT);
+      // ---- gather the chunk [c0, c1) of the list, drop entries the tile cannot blend
+      __syncthreads();                          // previous chunk fully consumed
+      bool keep = false;
+      uint32_t id = 0;
+      GaussRec g;
+      if (t < c1 - c0) id = inst_id[start + c0 + t];
+      if (t < c1 - c0 && id < (uint32_t)cam.n_gauss) {
+        g = rec[id];
+        keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
+      }
+      int nk;
+      const int pos = block_compact_index(keep, s_wc, &nk);
+      if (keep) {
+        s_r0[pos] = g.r0;
+        s_r1[pos] = g.r1;
+        s_r2[pos] = g.r2;
+        s_id[pos] = id;
+        s_orig[pos] = c0 + t;
+      }
+      __syncthreads();
+      FeatBatch<DP, BF16, B> fb;
+      if constexpr (DP > 0) {
+        fb.fetch(feats, D, s_id, max(0, nk - B), min(B, nk));
+        fb.store(D, s_fb);
+        __syncthreads();
+      }
+
+      // ---- batches of the compacted chunk, last entries first
+      for (int jb1 = nk, bi = 0; jb1 > 0; jb1 -= B, ++bi) {
+        const int jb0 = max(0, jb1 - B), bc = jb1 - jb0;
+        const float* s_f = s_fb + (bi & 1) * B * DP;
+
+        // phase 1: per pixel, reverse over the batch
+        for (int j = B - 1; j >= 0; --j) {
+          float w = 0.f, gs = 0.f, go = 0.f;
+          if (j < bc && s_orig[jb0 + j] < nc) {
+            const float4 r0 = s_r0[jb0 + j];
+            const float4 r1 = s_r1[jb0 + j];
+            const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+            if (sigma >= 0.f) {
+              const float G = blend_gauss(sigma);
+              const float oG = __fmul_rn(r1.y, G);
+              const float a = fminf(kAlphaMax, oG);
+              if (a >= kAlphaMin) {
+                const float inv = __fdividef(1.f, 1.f - a);
+                T = T * inv;                        // T_i
+                w = a * T;
+                const float4 r2 = s_r2[jb0 + j];
+                float dot = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r1.z;
+                if constexpr (DP > 0) {
+                  const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
+  #pragma unroll
+                  for (int q = 0; q < DP / 4; ++q) {
+                    const float4 f = f4[q];
+                    dot = fmaf(gF[4 * q], f.x, dot);
+                    dot = fmaf(gF[4 * q + 1], f.y, dot);
+                    dot = fmaf(gF[4 * q + 2], f.z, dot);
+                    dot = fmaf(gF[4 * q + 3], f.w, dot);
+                  }
+                }
+                const float galpha = T * (dot - s_run) + gAT * inv;
+                s_run = a * dot + (1.f - a) * s_run;
+                if (oG <= kAlphaMax) {
+                  go = galpha * G;
+                  gs = -galpha * a;
                 }
               }
-              const float galpha = T * (dot - s_run) + gAT * inv;
-              s_run = a * dot + (1.f - a) * s_run;
-              if (oG <= kAlphaMax) {
-                go = galpha * G;
-                gs = -galpha * a;
-              }
             }
           }
+          s_W[j * kWS + t] = w;
+          s_GS[j * kWS + t] = gs;
+          s_GO[j * kWS + t] = go;
         }
-        s_W[j * kWS + t] = w;
-        s_GS[j * kWS + t] = gs;
-        s_GO[j * kWS + t] = go;
-      }
-      __syncthreads();
+        __syncthreads();
 
-      // next batch's features: fetch now, store after phase 2
-      const bool more = jb0 > 0;
-      if constexpr (DP > 0) {
-        if (more) fb.fetch(feats, D, s_id, max(0, jb0 - B), min(B, jb0));
-      }
+        // next batch's features: fetch now, store after phase 2
+        const bool more = jb0 > 0;
+        if constexpr (DP > 0) {
+          if (more) fb.fetch(feats, D, s_id, max(0, jb0 - B), min(B, jb0));
+        }
 
-      // phase 2a: feature gradients, out[j][c] = sum_p W[j][p] g_F[p][c]
-      if constexpr (DP > 0) {
-        if (g_feats) {
-          const int cb = t % Cfg::CB;
-          const int jb = (t / Cfg::CB) % Cfg::JB;
-          const int part = t / Cfg::TASKS;
-          constexpr int PP = kT / Cfg::S;     // pixels per part
-          float acc[4][4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-          const int p0 = part * PP;
-#pragma unroll 2
-          for (int q = p0; q < p0 + PP; q += 4) {
-            float4 wv[4], ev[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) wv[a] = *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) ev[b] = *reinterpret_cast<const float4*>(s_E + (q + b) * Cfg::ES + 4 * cb);
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-              const float wa[4] = {wv[a].x, wv[a].y, wv[a].z, wv[a].w};
-#pragma unroll
+        // phase 2a: feature gradients, out[j][c] = sum_p W[j][p] g_F[p][c]
+        if constexpr (DP > 0) {
+          if (g_feats) {
+            const int cb = t % Cfg::CB;
+            const int jb = (t / Cfg::CB) % Cfg::JB;
+            const int part = t / Cfg::TASKS;
+            constexpr int PP = kT / Cfg::S;     // pixels per part
+            float acc[4][4];
+  #pragma unroll
+            for (int a = 0; a < 4; ++a)
+  #pragma unroll
+              for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+            const int p0 = part * PP;
+  #pragma unroll 2
+            for (int q = p0; q < p0 + PP; q += 4) {
+              float4 wv[4], ev[4];
+  #pragma unroll
+              for (int a = 0; a < 4; ++a) wv[a] = *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q);
+  #pragma unroll
+              for (int b = 0; b < 4; ++b) ev[b] = *reinterpret_cast<const float4*>(s_E + (q + b) * Cfg::ES + 4 * cb);
+  #pragma unroll
+              for (int a = 0; a < 4; ++a) {
+                const float wa[4] = {wv[a].x, wv[a].y, wv[a].z, wv[a].w};
+  #pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                  acc[a][0] = fmaf(wa[b], ev[b].x, acc[a][0]);
+                  acc[a][1] = fmaf(wa[b], ev[b].y, acc[a][1]);
+                  acc[a][2] = fmaf(wa[b], ev[b].z, acc[a][2]);
+                  acc[a][3] = fmaf(wa[b], ev[b].w, acc[a][3]);
+                }
+              }
+            }
+  #pragma unroll
+            for (int a = 0; a < 4; ++a)
+  #pragma unroll
               for (int b = 0; b < 4; ++b) {
-                acc[a][0] = fmaf(wa[b], ev[b].x, acc[a][0]);
-                acc[a][1] = fmaf(wa[b], ev[b].y, acc[a][1]);
-                acc[a][2] = fmaf(wa[b], ev[b].z, acc[a][2]);
-                acc[a][3] = fmaf(wa[b], ev[b].w, acc[a][3]);
+                if (Cfg::S > 1)
+                  atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
+                else
+                  s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
               }
-            }
           }
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              if (Cfg::S > 1)
-                atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
-              else
-                s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
-            }
         }
-      }
 
-      // phase 2b: per Gaussian sums over pixels (G threads per Gaussian, consecutive lanes)
-      {
-        constexpr int G = Cfg::G;
-        const int j = t / G, pg = t % G;
-        float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
-        float so = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sz = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < kT / G; ++k) {
-          const int q = pg + k * G;
-          const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
-          const float4 e = s_E4[q];
-          const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;
-          m1 += gs;
-          mx = fmaf(gs, x, mx);
-          my = fmaf(gs, y, my);
-          mxx = fmaf(gs * x, x, mxx);
-          mxy = fmaf(gs * x, y, mxy);
-          myy = fmaf(gs * y, y, myy);
-          so += go;
-          sr = fmaf(w, e.x, sr);
-          sg = fmaf(w, e.y, sg);
-          sb = fmaf(w, e.z, sb);
-          sz = fmaf(w, e.w, sz);
+        // phase 2b: per Gaussian sums over pixels (G threads per Gaussian, consecutive lanes)
+        {
+          constexpr int G = Cfg::G;
+          const int j = t / G, pg = t % G;
+          float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+          float so = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sz = 0.f;
+  #pragma unroll 4
+          for (int k = 0; k < kT / G; ++k) {
+            const int q = pg + k * G;
+            const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
+            const float4 e = s_E4[q];
+            const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;
+            m1 += gs;
+            mx = fmaf(gs, x, mx);
+            my = fmaf(gs, y, my);
+            mxx = fmaf(gs * x, x, mxx);
+            mxy = fmaf(gs * x, y, mxy);
+            myy = fmaf(gs * y, y, myy);
+            so += go;
+            sr = fmaf(w, e.x, sr);
+            sg = fmaf(w, e.y, sg);
+            sb = fmaf(w, e.z, sb);
+            sz = fmaf(w, e.w, sz);
+          }
+  #pragma unroll
+          for (int o = G / 2; o > 0; o >>= 1) {
+            m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+            mx += __shfl_xor_sync(0xffffffffu, mx, o);
+            my += __shfl_xor_sync(0xffffffffu, my, o);
+            mxx += __shfl_xor_sync(0xffffffffu, mxx, o);
+            mxy += __shfl_xor_sync(0xffffffffu, mxy, o);
+            myy += __shfl_xor_sync(0xffffffffu, myy, o);
+            so += __shfl_xor_sync(0xffffffffu, so, o);
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            sg += __shfl_xor_sync(0xffffffffu, sg, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+          }
+          if (pg == 0 && j < bc) {
+            const float4 r0 = s_r0[jb0 + j];
+            const float4 r1 = s_r1[jb0 + j];
+            // moments are about the tile centre: pixel offset dx = x - uc with uc = u - centre
+            const float uc = r0.x - ((float)tx0 + 8.f), vc = r0.y - ((float)ty0 + 8.f);
+            const float A = r0.z, Bq = r0.w, C = r1.x;
+            const float sdx = mx - uc * m1, sdy = my - vc * m1;            // sum gs dx, sum gs dy
+            const float sdxx = mxx - 2.f * uc * mx + uc * uc * m1;         // sum gs dx^2
+            const float sdyy = myy - 2.f * vc * my + vc * vc * m1;
+            const float sdxy = mxy - uc * my - vc * mx + uc * vc * m1;
+            const float gAq = 0.5f * sdxx, gBq = sdxy, gCq = 0.5f * sdyy;
+            const float gu = -(A * sdx + Bq * sdy), gv = -(C * sdy + Bq * sdx);
+            float* dst = g2d + (int64_t)s_id[jb0 + j] * kG2D;
+            red_add4(dst, gu, gv, gAq, gBq);
+            red_add4(dst + 4, gCq, so, sr, sg);
+            red_add4(dst + 8, sb, sz, 0.f, 0.f);
+          }
         }
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-          m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-          mx += __shfl_xor_sync(0xffffffffu, mx, o);
-          my += __shfl_xor_sync(0xffffffffu, my, o);
-          mxx += __shfl_xor_sync(0xffffffffu, mxx, o);
-          mxy += __shfl_xor_sync(0xffffffffu, mxy, o);
-          myy += __shfl_xor_sync(0xffffffffu, myy, o);
-          so += __shfl_xor_sync(0xffffffffu, so, o);
-          sr += __shfl_xor_sync(0xffffffffu, sr, o);
-          sg += __shfl_xor_sync(0xffffffffu, sg, o);
-          sb += __shfl_xor_sync(0xffffffffu, sb, o);
-          sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        if constexpr (DP > 0) {
+          if (more) fb.store(D, s_fb + ((bi + 1) & 1) * B * DP);
         }
-        if (pg == 0 && j < bc) {
-          const float4 r0 = s_r0[jb0 + j];
-          const float4 r1 = s_r1[jb0 + j];
-          // moments are about the tile centre: pixel offset dx = x - uc with uc = u - centre
-          const float uc = r0.x - ((float)tx0 + 8.f), vc = r0.y - ((float)ty0 + 8.f);
-          const float A = r0.z, Bq = r0.w, C = r1.x;
-          const float sdx = mx - uc * m1, sdy = my - vc * m1;            // sum gs dx, sum gs dy
-          const float sdxx = mxx - 2.f * uc * mx + uc * uc * m1;         // sum gs dx^2
-          const float sdyy = myy - 2.f * vc * my + vc * vc * m1;
-          const float sdxy = mxy - uc * my - vc * mx + uc * vc * m1;
-          const float gAq = 0.5f * sdxx, gBq = sdxy, gCq = 0.5f * sdyy;
-          const float gu = -(A * sdx + Bq * sdy), gv = -(C * sdy + Bq * sdx);
-          float* dst = g2d + (int64_t)s_id[jb0 + j] * kG2D;
-          red_add4(dst, gu, gv, gAq, gBq);
-          red_add4(dst + 4, gCq, so, sr, sg);
-          red_add4(dst + 8, sb, sz, 0.f, 0.f);
-        }
-      }
-      if constexpr (DP > 0) {
-        if (more) fb.store(D, s_fb + ((bi + 1) & 1) * B * DP);
-      }
-      __syncthreads();
+        __syncthreads();
 
-      // flush and clear the batch's feature-gradient sums
-      if constexpr (DP > 0) {
-        if (g_feats) {
-          if (D == DP) {
-            for (int e = t; e < bc * (DP / 4); e += kT) {
-              const int j = e / (DP / 4), q = e - j * (DP / 4);
-              float4* so = reinterpret_cast<float4*>(s_outF + j * DP + 4 * q);
-              atomicAdd(reinterpret_cast<float4*>(g_feats + (int64_t)s_id[jb0 + j] * D + 4 * q), *so);
-              *so = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-          } else {
-            for (int e = t; e < bc * DP; e += kT) {
-              const int j = e / DP, c = e - j * DP;
-              if (c < D) atomicAdd(g_feats + (int64_t)s_id[jb0 + j] * D + c, s_outF[e]);
-              s_outF[e] = 0.f;
+        // flush and clear the batch's feature-gradient sums
+        if constexpr (DP > 0) {
+          if (g_feats) {
+            if (D == DP) {
+              for (int e = t; e < bc * (DP / 4); e += kT) {
+                const int j = e / (DP / 4), q = e - j * (DP / 4);
+                float4* so = reinterpret_cast<float4*>(s_outF + j * DP + 4 * q);
+                atomicAdd(reinterpret_cast<float4*>(g_feats + (int64_t)s_id[jb0 + j] * D + 4 * q), *so);
+                *so = make_float4(0.f, 0.f, 0.f, 0.f);
+              }
+            } else {
+              for (int e = t; e < bc * DP; e += kT) {
+                const int j = e / DP, c = e - j * DP;
+                if (c < D) atomicAdd(g_feats + (int64_t)s_id[jb0 + j] * D + c, s_outF[e]);
+                s_outF[e] = 0.f;
+              }
             }
           }
         }
       }
     }
+    }
+    __syncthreads();   // shared memory and s_tile are reused by the next tile
   }
 }
 
 template <int DP, bool BF16>
-void launch_t(const CamDev& cam, const GaussRec* rec, const void* feats, int D, const uint2* ranges,
-              const uint32_t* inst_id, const float* T_final, const uint32_t* n_contrib,
+void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const void* feats, int D,
+              const uint2* ranges, const uint32_t* inst_id, const float* T_final,
+              const uint32_t* n_contrib,
               const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
               float* g2d, float* g_feats, cudaStream_t st) {
   const size_t smem = sizeof(float) * BwdCfg<DP>::smem_floats;
   auto kern = k_raster_bwd<DP, BF16>;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  static uint64_t configured = 0;   // one bit per device
-  if (smem > 48 * 1024 && !(configured >> (dev & 63) & 1)) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured |= 1ull << (dev & 63);
-  }
-  kern<<<cam.TX * cam.TY, kT, smem, st>>>(cam, rec, feats, D, ranges, inst_id, T_final, n_contrib,
-                                          g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats);
+  const int grid = persistent_grid(kern, kT, smem, tq.n_tiles);
+  kern<<<grid, kT, smem, st>>>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,
+                               g_depth, g_alpha, g_feat, g2d, g_feats);
   note_launch();
 }
 
 }  // namespace
 
-void launch_raster_bwd(const CamDev& cam, const GaussRec* rec, const void* feats, int feat_dtype,
-                       int D, const uint2* ranges, const uint32_t* inst_id, const float* T_final,
+void launch_raster_bwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
+                       const void* feats, int feat_dtype, int D, const uint2* ranges, const uint32_t* inst_id, const float* T_final,
                        const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
                        const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,
                        cudaStream_t st) {
@@ -434,9 +442,9 @@ void launch_raster_bwd(const CamDev& cam, const GaussRec* rec, const void* feats
   const bool bf = feat_dtype == GS_BF16;
   const int DP = g_feat ? padded_feat(D) : 0;
 #define GS_BWD(dp)                                                                           \
-  (bf ? launch_t<dp, true>(cam, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,  \
-                           g_depth, g_alpha, g_feat, g2d, g_feats, st)                      \
-      : launch_t<dp, false>(cam, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb, \
+  (bf ? launch_t<dp, true>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb, \
+                           g_depth, g_alpha, g_feat, g2d, g_feats, st)                          \
+      : launch_t<dp, false>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,  \
                             g_depth, g_alpha, g_feat, g2d, g_feats, st))
   switch (DP) {
     case 0: GS_BWD(0); break;

@@ -62,134 +62,141 @@ __device__ __forceinline__ void stage_features(const void* __restrict__ feats, i
 
 template <int DP, bool BF16>
 __global__ void __launch_bounds__(kB)
-k_raster_fwd(CamDev cam, const GaussRec* __restrict__ rec, const void* __restrict__ feats, int D,
-             const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_id,
-             float* __restrict__ rgb, float* __restrict__ depth, float* __restrict__ alpha,
-             float* __restrict__ feat, float* __restrict__ T_final,
-             uint32_t* __restrict__ n_contrib) {
+k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
+             const void* __restrict__ feats, int D, const uint2* __restrict__ ranges,
+             const uint32_t* __restrict__ inst_id, float* __restrict__ rgb,
+             float* __restrict__ depth, float* __restrict__ alpha, float* __restrict__ feat,
+             float* __restrict__ T_final, uint32_t* __restrict__ n_contrib) {
   __shared__ float4 s_r0[kB], s_r1[kB], s_r2[kB];
   __shared__ uint32_t s_id[kB];
   __shared__ int s_orig[kB];
   __shared__ int s_wc[8];
+  __shared__ int s_tile;
   extern __shared__ __align__(16) float s_feat[];   // [kB][DP]
 
-  const int tile = blockIdx.x;
-  const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
-  const int px = tx0 + (threadIdx.x & 15);
-  const int py = ty0 + (threadIdx.x >> 4);
-  const bool inside = px < cam.W && py < cam.H;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-  const uint2 rg = ranges[tile];
-  const int start = (int)rg.x, end = (int)rg.y;
+  // persistent CTA: tiles from the queue, heaviest first
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t q = atomicAdd(tq.head, 1u);
+      s_tile = q < (uint32_t)tq.n_tiles ? (int)(tq.order ? tq.order[q] : q) : -1;
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile < 0) break;
 
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
-  float acc[DP > 0 ? DP : 1];
+    const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
+    const int px = tx0 + (threadIdx.x & 15);
+    const int py = ty0 + (threadIdx.x >> 4);
+    const bool inside = px < cam.W && py < cam.H;
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const uint2 rg = ranges[tile];
+    const int start = (int)rg.x, end = (int)rg.y;
+
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
+    float acc[DP > 0 ? DP : 1];
 #pragma unroll
-  for (int c = 0; c < (DP > 0 ? DP : 1); ++c) acc[c] = 0.f;
-  int last = 0;
-  bool done = !inside;
+    for (int c = 0; c < (DP > 0 ? DP : 1); ++c) acc[c] = 0.f;
+    int last = 0;
+    bool done = !inside;
 
-  for (int b0 = start; b0 < end; b0 += kB) {
-    if (__syncthreads_count(done) == kB) break;
-    const int cnt = min(kB, end - b0);
-    // gather the batch and drop entries that no pixel of this tile can blend
-    bool keep = false;
-    uint32_t id = 0;
-    GaussRec g;
-    if ((int)threadIdx.x < cnt) id = inst_id[b0 + threadIdx.x];
-    if ((int)threadIdx.x < cnt && id < (uint32_t)cam.n_gauss) {
-      g = rec[id];
-      keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
-    }
-    int nk;
-    const int pos = block_compact_index(keep, s_wc, &nk);
-    if (keep) {
-      s_r0[pos] = g.r0;
-      s_r1[pos] = g.r1;
-      s_r2[pos] = g.r2;
-      s_id[pos] = id;
-      s_orig[pos] = b0 + (int)threadIdx.x - start;
-    }
-    __syncthreads();
-    stage_features<DP, BF16>(feats, D, s_id, nk, s_feat);
-    __syncthreads();
-    for (int j = 0; j < nk; ++j) {
-      if (__all_sync(0xffffffffu, done)) break;
-      const float4 r0 = s_r0[j];
-      const float4 r1 = s_r1[j];
-      float w = 0.f;
-      if (!done) {
-        const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-        if (sigma >= 0.f) {
-          const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
-          if (a >= kAlphaMin) {
-            const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
-            if (Tn < kTMin) {
-              done = true;
-            } else {
-              w = __fmul_rn(a, T);
-              T = Tn;
-              last = s_orig[j] + 1;
+    for (int b0 = start; b0 < end; b0 += kB) {
+      if (__syncthreads_count(done) == kB) break;
+      const int cnt = min(kB, end - b0);
+      // gather the batch and drop entries that no pixel of this tile can blend
+      bool keep = false;
+      uint32_t id = 0;
+      GaussRec g;
+      if ((int)threadIdx.x < cnt) id = inst_id[b0 + threadIdx.x];
+      if ((int)threadIdx.x < cnt && id < (uint32_t)cam.n_gauss) {
+        g = rec[id];
+        keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
+      }
+      int nk;
+      const int pos = block_compact_index(keep, s_wc, &nk);
+      if (keep) {
+        s_r0[pos] = g.r0;
+        s_r1[pos] = g.r1;
+        s_r2[pos] = g.r2;
+        s_id[pos] = id;
+        s_orig[pos] = b0 + (int)threadIdx.x - start;
+      }
+      __syncthreads();
+      stage_features<DP, BF16>(feats, D, s_id, nk, s_feat);
+      __syncthreads();
+      for (int j = 0; j < nk; ++j) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const float4 r0 = s_r0[j];
+        const float4 r1 = s_r1[j];
+        float w = 0.f;
+        if (!done) {
+          const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+          if (sigma >= 0.f) {
+            const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
+            if (a >= kAlphaMin) {
+              const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+              if (Tn < kTMin) {
+                done = true;
+              } else {
+                w = __fmul_rn(a, T);
+                T = Tn;
+                last = s_orig[j] + 1;
+              }
+            }
+          }
+        }
+        if (__any_sync(0xffffffffu, w != 0.f)) {
+          const float4 r2 = s_r2[j];
+          c0 = fmaf(w, r2.x, c0);
+          c1 = fmaf(w, r2.y, c1);
+          c2 = fmaf(w, r2.z, c2);
+          dep = fmaf(w, r1.z, dep);
+          if constexpr (DP > 0) {
+            const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * DP);
+#pragma unroll
+            for (int q = 0; q < DP / 4; ++q) {
+              const float4 f = f4[q];
+              acc[4 * q] = fmaf(w, f.x, acc[4 * q]);
+              acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
+              acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
+              acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
             }
           }
         }
       }
-      if (__any_sync(0xffffffffu, w != 0.f)) {
-        const float4 r2 = s_r2[j];
-        c0 = fmaf(w, r2.x, c0);
-        c1 = fmaf(w, r2.y, c1);
-        c2 = fmaf(w, r2.z, c2);
-        dep = fmaf(w, r1.z, dep);
-        if constexpr (DP > 0) {
-          const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * DP);
+    }
+    if (inside) {
+      const int64_t HW = (int64_t)cam.W * cam.H;
+      const int64_t p = (int64_t)py * cam.W + px;
+      if (rgb) {
+        rgb[p] = c0;
+        rgb[HW + p] = c1;
+        rgb[2 * HW + p] = c2;
+      }
+      if (depth) depth[p] = dep;
+      if (alpha) alpha[p] = 1.f - T;
+      if constexpr (DP > 0) {
+        if (feat) {
 #pragma unroll
-          for (int q = 0; q < DP / 4; ++q) {
-            const float4 f = f4[q];
-            acc[4 * q] = fmaf(w, f.x, acc[4 * q]);
-            acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
-            acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
-            acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
-          }
+          for (int c = 0; c < DP; ++c)
+            if (c < D) feat[c * HW + p] = acc[c];
         }
       }
+      T_final[p] = T;
+      n_contrib[p] = (uint32_t)last;
     }
+    __syncthreads();   // shared memory and s_tile are reused by the next tile
   }
-  if (!inside) return;
-  const int64_t HW = (int64_t)cam.W * cam.H;
-  const int64_t p = (int64_t)py * cam.W + px;
-  if (rgb) {
-    rgb[p] = c0;
-    rgb[HW + p] = c1;
-    rgb[2 * HW + p] = c2;
-  }
-  if (depth) depth[p] = dep;
-  if (alpha) alpha[p] = 1.f - T;
-  if constexpr (DP > 0) {
-    if (feat) {
-#pragma unroll
-      for (int c = 0; c < DP; ++c)
-        if (c < D) feat[c * HW + p] = acc[c];
-    }
-  }
-  T_final[p] = T;
-  n_contrib[p] = (uint32_t)last;
 }
 
 template <int DP, bool BF16>
-void launch_t(const CamDev& cam, const GaussRec* rec, const void* feats, int D, const uint2* ranges,
-              const uint32_t* inst_id, float* rgb, float* depth, float* alpha, float* feat,
-              float* T_final, uint32_t* n_contrib, cudaStream_t st) {
+void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const void* feats, int D,
+              const uint2* ranges, const uint32_t* inst_id, float* rgb, float* depth, float* alpha,
+              float* feat, float* T_final, uint32_t* n_contrib, cudaStream_t st) {
   const size_t smem = sizeof(float) * kB * DP;
   auto kern = k_raster_fwd<DP, BF16>;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  static uint64_t configured = 0;   // one bit per device
-  if (smem > 48 * 1024 && !(configured >> (dev & 63) & 1)) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured |= 1ull << (dev & 63);
-  }
-  kern<<<cam.TX * cam.TY, kB, smem, st>>>(cam, rec, feats, D, ranges, inst_id, rgb, depth, alpha,
-                                          feat, T_final, n_contrib);
+  const int grid = persistent_grid(kern, kB, smem, tq.n_tiles);
+  kern<<<grid, kB, smem, st>>>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
+                               T_final, n_contrib);
   note_launch();
 }
 
@@ -203,17 +210,17 @@ int padded_feat(int D) {
   return 64;
 }
 
-void launch_raster_fwd(const CamDev& cam, const GaussRec* rec, const void* feats, int feat_dtype,
-                       int D, const uint2* ranges, const uint32_t* inst_id, float* rgb,
-                       float* depth, float* alpha, float* feat, float* T_final,
-                       uint32_t* n_contrib, cudaStream_t st) {
+void launch_raster_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
+                       const void* feats, int feat_dtype, int D, const uint2* ranges,
+                       const uint32_t* inst_id, float* rgb, float* depth, float* alpha, float* feat,
+                       float* T_final, uint32_t* n_contrib, cudaStream_t st) {
   if (cam.TX * cam.TY == 0) return;
   const bool bf = feat_dtype == GS_BF16;
   const int DP = feat ? padded_feat(D) : 0;   // no feature output: skip feature blending
 #define GS_FWD(dp)                                                                             \
-  (bf ? launch_t<dp, true>(cam, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat, T_final, \
-                           n_contrib, st)                                                       \
-      : launch_t<dp, false>(cam, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,       \
+  (bf ? launch_t<dp, true>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,     \
+                           T_final, n_contrib, st)                                              \
+      : launch_t<dp, false>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,    \
                             T_final, n_contrib, st))
   switch (DP) {
     case 0: GS_FWD(0); break;

@@ -350,6 +350,34 @@ __global__ void k_ranges(const uint32_t* __restrict__ tile, const uint32_t* coun
   if (i + 1 == n || tile[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
+// Heavy-first tile order for the persistent raster kernels: tiles bucketed by the bit
+// length of their list length, longest buckets first (order inside a bucket is arbitrary;
+// results do not depend on the order tiles are processed in).  One block.
+constexpr int kOrderThreads = 1024;
+__global__ void __launch_bounds__(kOrderThreads)
+k_tile_order(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_cnt[33], s_cur[33];
+  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += kOrderThreads) {
+    const uint2 r = ranges[t];
+    atomicAdd(&s_cnt[__clz((int)(r.y - r.x))], 1u);   // 32 - bit length: longest first
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int b = 0; b < 33; ++b) {
+      s_cur[b] = acc;
+      acc += s_cnt[b];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += kOrderThreads) {
+    const uint2 r = ranges[t];
+    order[atomicAdd(&s_cur[__clz((int)(r.y - r.x))], 1u)] = (uint32_t)t;
+  }
+}
+
 // I_eff = sum over tiles of max n_contrib inside the tile.
 __global__ void __launch_bounds__(kThreads)
 k_inst_eff(const uint32_t* __restrict__ n_contrib, int TX, int W, int H, uint32_t* counters) {
@@ -450,6 +478,13 @@ void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int
   k_ranges<<<(int)ceil_div(b, 256), 256, 0, st>>>(inst_tile, counters, bound_i, cap, n_tiles,
                                                    ranges);
   note_launch();
+}
+
+bool launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t st) {
+  if (n_tiles <= 0 || n_tiles > kMaxOrderedTiles) return false;
+  k_tile_order<<<1, kOrderThreads, 0, st>>>(ranges, n_tiles, order);
+  note_launch();
+  return true;
 }
 
 void launch_inst_eff(const uint32_t* n_contrib, int TX, int TY, int W, int H, uint32_t* counters,
