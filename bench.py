@@ -73,7 +73,112 @@ def stage_bytes(st, D, bf, K):
     }
 
 
+def stage_flops(st, D, K):
+    """Algorithmic FP32 FLOPs per launch (FMA = 2, exp = 1) from the exact pair counts:
+    E = pairs up to each pixel's last contributor, Eb = pairs blended."""
+    V, E, Eb = st["visible"], st["pairs_eval"], st["pairs_blend"]
+    return {
+        "project": V * (150 + 6 * K),
+        "bin": 0,
+        "fwd": 12 * E + 2 * (4 + D) * Eb,
+        "bwd_raster": 30 * E + 6 * (4 + D) * Eb,
+        "bwd_project": V * (400 + 12 * K),
+    }
+
+
+def fp32_peak_tflops(peaks):
+    """FP32 FMA peak derived from the unit counts: 152 SMs x 128 lanes x 2 FLOP x max clock."""
+    return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+KERNEL_SOURCES = {
+    "bwd_raster": ["gs_raster_bwd.cu", "gs_blend.cuh", "gs_internal.cuh"],
+    "fwd": ["gs_raster_fwd.cu", "gs_blend.cuh", "gs_internal.cuh"],
+    "bin": ["gs_sort.cu", "gs_internal.cuh"],
+    "project": ["gs_project_fwd.cu", "gs_internal.cuh"],
+    "bwd_project": ["gs_project_bwd.cu", "gs_internal.cuh"],
+}
+
+
+def source_hash(stage):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[stage]:
+        with open(os.path.join(ROOT, "paper_2603_09632_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(stage, workload):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(stage)
+    if e and e.get("source_sha") == source_hash(stage):
+        return e["dram_bytes_per_launch"]
+    return None
+
+
 # ---------------------------------------------------------------- clocks
+
+class NvmlClockSampler:
+    """SM clock and clock-event reasons every ~1 ms through the driver's NVML library
+    (read-only queries), for timed regions far shorter than nvidia-smi's sampling period."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device):
+        import ctypes
+        self.C = ctypes
+        self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        import torch
+        pr = torch.cuda.get_device_properties(torch_device)
+        bus = f"{getattr(pr, 'pci_domain_id', 0):08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+        self.h = ctypes.c_void_p()
+        if self.nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle for " + bus)
+        self.getr = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples, self.reasons, self.run = [], 0, False
+        mx = ctypes.c_uint()
+        self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx))
+        self.max_mhz = float(mx.value)
+
+    def _loop(self):
+        C = self.C
+        v, r = C.c_uint(), C.c_ulonglong()
+        while self.run:
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, C.byref(v)) == 0:
+                self.samples.append(float(v.value))
+            if self.getr(self.h, C.byref(r)) == 0:
+                self.reasons |= int(r.value)
+            time.sleep(0.001)
+
+    def start(self):
+        self.run = True
+        self.t = threading.Thread(target=self._loop, daemon=True)
+        self.t.start()
+
+    def stop(self):
+        self.run = False
+        self.t.join(timeout=2)
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(n for b, n in self.REASONS.items() if self.reasons & b),
+                "samples": len(self.samples), "source": "nvml"}
+
+
+def make_clock_sampler(dev, index):
+    try:
+        return NvmlClockSampler(dev)
+    except (OSError, AttributeError):
+        return ClockSampler(index)
+
 
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -200,9 +305,8 @@ def run_gpu(args):
            for _ in range(args.steps)]
     L.gs_timing_enable(ws, True)
     L.gs_timing_collect(ws)
-    clocks = ClockSampler(local)
+    clocks = make_clock_sampler(dev, local)
     clocks.start()
-    time.sleep(0.3)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -230,25 +334,47 @@ def run_gpu(args):
     value = world * args.steps * P / (ms * 1e-3) / 1e6
 
     # algorithmic bytes per stage, averaged over the timed poses (untimed recount)
-    sb_tot = {}
+    sb_tot, sf_tot, pairs = {}, {}, [0, 0]
     for k in range(args.steps):
         c = gcams[poses[args.warmup + k]]
         L.gs_project(scene, c, ws)
         L.gs_bin_tiles(ws, sync=True)
         L.gs_render_fwd(scene, c, ws, out["rgb"], out["depth"], out["alpha"], out["feat"])
         st = L.gs_get_stats(ws)
+        pairs[0] += st["pairs_eval"]
+        pairs[1] += st["pairs_blend"]
         for name, b in stage_bytes(st, D, bf, K).items():
             sb_tot[name] = sb_tot.get(name, 0.0) + b
+        for name, f in stage_flops(st, D, K).items():
+            sf_tot[name] = sf_tot.get(name, 0.0) + f
     stage_ms = {name: stage[name][0] / max(stage[name][1], 1) for name in stage}
     dom = max(stage_ms, key=stage_ms.get)
     peaks, src = load_peaks()
-    alg = sb_tot[dom] / args.steps
-    achieved = alg / (stage_ms[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "traffic": None, "peak_source": src,
-                "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-                "stage_alg_mb": {k: round(v / args.steps / 1e6, 3) for k, v in sb_tot.items()}}
+    alg_b = sb_tot[dom] / args.steps
+    alg_f = sf_tot[dom] / args.steps
+    p_alu = fp32_peak_tflops(peaks)
+    t_hbm = alg_b / (peaks["hbm_gbs"] * 1e9)
+    t_alu = alg_f / (p_alu * 1e12)
+    t_meas = stage_ms[dom] * 1e-3
+    traffic = captured_traffic(dom, args.workload)
+    if t_alu > t_hbm:
+        achieved = alg_f / t_meas / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(p_alu, 1),
+                    "unit": "TFLOP/s", "frac": round(achieved / p_alu, 4),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
+    else:
+        achieved = alg_b / t_meas / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                    "peak_source": src}
+    roofline.update({
+        "traffic": traffic, "alg_bytes": int(alg_b), "alg_flops": int(alg_f),
+        "hbm_frac": round(alg_b / t_meas / 1e9 / peaks["hbm_gbs"], 4),
+        "alu_frac": round(alg_f / t_meas / 1e12 / p_alu, 4),
+        "pairs_eval_per_step": int(pairs[0] / args.steps), "pairs_blend_per_step": int(pairs[1] / args.steps),
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_alg_mb": {k: round(v / args.steps / 1e6, 3) for k, v in sb_tot.items()},
+        "stage_alg_gflop": {k: round(v / args.steps / 1e9, 3) for k, v in sf_tot.items()}})
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, L, scene_np, gcams, poses, wl, dev, stream, ws, K, D, fdt, H, W)

@@ -91,6 +91,8 @@ typedef struct {
   int64_t inst_eff;     /* I_eff: sum over tiles of the longest list prefix a pixel used */
   int64_t pixels;       /* P */
   int64_t tiles;        /* T */
+  int64_t pairs_eval;   /* sum over pixels of the list entries up to the last contributor */
+  int64_t pairs_blend;  /* sum over pixels of the Gaussians actually blended */
 } gs_stats;
 
 /* Human-readable name of a status code (static string). */

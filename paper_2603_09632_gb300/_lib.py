@@ -45,7 +45,8 @@ class gs_scene(C.Structure):
 
 class gs_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("visible", C.c_int64), ("instances", C.c_int64),
-                ("inst_eff", C.c_int64), ("pixels", C.c_int64), ("tiles", C.c_int64)]
+                ("inst_eff", C.c_int64), ("pixels", C.c_int64), ("tiles", C.c_int64),
+                ("pairs_eval", C.c_int64), ("pairs_blend", C.c_int64)]
 
 
 def _load():

@@ -61,6 +61,8 @@ struct gs_workspace {
   // scratch
   DevBuf<uint32_t> bin_zero, counters;   // bin_zero: digit histograms + chunk tickets
   DevBuf<unsigned long long> bin_status;  // look-back status words
+  DevBuf<unsigned long long> stats64;     // pair counts (statistics only)
+  CamDev cam{};                           // camera of the last gs_project
   uint32_t epoch = 0;
   uint32_t* h_counters = nullptr;   // pinned mirror
   // state
@@ -257,7 +259,7 @@ void gs_workspace_destroy(gs_workspace* ws) {
     ws->inst_tile.release(); ws->inst_id.release(); ws->inst_tile2.release(); ws->inst_id2.release();
     ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
     ws->tile_order.release(); ws->queue.release();
-    ws->bin_zero.release(); ws->bin_status.release(); ws->counters.release();
+    ws->bin_zero.release(); ws->bin_status.release(); ws->counters.release(); ws->stats64.release();
     if (ws->h_counters) cudaFreeHost(ws->h_counters);
     if (ws->ev_created)
       for (int k = 0; k < GS_NUM_TIMERS; ++k)
@@ -313,6 +315,7 @@ gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
                  st);
   GS_TRY(cudaGetLastError());
   ws->n = scene->n;
+  ws->cam = cd;
   ws->W = cd.W;
   ws->H = cd.H;
   ws->TX = cd.TX;
@@ -446,6 +449,13 @@ gs_status gs_get_stats(gs_workspace* ws, gs_stats* out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (ws->stage >= 3)
     launch_inst_eff(ws->n_contrib.p, ws->TX, ws->TY, ws->W, ws->H, ws->counters.p, st);
+  unsigned long long pairs[2] = {0ull, 0ull};
+  if (ws->stage >= 3) {
+    GS_TRY(ws->stats64.ensure(2));
+    launch_pair_stats(ws->cam, ws->rec.p, ws->ranges.p, ws->id_sorted, ws->n_contrib.p,
+                      ws->stats64.p, st);
+    GS_TRY(cudaMemcpyAsync(pairs, ws->stats64.p, sizeof(pairs), cudaMemcpyDeviceToHost, st));
+  }
   GS_TRY(cudaMemcpyAsync(ws->h_counters, ws->counters.p, kCntNum * sizeof(uint32_t),
                          cudaMemcpyDeviceToHost, st));
   GS_TRY(cudaStreamSynchronize(st));
@@ -455,6 +465,8 @@ gs_status gs_get_stats(gs_workspace* ws, gs_stats* out, void* stream) {
   out->inst_eff = ws->stage >= 3 ? ws->h_counters[kCntInstEff] : 0;
   out->pixels = (int64_t)ws->W * ws->H;
   out->tiles = (int64_t)ws->TX * ws->TY;
+  out->pairs_eval = (int64_t)pairs[0];
+  out->pairs_blend = (int64_t)pairs[1];
   return GS_OK;
 }
 

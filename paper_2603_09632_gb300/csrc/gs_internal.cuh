@@ -95,6 +95,10 @@ void launch_inst_eff(const uint32_t* n_contrib, int TX, int TY, int W, int H, ui
 // index order.
 constexpr int kMaxOrderedTiles = 1 << 18;
 bool launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t st);
+// Pair counts for the roofline model (stats only): stats64[0] = evaluated, [1] = blended.
+void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* ranges,
+                       const uint32_t* inst_id, const uint32_t* n_contrib,
+                       unsigned long long* stats64, cudaStream_t st);
 
 // Persistent raster scheduling: a CTA takes the next tile index from *queue (zeroed
 // before each launch) and maps it through `order` (identity when null).

@@ -15,6 +15,7 @@
 // carries on with guarded writes).  Digit histograms of all passes are computed up front
 // (depth keys) or while emitting the instances (tile keys).  The tile-count prefix sum
 // is fused into the emission kernel with the same look-back.
+#include "gs_blend.cuh"
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -378,6 +379,46 @@ k_tile_order(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict
   }
 }
 
+// Statistics for the roofline model (not on the rendering path): per pixel, the list
+// entries up to its last contributor (the pairs the backward pass evaluates) and how many
+// of them it blended, summed over the image into stats64[0..1].  The opacity test is the
+// rasterizer's own (gs_blend.cuh).
+__global__ void __launch_bounds__(kThreads)
+k_pair_stats(CamDev cam, const GaussRec* __restrict__ rec, const uint2* __restrict__ ranges,
+             const uint32_t* __restrict__ inst_id, const uint32_t* __restrict__ n_contrib,
+             unsigned long long* __restrict__ stats64) {
+  const int tile = blockIdx.x;
+  const int px = (tile % cam.TX) * 16 + (threadIdx.x & 15), py = (tile / cam.TX) * 16 + (threadIdx.x >> 4);
+  uint32_t eval = 0, blend = 0;
+  if (px < cam.W && py < cam.H) {
+    const uint32_t nc = n_contrib[(int64_t)py * cam.W + px];
+    const uint2 rg = ranges[tile];
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    for (uint32_t k = 0; k < nc && rg.x + k < rg.y; ++k) {
+      const uint32_t id = inst_id[rg.x + k];
+      if (id >= (uint32_t)cam.n_gauss) continue;
+      const float4 r0 = rec[id].r0, r1 = rec[id].r1;
+      ++eval;
+      const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+      if (sigma >= 0.f && fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma))) >= kAlphaMin) ++blend;
+    }
+  }
+  __shared__ unsigned long long s[2];
+  if (threadIdx.x == 0) s[0] = s[1] = 0ull;
+  __syncthreads();
+  eval = __reduce_add_sync(0xffffffffu, eval);
+  blend = __reduce_add_sync(0xffffffffu, blend);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s[0], (unsigned long long)eval);
+    atomicAdd(&s[1], (unsigned long long)blend);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&stats64[0], s[0]);
+    atomicAdd(&stats64[1], s[1]);
+  }
+}
+
 // I_eff = sum over tiles of max n_contrib inside the tile.
 __global__ void __launch_bounds__(kThreads)
 k_inst_eff(const uint32_t* __restrict__ n_contrib, int TX, int W, int H, uint32_t* counters) {
@@ -477,6 +518,15 @@ void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int
   if (b <= 0) return;
   k_ranges<<<(int)ceil_div(b, 256), 256, 0, st>>>(inst_tile, counters, bound_i, cap, n_tiles,
                                                    ranges);
+  note_launch();
+}
+
+void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* ranges,
+                       const uint32_t* inst_id, const uint32_t* n_contrib,
+                       unsigned long long* stats64, cudaStream_t st) {
+  cudaMemsetAsync(stats64, 0, 2 * sizeof(unsigned long long), st);
+  if (cam.TX * cam.TY == 0) return;
+  k_pair_stats<<<cam.TX * cam.TY, kThreads, 0, st>>>(cam, rec, ranges, inst_id, n_contrib, stats64);
   note_launch();
 }
 
