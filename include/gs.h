@@ -202,6 +202,32 @@ gs_status gs_timing_collect(gs_workspace* ws, double* ms_out, int64_t* count_out
  * workspaces, all devices).  Host-side counter; no synchronisation. */
 int64_t gs_launch_count(void);
 
+/* ---- rendering without allocation ------------------------------------------------
+ *
+ * gs_render_fwd_noalloc renders like gs_project -> gs_bin_tiles -> gs_render_fwd (same
+ * kernels, same images) but allocates nothing: no workspace, no cudaMalloc, no
+ * allocating library call.  It serves callers that cannot allocate device memory when
+ * they render -- a plugin inside a host application that owns every allocation, code
+ * held to a fixed device-memory budget, or a context where a cudaMalloc would stall or
+ * fail.  The paper has no counterpart; this is an interface convenience.
+ *
+ * Every intermediate buffer lives in one file-scope device array of about 4 MB that
+ * each device using the library holds until the process exits.  That bounds the
+ * request: at most 16384 Gaussians, 131072 tile instances, 65536 pixels and 1024 tiles
+ * (e.g. 256 x 256); a larger request returns GS_ERR_OVER_BUDGET and writes nothing.
+ *   - The first call on a device, with that device current, looks the array up with
+ *     cudaGetSymbolAddress and clears part of it (and synchronises the device once);
+ *     make that first call before any stream capture.
+ *   - Every call on a device shares the array and it keeps the last call's contents:
+ *     calls that overlap on the GPU (other streams, other threads) race and must be
+ *     serialised by the caller.
+ *   - The call synchronises `stream` once (after projection) to check the instance count.
+ * scene, cam and the outputs are as for gs_project / gs_render_fwd (device pointers,
+ * outputs channel-major, any output may be NULL).  Errors: GS_ERR_ARG, GS_ERR_OVER_BUDGET,
+ * GS_ERR_CUDA. */
+gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camera* cam, float* rgb,
+                                float* depth, float* alpha, float* feat, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

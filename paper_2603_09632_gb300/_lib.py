@@ -73,6 +73,7 @@ def _load():
         "gs_timing_enable": ([P, i32], st),
         "gs_timing_collect": ([P, P, P], st),
         "gs_launch_count": ([], i64),
+        "gs_render_fwd_noalloc": ([P, P, P, P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -271,6 +272,13 @@ def gs_get_pixel_state(ws, H, W, stream=None):
     _check(lib.gs_get_pixel_state(ws.h, P(T.ctypes.data), P(nc.ctypes.data), _stream(stream)),
            "gs_get_pixel_state")
     return T, nc
+
+
+def gs_render_fwd_noalloc(scene, cam, rgb=None, depth=None, alpha=None, feat=None, stream=None):
+    """Forward render with no allocation (library-held fixed scratch; small scenes only).
+    Returns the status code instead of raising, so callers can test GS_ERR_OVER_BUDGET."""
+    return lib.gs_render_fwd_noalloc(C.byref(scene.c), C.byref(cam), _ptr(rgb), _ptr(depth),
+                                     _ptr(alpha), _ptr(feat), _stream(stream))
 
 
 def gs_launch_count() -> int:

@@ -1,0 +1,183 @@
+// gs_render_fwd_noalloc: a forward render that allocates no memory.
+//
+// For callers that cannot allocate device memory when they render -- a plugin that
+// runs inside a host application owning every allocation, code running under a fixed
+// device-memory budget, or a renderer called from a context where a cudaMalloc would
+// stall or fail -- this entry point renders small scenes with every intermediate buffer
+// (projection records, sort buffers, tile lists, per-pixel state) carved out of one
+// file-scope device array of fixed size that the library holds for as long as it is
+// loaded.  The caller passes only the scene, the camera and the output images.
+//
+// It runs the same kernels as gs_project -> gs_bin_tiles -> gs_render_fwd, so its images
+// are the same.  Limits: at most kNaMaxGauss Gaussians, kNaMaxInst tile instances,
+// kNaMaxPix pixels and kNaMaxTiles tiles; larger requests return GS_ERR_OVER_BUDGET.
+#include <mutex>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int64_t kNaMaxGauss = 16384;
+constexpr int64_t kNaMaxInst = 131072;
+constexpr int64_t kNaMaxPix = 65536;
+constexpr int64_t kNaMaxTiles = 1024;
+constexpr int kNaMaxDevices = 64;
+
+constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+// byte offsets of the sub-buffers inside the scratch array
+constexpr size_t oRec = 0;
+constexpr size_t oKey = al(oRec + kNaMaxGauss * sizeof(GaussRec));
+constexpr size_t oNt = al(oKey + kNaMaxGauss * 4);
+constexpr size_t oRect = al(oNt + kNaMaxGauss * 4);
+constexpr size_t oK0 = al(oRect + kNaMaxGauss * 8);
+constexpr size_t oV0 = al(oK0 + kNaMaxGauss * 4);
+constexpr size_t oK1 = al(oV0 + kNaMaxGauss * 4);
+constexpr size_t oV1 = al(oK1 + kNaMaxGauss * 4);
+constexpr size_t oIT0 = al(oV1 + kNaMaxGauss * 4);
+constexpr size_t oII0 = al(oIT0 + kNaMaxInst * 4);
+constexpr size_t oIT1 = al(oII0 + kNaMaxInst * 4);
+constexpr size_t oII1 = al(oIT1 + kNaMaxInst * 4);
+constexpr size_t oTf = al(oII1 + kNaMaxInst * 4);
+constexpr size_t oNc = al(oTf + kNaMaxPix * 4);
+constexpr size_t oRanges = al(oNc + kNaMaxPix * 4);
+constexpr size_t oOrder = al(oRanges + kNaMaxTiles * 8);
+constexpr size_t oZero = al(oOrder + kNaMaxTiles * 4);          // digit histograms + tickets
+constexpr size_t oCnt = al(oZero + kBinZeroWords * 4);           // counters
+constexpr size_t oQueue = al(oCnt + kCntNum * 4);                // raster tile-queue head
+constexpr size_t oStatus = al(oQueue + 4 * 4);                   // look-back status words
+constexpr size_t kNaBytes = al(oStatus + (size_t)kNaMaxInst / 8 * 8 * 8 + 64 * 1024);
+
+}  // namespace
+}  // namespace gs
+
+// The scratch: one array per device, shared by every call (about 4 MB).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[gs::kNaBytes];
+
+namespace gs {
+namespace {
+
+std::mutex g_na_mu;
+unsigned char* g_na_ptr[kNaMaxDevices] = {};
+uint32_t g_na_epoch[kNaMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+gs_status na_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kNaMaxDevices) return GS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (!g_na_ptr[dev]) {
+    if (bin_status_words(kNaMaxInst) * sizeof(unsigned long long) > kNaBytes - oStatus)
+      return GS_ERR_ARG;   // layout inconsistent with the sort's chunking (build error)
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GS_ERR_CUDA;
+    // the look-back status words must start at zero (they are epoch-tagged afterwards)
+    if (cudaMemset(static_cast<unsigned char*>(p) + oStatus, 0, kNaBytes - oStatus) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      return GS_ERR_CUDA;
+    g_na_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_na_ptr[dev];
+  return GS_OK;
+}
+
+bool na_aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int na_bits_for(int64_t n_values) {
+  int b = 0;
+  while ((int64_t(1) << b) < n_values) ++b;
+  return b;
+}
+
+}  // namespace
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camera* c, float* rgb,
+                                           float* depth, float* alpha, float* feat, void* stream) {
+  if (!scene || !c) return GS_ERR_ARG;
+  if (scene->n < 0 || scene->sh_degree < 0 || scene->sh_degree > 3 || scene->n_feat < 0 ||
+      scene->n_feat > kMaxFeat || (scene->feat_dtype != GS_F32 && scene->feat_dtype != GS_BF16))
+    return GS_ERR_ARG;
+  if (scene->n > 0 && (!scene->means || !scene->scales || !scene->quats || !scene->opacities ||
+                       !scene->sh || (scene->n_feat > 0 && !scene->feats)))
+    return GS_ERR_ARG;
+  if (!na_aligned16(scene->means) || !na_aligned16(scene->scales) || !na_aligned16(scene->quats) ||
+      !na_aligned16(scene->sh) || (scene->feats && !na_aligned16(scene->feats)) ||
+      (feat && !na_aligned16(feat)))
+    return GS_ERR_ARG;
+  if (c->W <= 0 || c->H <= 0 || c->tile != kTile || !(c->fx > 0.f) || !(c->fy > 0.f) ||
+      !(c->near_z > 0.f) || c->stride != 1 || c->off_x != 0 || c->off_y != 0)
+    return GS_ERR_ARG;
+  CamDev cd;
+  cd.W = c->W;
+  cd.H = c->H;
+  cd.TX = (c->W + kTile - 1) / kTile;
+  cd.TY = (c->H + kTile - 1) / kTile;
+  cd.n_gauss = (int)scene->n;
+  cd.fx = c->fx;
+  cd.fy = c->fy;
+  cd.cx = c->cx;
+  cd.cy = c->cy;
+  for (int k = 0; k < 9; ++k) cd.R[k] = c->R[k];
+  for (int k = 0; k < 3; ++k) cd.t[k] = c->t[k];
+  cd.near_z = c->near_z;
+  const int64_t ntl = (int64_t)cd.TX * cd.TY;
+  if (scene->n > kNaMaxGauss || (int64_t)c->W * c->H > kNaMaxPix || ntl > kNaMaxTiles)
+    return GS_ERR_OVER_BUDGET;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
+  unsigned char* base = nullptr;
+  gs_status s = na_scratch(dev, &base);
+  if (s != GS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  GaussRec* rec = reinterpret_cast<GaussRec*>(base + oRec);
+  uint32_t* key = reinterpret_cast<uint32_t*>(base + oKey);
+  uint32_t* nt = reinterpret_cast<uint32_t*>(base + oNt);
+  uint2* rect = reinterpret_cast<uint2*>(base + oRect);
+  uint32_t *k0 = reinterpret_cast<uint32_t*>(base + oK0), *v0 = reinterpret_cast<uint32_t*>(base + oV0);
+  uint32_t *k1 = reinterpret_cast<uint32_t*>(base + oK1), *v1 = reinterpret_cast<uint32_t*>(base + oV1);
+  uint32_t *it0 = reinterpret_cast<uint32_t*>(base + oIT0), *ii0 = reinterpret_cast<uint32_t*>(base + oII0);
+  uint32_t *it1 = reinterpret_cast<uint32_t*>(base + oIT1), *ii1 = reinterpret_cast<uint32_t*>(base + oII1);
+  float* Tf = reinterpret_cast<float*>(base + oTf);
+  uint32_t* nc = reinterpret_cast<uint32_t*>(base + oNc);
+  uint2* ranges = reinterpret_cast<uint2*>(base + oRanges);
+  uint32_t* order = reinterpret_cast<uint32_t*>(base + oOrder);
+  uint32_t* zero = reinterpret_cast<uint32_t*>(base + oZero);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(base + oCnt);
+  uint32_t* queue = reinterpret_cast<uint32_t*>(base + oQueue);
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(base + oStatus);
+
+  // the array keeps the previous call's contents: clear what must start at zero
+  if (cudaMemsetAsync(cnt, 0, kCntNum * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(zero, 0, kBinZeroWords * 4, st) != cudaSuccess)
+    return GS_ERR_CUDA;
+  launch_project(*scene, cd, rec, key, nt, rect, cnt, st);
+  // the instance count decides whether the request fits: one synchronisation
+  uint32_t h_cnt[kCntNum];
+  if (cudaMemcpyAsync(h_cnt, cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GS_ERR_CUDA;
+  const int64_t I = h_cnt[kCntInst];
+  if (I > kNaMaxInst) return GS_ERR_OVER_BUDGET;
+  BinScratch bs;
+  bs.ghist = zero;
+  bs.tickets = zero + 7 * 256;
+  bs.status = status;
+  bs.counters = cnt;
+  bs.epoch = &g_na_epoch[dev];
+  const int64_t n = scene->n;
+  launch_depth_sort(key, n, k1, v1, k0, v0, bs, st);
+  launch_emit_instances(v0, nt, rect, n, cd.TX, kNaMaxInst, k1, it0, ii0, bs, st);
+  const int w2 = launch_tile_sort(I, na_bits_for(ntl), it0, ii0, it1, ii1, bs, st);
+  const uint32_t* tiles = w2 ? it1 : it0;
+  const uint32_t* ids = w2 ? ii1 : ii0;
+  launch_tile_ranges(tiles, cnt, I, kNaMaxInst, (int)ntl, ranges, st);
+  const bool ordered = launch_tile_order(ranges, (int)ntl, order, st);
+  if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GS_ERR_CUDA;
+  const TileQueue tq{queue, ordered ? order : nullptr, (int)ntl};
+  launch_raster_fwd(cd, tq, rec, scene->feats, scene->feat_dtype, scene->n_feat, ranges, ids, rgb,
+                    depth, alpha, scene->n_feat > 0 ? feat : nullptr, Tf, nc, st);
+  return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
