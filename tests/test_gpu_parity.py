@@ -148,6 +148,59 @@ def test_full_size_slam_frame_sampled(oracle):
         assert U.rel_err(gpu["grads"][k], rb[k]) <= TOL_BWD, k
 
 
+def _tile_pixels(cam, n_tiles, seed):
+    """All pixels of n_tiles random 16x16 tiles (flat indices)."""
+    rng = np.random.default_rng(seed)
+    TX, TY = (cam.W + 15) // 16, (cam.H + 15) // 16
+    out = []
+    for t in rng.choice(TX * TY, size=n_tiles, replace=False):
+        x0, y0 = (t % TX) * 16, (t // TX) * 16
+        ys, xs = np.mgrid[y0:min(y0 + 16, cam.H), x0:min(x0 + 16, cam.W)]
+        out.append((ys * cam.W + xs).ravel())
+    return np.concatenate(out)
+
+
+def _sampled_parity(oracle, sc, cam, pix, bf16, mode):
+    g = S.upstream_grads(cam.H, cam.W, sc.n_feat)
+    mask = np.zeros(cam.W * cam.H, bool)
+    mask[pix] = True
+    gm = {k: (v.reshape(v.shape[:-2] + (-1,)) * mask).reshape(v.shape) for k, v in g.items()}
+    gpu = U.run(sc, cam, gm, bf16=bf16)
+    feats = U.bf16_round(sc.feats) if bf16 else None
+    scr = sc if feats is None else S.Scene(**{k: getattr(sc, k) for k in
+                                               ("means", "scales", "quats", "opacities", "sh")},
+                                           feats=feats, sh_degree=sc.sh_degree)
+    ref = oracle.render(scr, cam, "f32", pixels=pix, mode=mode)
+    flags = ref["flags"]
+    assert (flags != 0).mean() < 0.03      # large Gaussians at 4K cross more thresholds
+    P = cam.W * cam.H
+    for k in ("rgb", "depth", "alpha", "feat"):
+        v = gpu[k].reshape(gpu[k].shape[:-2] + (P,))[..., pix]
+        assert U.max_abs_unflagged(v, ref[k], flags) <= TOL_FWD, k
+    gs = {k: v.reshape(v.shape[:-2] + (-1,))[..., pix] for k, v in g.items()}
+    rb = oracle.backward(scr, cam, gs, "f32", pixels=pix, mode=mode)
+    for k in GRAD_KEYS:
+        assert U.rel_err(gpu["grads"][k], rb[k]) <= TOL_BWD, k
+    return gpu
+
+
+def test_full_size_semantic_frame_sampled(oracle):
+    """1200x680, 1M room Gaussians, SH 3, 64 bf16 features: forward on 12 sampled tiles,
+    backward of a loss restricted to them (oracle fed the same bf16 feature values)."""
+    sc, cams = S.config_semantic(n_poses=100)
+    cam = cams[7]
+    _sampled_parity(oracle, sc, cam, _tile_pixels(cam, 12, 3), bf16=True, mode=1)
+
+
+def test_full_size_memory_frame_sampled(oracle):
+    """3840x2160, 3M room Gaussians, 32 fp32 features (per-tile recomputation, no stored
+    blend lists): 8 sampled tiles, oracle by brute force over all Gaussians per tile."""
+    sc, cams = S.config_memory(n_poses=10)
+    cam = cams[3]
+    gpu = _sampled_parity(oracle, sc, cam, _tile_pixels(cam, 8, 4), bf16=False, mode=0)
+    assert gpu["instances"] > 1_000_000
+
+
 # ---------------------------------------------------------------- edge cases
 
 def test_empty_scene():
