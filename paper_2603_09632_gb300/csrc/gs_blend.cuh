@@ -28,19 +28,30 @@ __device__ __forceinline__ float edge_min_sigma(float dx, float lo, float hi, fl
   return 0.5f * (a * dx * dx + c * dy * dy) + b * dx * dy;
 }
 
+// sigma above which a pixel cannot reach alpha >= 1/255: ln(255 o) plus a margin of 1e-3
+// (0.1 % in alpha), far above the rounding of sigma and of __expf.  A pixel whose sigma
+// exceeds it is skipped by the exact test below as well, so using it as a pre-test (to skip
+// the exponential) or for culling (conservative) changes no decision.
+__device__ __forceinline__ float sigma_cut(float o) { return __logf(255.f * o) + 1e-3f; }
+
+// Minimum of sigma over the box of pixel centres [bx0, bx1] x [by0, by1] (absolute pixel
+// coordinates).  sigma is convex, so the minimum is 0 when the mean lies inside the box and
+// otherwise lies on one of the four edges.
+__device__ __forceinline__ float box_min_sigma(float bx0, float by0, float bx1, float by1, float u,
+                                               float v, float A, float B, float C) {
+  const float lx = bx0 - u, hx = bx1 - u;
+  const float ly = by0 - v, hy = by1 - v;
+  if (lx <= 0.f && hx >= 0.f && ly <= 0.f && hy >= 0.f) return 0.f;
+  return fminf(fminf(edge_min_sigma(lx, ly, hy, A, B, C), edge_min_sigma(hx, ly, hy, A, B, C)),
+               fminf(edge_min_sigma(ly, lx, hx, C, B, A), edge_min_sigma(hy, lx, hx, C, B, A)));
+}
+
 // Conservative per-tile test: true when no pixel centre of the 16x16 tile with origin
 // (x0, y0) can reach alpha >= 1/255 for this Gaussian, so the tile can skip it without
-// changing any output.  sigma is convex, so its minimum over the box of pixel centres is
-// 0 when the mean lies inside the box and otherwise lies on one of the four edges.  The
-// test keeps a margin of 1e-3 in sigma (0.1 % in alpha), far above rounding.
+// changing any output.
 __device__ __forceinline__ bool tile_culled(float x0, float y0, float u, float v, float A, float B,
                                             float C, float o) {
-  const float lx = x0 + 0.5f - u, hx = x0 + 15.5f - u;
-  const float ly = y0 + 0.5f - v, hy = y0 + 15.5f - v;
-  if (lx <= 0.f && hx >= 0.f && ly <= 0.f && hy >= 0.f) return false;
-  const float s = fminf(fminf(edge_min_sigma(lx, ly, hy, A, B, C), edge_min_sigma(hx, ly, hy, A, B, C)),
-                        fminf(edge_min_sigma(ly, lx, hx, C, B, A), edge_min_sigma(hy, lx, hx, C, B, A)));
-  return s > __logf(255.f * o) + 1e-3f;
+  return box_min_sigma(x0 + 0.5f, y0 + 0.5f, x0 + 15.5f, y0 + 15.5f, u, v, A, B, C) > sigma_cut(o);
 }
 
 // Ordered compaction of one flag per thread over a 256-thread block.  Returns the

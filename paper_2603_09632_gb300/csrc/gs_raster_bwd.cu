@@ -136,6 +136,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   __shared__ int s_orig[kT];                        // list position of each compacted entry
   __shared__ float4 s_E4[kT];                       // (g_r, g_g, g_b, g_depth) per pixel
   __shared__ int s_wc[8];
+  __shared__ unsigned s_live[8];                    // per warp strip: batch entries that can reach it
   __shared__ uint32_t s_maxn;
   extern __shared__ __align__(16) float smem[];
   float* s_E = smem;                          // [kT][ES]
@@ -160,6 +161,9 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     const int px = tx0 + (t & 15), py = ty0 + (t >> 4);
     const bool inside = px < cam.W && py < cam.H;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int lane = t & 31;
+    // pixel-centre box of this warp's 16 x 2 strip
+    const float wbx0 = (float)tx0 + 0.5f, wby0 = (float)(ty0 + 2 * (t >> 5)) + 0.5f;
     const int64_t HW = (int64_t)cam.W * cam.H;
     const int64_t p = (int64_t)py * cam.W + px;
     const uint2 rg = ranges[tile];
@@ -213,7 +217,9 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       if (t < c1 - c0) id = inst_id[start + c0 + t];
       if (t < c1 - c0 && id < (uint32_t)cam.n_gauss) {
         g = rec[id];
-        keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
+        g.r1.w = sigma_cut(g.r1.y);
+        keep = box_min_sigma((float)tx0 + 0.5f, (float)ty0 + 0.5f, (float)tx0 + 15.5f,
+                             (float)ty0 + 15.5f, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x) <= g.r1.w;
       }
       int nk;
       const int pos = block_compact_index(keep, s_wc, &nk);
@@ -237,14 +243,23 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         const int jb0 = max(0, jb1 - B), bc = jb1 - jb0;
         const float* s_f = s_fb + (bi & 1) * B * DP;
 
+        // entries of the batch that can reach this warp's 16 x 2 pixel strip
+        bool hit = false;
+        if (lane < bc) {
+          const float4 q0 = s_r0[jb0 + lane], q1 = s_r1[jb0 + lane];
+          hit = box_min_sigma(wbx0, wby0, wbx0 + 15.f, wby0 + 1.f, q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
+        }
+        const unsigned live = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) s_live[t >> 5] = live;   // phase 2 skips (Gaussian, strip) pairs not live
+
         // phase 1: per pixel, reverse over the batch
         for (int j = B - 1; j >= 0; --j) {
           float w = 0.f, gs = 0.f, go = 0.f;
-          if (j < bc && s_orig[jb0 + j] < nc) {
+          if ((live >> j & 1u) && s_orig[jb0 + j] < nc) {
             const float4 r0 = s_r0[jb0 + j];
             const float4 r1 = s_r1[jb0 + j];
             const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-            if (sigma >= 0.f) {
+            if (sigma >= 0.f && sigma <= r1.w) {
               const float G = blend_gauss(sigma);
               const float oG = __fmul_rn(r1.y, G);
               const float a = fminf(kAlphaMax, oG);
@@ -274,9 +289,11 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
               }
             }
           }
-          s_W[j * kWS + t] = w;
-          s_GS[j * kWS + t] = gs;
-          s_GO[j * kWS + t] = go;
+          if (live >> j & 1u) {   // entries not live for this strip are never read
+            s_W[j * kWS + t] = w;
+            s_GS[j * kWS + t] = gs;
+            s_GO[j * kWS + t] = go;
+          }
         }
         __syncthreads();
 
@@ -298,12 +315,15 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             for (int a = 0; a < 4; ++a)
   #pragma unroll
               for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-            const int p0 = part * PP;
+            const int p0 = part * PP;                     // the part lies in one warp strip
+            const unsigned lv = (s_live[p0 >> 5] >> (4 * jb)) & 15u;
   #pragma unroll 2
-            for (int q = p0; q < p0 + PP; q += 4) {
+            for (int q = p0; q < (lv ? p0 + PP : p0); q += 4) {
               float4 wv[4], ev[4];
   #pragma unroll
-              for (int a = 0; a < 4; ++a) wv[a] = *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q);
+              for (int a = 0; a < 4; ++a)
+                wv[a] = (lv >> a & 1u) ? *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
   #pragma unroll
               for (int b = 0; b < 4; ++b) ev[b] = *reinterpret_cast<const float4*>(s_E + (q + b) * Cfg::ES + 4 * cb);
   #pragma unroll
@@ -322,10 +342,11 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             for (int a = 0; a < 4; ++a)
   #pragma unroll
               for (int b = 0; b < 4; ++b) {
-                if (Cfg::S > 1)
-                  atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
-                else
+                if (Cfg::S > 1) {
+                  if (lv >> a & 1u) atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
+                } else {
                   s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
+                }
               }
           }
         }
@@ -339,6 +360,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   #pragma unroll 4
           for (int k = 0; k < kT / G; ++k) {
             const int q = pg + k * G;
+            if (!(s_live[q >> 5] >> j & 1u)) continue;   // uniform over the G lanes of j
             const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
             const float4 e = s_E4[q];
             const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;

@@ -91,6 +91,9 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
     const uint2 rg = ranges[tile];
     const int start = (int)rg.x, end = (int)rg.y;
+    const int lane = threadIdx.x & 31;
+    // pixel-centre box of this warp's 16 x 2 strip
+    const float wbx0 = (float)tx0 + 0.5f, wby0 = (float)(ty0 + 2 * (threadIdx.x >> 5)) + 0.5f;
 
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
     float acc[DP > 0 ? DP : 1];
@@ -109,13 +112,15 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       if ((int)threadIdx.x < cnt) id = inst_id[b0 + threadIdx.x];
       if ((int)threadIdx.x < cnt && id < (uint32_t)cam.n_gauss) {
         g = rec[id];
-        keep = !tile_culled((float)tx0, (float)ty0, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x, g.r1.y);
+        g.r1.w = sigma_cut(g.r1.y);
+        keep = box_min_sigma((float)tx0 + 0.5f, (float)ty0 + 0.5f, (float)tx0 + 15.5f,
+                             (float)ty0 + 15.5f, g.r0.x, g.r0.y, g.r0.z, g.r0.w, g.r1.x) <= g.r1.w;
       }
       int nk;
       const int pos = block_compact_index(keep, s_wc, &nk);
       if (keep) {
         s_r0[pos] = g.r0;
-        s_r1[pos] = g.r1;
+        s_r1[pos] = g.r1;      // r1.w = sigma cut
         s_r2[pos] = g.r2;
         s_id[pos] = id;
         s_orig[pos] = b0 + (int)threadIdx.x - start;
@@ -123,14 +128,25 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       __syncthreads();
       stage_features<DP, BF16>(feats, D, s_id, nk, s_feat);
       __syncthreads();
-      for (int j = 0; j < nk; ++j) {
+      // each warp (a 16 x 2 pixel strip) visits only the entries that can reach its strip:
+      // the lanes test 32 entries at a time and the ballot lists the survivors
+      for (int g0 = 0; g0 < nk; g0 += 32) {
         if (__all_sync(0xffffffffu, done)) break;
+        bool hit = false;
+        if (g0 + lane < nk) {
+          const float4 q0 = s_r0[g0 + lane], q1 = s_r1[g0 + lane];
+          hit = box_min_sigma(wbx0, wby0, wbx0 + 15.f, wby0 + 1.f, q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
+        }
+        unsigned live = __ballot_sync(0xffffffffu, hit);
+      while (live) {
+        const int j = g0 + __ffs(live) - 1;
+        live &= live - 1;
         const float4 r0 = s_r0[j];
         const float4 r1 = s_r1[j];
         float w = 0.f;
         if (!done) {
           const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-          if (sigma >= 0.f) {
+          if (sigma >= 0.f && sigma <= r1.w) {
             const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
             if (a >= kAlphaMin) {
               const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
@@ -162,6 +178,8 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             }
           }
         }
+        if (__all_sync(0xffffffffu, done)) live = 0u;
+      }
       }
     }
     if (inside) {
