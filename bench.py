@@ -527,6 +527,222 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+SERVE_RATES = (0.25, 0.5, 1.0, 1.5, 2.0)
+
+
+def wait_until(t):
+    """Sleep until perf_counter() reaches t (spinning only for the last 0.2 ms, so that
+    other Python threads keep running)."""
+    while True:
+        d = t - time.perf_counter()
+        if d <= 0:
+            return
+        time.sleep(d - 2e-4) if d > 4e-4 else time.sleep(0)
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs, np.float64), q)) if len(xs) else float("nan")
+
+
+def run_serve(args):
+    """Serving mix: 8 resident scenes (100k-2M Gaussians, SH = id mod 4, 16/32/64 bf16
+    feature channels), Poisson arrivals of single-pose requests at resolutions drawn from
+    {256x256, 640x480, 1200x680, 1920x1080}, 30 % with backward.  Two arms on the same
+    request sequence and arrival times:
+      plain: one request at a time through gs_project -> gs_bin_tiles -> gs_render_fwd
+             (-> gs_render_bwd) on one stream, synchronised per request;
+      serve: the serving loop (gs_serve_submit / gs_serve_poll) with --serve-slots slots.
+    The rate is swept from 0.25x to 2x the plain arm's closed-loop capacity.  Latency runs
+    from the scheduled arrival to poll-visible completion (so time a request waits for a
+    client buffer counts); throughput is served pixels over first arrival -> last
+    completion."""
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    from paper_2603_09632_gb300.render import as_camera
+
+    rank, world, local = env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scenes_np = S.serving_scenes(scale=args.serve_scale)
+    scenes = []
+    for sc in scenes_np:
+        t = [torch.from_numpy(np.ascontiguousarray(getattr(sc, k), np.float32)).to(dev)
+             for k in ("means", "scales", "quats", "opacities", "sh")]
+        ft = torch.from_numpy(np.ascontiguousarray(sc.feats, np.float32)).to(dev).to(torch.bfloat16)
+        scenes.append(L.Scene(*t, ft))
+    reqs = S.serving_requests(args.serve_requests, 1.0)     # arrival times at 1 request/s
+    max_pix = max(c.W * c.H for _, _, c, _ in reqs)
+    max_d = max(sc.n_feat for sc in scenes_np)
+    max_n = max(sc.n for sc in scenes_np)
+
+    def align(x):
+        return (x + 63) // 64 * 64
+
+    out_floats = align(5 * max_pix) + align(max_d * max_pix)
+    g_floats = align(max_n * 3) * 2 + align(max_n * 4) + align(max_n) + align(max_n * 48) \
+        + align(max_n * max_d) + 64
+    n_sets = 4 * args.serve_slots
+    pool = [(torch.empty(out_floats, device=dev), torch.empty(g_floats, device=dev))
+            for _ in range(n_sets)]
+    # upstream gradients per resolution (read-only, shared by every request)
+    ups = {}
+    for _, _, c, _ in reqs:
+        if (c.W, c.H) not in ups:
+            g = S.upstream_grads(c.H, c.W, max_d)
+            ups[(c.W, c.H)] = {k: torch.from_numpy(v).to(dev) for k, v in g.items()}
+
+    def views(k, sid, cam, want_bwd):
+        ob, gb = pool[k]
+        P, D, n = cam.W * cam.H, scenes_np[sid].n_feat, scenes_np[sid].n
+        Kc = (scenes_np[sid].sh_degree + 1) ** 2
+        out = dict(rgb=ob[:3 * P].view(3, cam.H, cam.W), depth=ob[3 * P:4 * P].view(cam.H, cam.W),
+                   alpha=ob[4 * P:5 * P].view(cam.H, cam.W),
+                   feat=ob[align(5 * P):align(5 * P) + D * P].view(D, cam.H, cam.W))
+        if not want_bwd:
+            return out, None, None
+        u = ups[(cam.W, cam.H)]
+        gin = dict(rgb=u["rgb"], depth=u["depth"], alpha=u["alpha"], feat=u["feat"][:D])
+        o, gout = 0, {}
+        for name, m in (("means", 3), ("scales", 3), ("quats", 4), ("opacities", 1), ("sh", Kc * 3),
+                        ("feats", D), ("pose", 0)):
+            sz = 6 if name == "pose" else n * m
+            gout[name] = gb[o:o + sz]
+            o += align(sz)
+        return out, gin, gout
+
+    cams = [as_camera(c) for _, _, c, _ in reqs]
+    pixels = [c.W * c.H for _, _, c, _ in reqs]
+    ws = L.Workspace(local)
+    L.gs_workspace_reserve(ws, max_n, 0, max_pix)
+    stream = torch.cuda.current_stream()
+
+    def plain_one(i):
+        _, sid, cam, bwd = reqs[i]
+        out, gin, gout = views(i % n_sets, sid, cam, bwd)
+        sc = scenes[sid]
+        L.gs_project(sc, cams[i], ws, stream)
+        L.gs_bin_tiles(ws, sync=True, stream=stream)
+        L.gs_render_fwd(sc, cams[i], ws, out["rgb"], out["depth"], out["alpha"], out["feat"], stream)
+        if bwd:
+            L.gs_render_bwd(sc, cams[i], ws, gin["rgb"], gin["depth"], gin["alpha"], gin["feat"],
+                            gout["means"], gout["scales"], gout["quats"], gout["opacities"],
+                            gout["sh"], gout["feats"], gout["pose"], stream)
+        stream.synchronize()
+
+    # warm-up and plain closed-loop capacity
+    for i in range(min(len(reqs), 3 * args.warmup)):
+        plain_one(i)
+    m = min(len(reqs), args.serve_capacity_requests)
+    t0 = time.perf_counter()
+    for i in range(m):
+        plain_one(i)
+    t_cap = time.perf_counter() - t0
+    cap_rps = m / t_cap
+    cap_mpix = sum(pixels[:m]) / t_cap / 1e6
+
+    def plain_open(rate):
+        lat, t0 = [], time.perf_counter()
+        last = t0
+        for i, (ta, _, _, _) in enumerate(reqs):
+            arrive = t0 + ta / rate
+            wait_until(arrive)
+            plain_one(i)
+            last = time.perf_counter()
+            lat.append(last - arrive)
+        return lat, last - (t0 + reqs[0][0] / rate)
+
+    server = L.Server(int(args.serve_budget_gb * (1 << 30)), args.serve_slots, local)
+    ids = [L.gs_serve_add_scene(server, sc) for sc in scenes]
+
+    def serve_open(rate, n_req=None):
+        n_req = len(reqs) if n_req is None else n_req
+        free = list(range(n_sets))
+        cv = threading.Condition()
+        outstanding = {}      # ticket -> (i, set, t_submit, arrive)
+        lat = [None] * n_req
+        fail = []
+        done_flag = [False]
+
+        def poller():
+            while True:
+                with cv:
+                    items = list(outstanding.items())
+                    if not items and done_flag[0]:
+                        return
+                got = False
+                for t, (i, k, ts, ta) in items:
+                    st, res = L.gs_serve_poll(server, t, 0)
+                    if st == L.GS_OK:
+                        got = True
+                        if res["status"] != L.GS_OK:
+                            fail.append((i, res["status"]))
+                        lat[i] = (ts - ta) + res["latency_us"] * 1e-6
+                        with cv:
+                            del outstanding[t]
+                            free.append(k)
+                            cv.notify_all()
+                if not got:
+                    time.sleep(50e-6)
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            ta, sid, cam, bwd = reqs[i]
+            arrive = t0 + ta / rate
+            wait_until(arrive)
+            with cv:
+                while not free:
+                    cv.wait()
+                k = free.pop()
+            out, gin, gout = views(k, sid, cam, bwd)
+            ts = time.perf_counter()
+            st, t = L.gs_serve_submit(server, L.make_request(ids[sid], cams[i], out, gin, gout))
+            if st != L.GS_OK:
+                raise RuntimeError(f"gs_serve_submit: {L.status_string(st)}")
+            with cv:
+                outstanding[t] = (i, k, ts, arrive)
+        with cv:
+            done_flag[0] = True
+        th.join()
+        if fail:
+            raise RuntimeError(f"served requests failed: {fail[:4]}")
+        first = t0 + reqs[0][0] / rate
+        last = max(t0 + reqs[i][0] / rate + lat[i] for i in range(n_req))
+        return lat, last - first
+
+    serve_open(cap_rps, min(len(reqs), 4 * args.serve_slots))     # warm the slots
+    rows = []
+    for x in SERVE_RATES:
+        rate = x * cap_rps
+        lp, tp = plain_open(rate)
+        ls, tsv = serve_open(rate)
+        px = sum(pixels)
+        rows.append({"x_capacity": x, "rate_rps": round(rate, 2),
+                     "plain": {"mpix_s": round(px / tp / 1e6, 2), "p50_ms": round(1e3 * _pct(lp, 50), 3),
+                               "p99_ms": round(1e3 * _pct(lp, 99), 3)},
+                     "serve": {"mpix_s": round(px / tsv / 1e6, 2), "p50_ms": round(1e3 * _pct(ls, 50), 3),
+                               "p99_ms": round(1e3 * _pct(ls, 99), 3)}})
+    info = L.gs_serve_info(server)
+    server.close()
+    top = rows[-1]
+    line = {"metric": "serving Mpix/s with p50/p99 latency, mixed scenes/resolutions, 30% fwd+bwd",
+            "value": top["serve"]["mpix_s"], "unit": "Mpix/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32 (bf16 features)", "data": "synthetic",
+            "plain_capacity": {"rps": round(cap_rps, 2), "mpix_s": round(cap_mpix, 2), "requests": m},
+            "sweep": rows,
+            "config": {"workload": "serve_mix_8_scenes", "scenes": [
+                {"n": sc.n, "sh": sc.sh_degree, "feat": sc.n_feat} for sc in scenes_np],
+                "requests": len(reqs), "slots": args.serve_slots,
+                "budget_gb": args.serve_budget_gb, "client_buffer_sets": n_sets,
+                "resolutions": sorted({(c.W, c.H) for _, _, c, _ in reqs}),
+                "bwd_fraction": round(sum(r[3] for r in reqs) / len(reqs), 3)},
+            "server": info}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -537,11 +753,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cpu-tiles", type=int, default=300)
+    ap.add_argument("--serve", action="store_true", help="serving-loop benchmark instead")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-capacity-requests", type=int, default=100)
+    ap.add_argument("--serve-budget-gb", type=float, default=48.0)
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="scale of the scene sizes")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_gpu(args)
 

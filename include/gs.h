@@ -47,7 +47,8 @@ typedef enum {
   GS_ERR_TIMEOUT = 5,      /* a bounded wait expired */
   GS_ERR_BUSY = 6,         /* request not finished yet (serving poll) */
   GS_ERR_OVER_BUDGET = 7,  /* request cannot fit the serving memory budget */
-  GS_ERR_STATE = 8         /* calls out of order (e.g. render before project/bin) */
+  GS_ERR_STATE = 8,        /* calls out of order (e.g. render before project/bin) */
+  GS_ERR_CANCELLED = 9     /* serving request cancelled before it started */
 } gs_status;
 
 typedef enum { GS_F32 = 0, GS_BF16 = 1 } gs_dtype;
@@ -201,6 +202,72 @@ gs_status gs_timing_collect(gs_workspace* ws, double* ms_out, int64_t* count_out
 /* Number of CUDA kernels this library has launched in the process so far (all
  * workspaces, all devices).  Host-side counter; no synchronisation. */
 int64_t gs_launch_count(void);
+
+/* ---- serving ----------------------------------------------------------------------
+ *
+ * Keeps several scenes resident on one GPU and renders requests (forward, optionally
+ * backward) with continuous admission: each of max_slots slots is a host worker with
+ * its own CUDA stream and workspace; a free slot takes the oldest pending request whose
+ * device-memory estimate fits what is left of the HBM budget, so requests that arrive
+ * while others run are admitted as slots and memory free up and their kernels overlap
+ * on the device.  The Perceiver renders many views of the same map (tracking, mapping
+ * over a keyframe window, semantic phases; Sec. 3.2, Eq. 2-3); serving is the systems
+ * form of that load.  A request's results equal those of the same request rendered
+ * alone (forward bit for bit; backward up to the order of atomic additions).
+ * Host-side waits are bounded by the caller's timeout; no kernel waits on another. */
+typedef struct gs_server gs_server;
+
+typedef struct {
+  int32_t scene_id;       /* from gs_serve_add_scene */
+  gs_camera cam;
+  int32_t want_bwd;       /* 1: also run gs_render_bwd */
+  /* caller-owned device outputs, as for gs_render_fwd (any may be NULL) */
+  float *rgb, *depth, *alpha, *feat;
+  /* when want_bwd: upstream gradients and gradient outputs, as for gs_render_bwd */
+  const float *g_rgb, *g_depth, *g_alpha, *g_feat;
+  float *g_means, *g_scales, *g_quats, *g_opac, *g_sh, *g_feats, *g_pose6;
+} gs_request;
+
+typedef struct {
+  gs_status status;       /* outcome of the request */
+  int32_t slot;           /* slot that ran it (-1 if it never started) */
+  int64_t instances;      /* tile instances of its binning */
+  double queue_us;        /* submit -> start */
+  double run_us;          /* start -> results ready on the device */
+  double latency_us;      /* submit -> results ready */
+} gs_result;
+
+/* Create a server on `device` with a device-memory budget (bytes) shared by resident
+ * scenes and in-flight requests, and max_slots (1..64) concurrent slots.
+ * Errors: GS_ERR_ARG, GS_ERR_CUDA. */
+gs_status gs_serve_create(gs_server** server, int device, int64_t hbm_budget_bytes, int max_slots);
+
+/* Cancel pending requests, wait for running ones, free everything. */
+void gs_serve_destroy(gs_server* server);
+
+/* Copy a scene (device pointers, as for gs_project) into server-owned device memory.
+ * *scene_id receives its id.  GS_ERR_OVER_BUDGET if it does not fit the budget. */
+gs_status gs_serve_add_scene(gs_server* server, const gs_scene* scene, int* scene_id);
+
+/* Queue a request; *ticket identifies it.  The request struct is copied; its buffers
+ * must stay valid until the request is polled.  GS_ERR_OVER_BUDGET if its memory
+ * estimate can never fit the budget; GS_ERR_ARG for an unknown scene or bad camera. */
+gs_status gs_serve_submit(gs_server* server, const gs_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_us (0: do not wait; negative: wait without limit) for a request.
+ * GS_OK with *result filled (result->status is the request's own outcome) and the
+ * ticket released; GS_ERR_BUSY if not finished in time; GS_ERR_ARG for an unknown or
+ * already released ticket. */
+gs_status gs_serve_poll(gs_server* server, uint64_t ticket, int64_t timeout_us, gs_result* result);
+
+/* Cancel a request that has not started (its result status becomes GS_ERR_CANCELLED);
+ * GS_ERR_BUSY if it is running or finished. */
+gs_status gs_serve_cancel(gs_server* server, uint64_t ticket);
+
+/* Memory held by resident scenes, admission estimate of the requests running now and
+ * its peak, and the peak number of requests running at once (any may be NULL). */
+gs_status gs_serve_info(gs_server* server, int64_t* scene_bytes, int64_t* in_flight_bytes,
+                        int64_t* peak_in_flight_bytes, int32_t* peak_running);
 
 /* ---- rendering without allocation ------------------------------------------------
  *

@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libgs.so")
 
 GS_OK, GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA, GS_ERR_DEVICE = 0, 1, 2, 3, 4
-GS_ERR_TIMEOUT, GS_ERR_BUSY, GS_ERR_OVER_BUDGET, GS_ERR_STATE = 5, 6, 7, 8
+GS_ERR_TIMEOUT, GS_ERR_BUSY, GS_ERR_OVER_BUDGET, GS_ERR_STATE, GS_ERR_CANCELLED = 5, 6, 7, 8, 9
 GS_F32, GS_BF16 = 0, 1
 GS_TIMER_NAMES = ("project", "bin", "fwd", "bwd_raster", "bwd_project")
 GS_NUM_TIMERS = len(GS_TIMER_NAMES)
@@ -41,6 +41,20 @@ class gs_scene(C.Structure):
                 ("feat_dtype", C.c_int32), ("means", C.c_void_p), ("scales", C.c_void_p),
                 ("quats", C.c_void_p), ("opacities", C.c_void_p), ("sh", C.c_void_p),
                 ("feats", C.c_void_p)]
+
+
+class gs_request(C.Structure):
+    _fields_ = [("scene_id", C.c_int32), ("cam", gs_camera), ("want_bwd", C.c_int32),
+                ("rgb", C.c_void_p), ("depth", C.c_void_p), ("alpha", C.c_void_p), ("feat", C.c_void_p),
+                ("g_rgb", C.c_void_p), ("g_depth", C.c_void_p), ("g_alpha", C.c_void_p),
+                ("g_feat", C.c_void_p), ("g_means", C.c_void_p), ("g_scales", C.c_void_p),
+                ("g_quats", C.c_void_p), ("g_opac", C.c_void_p), ("g_sh", C.c_void_p),
+                ("g_feats", C.c_void_p), ("g_pose6", C.c_void_p)]
+
+
+class gs_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("slot", C.c_int32), ("instances", C.c_int64),
+                ("queue_us", C.c_double), ("run_us", C.c_double), ("latency_us", C.c_double)]
 
 
 class gs_stats(C.Structure):
@@ -74,6 +88,13 @@ def _load():
         "gs_timing_collect": ([P, P, P], st),
         "gs_launch_count": ([], i64),
         "gs_render_fwd_noalloc": ([P, P, P, P, P, P, P], st),
+        "gs_serve_create": ([C.POINTER(C.c_void_p), i32, i64, i32], st),
+        "gs_serve_destroy": ([P], None),
+        "gs_serve_add_scene": ([P, P, C.POINTER(C.c_int)], st),
+        "gs_serve_submit": ([P, P, C.POINTER(C.c_uint64)], st),
+        "gs_serve_poll": ([P, C.c_uint64, i64, P], st),
+        "gs_serve_cancel": ([P, C.c_uint64], st),
+        "gs_serve_info": ([P, P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -272,6 +293,81 @@ def gs_get_pixel_state(ws, H, W, stream=None):
     _check(lib.gs_get_pixel_state(ws.h, P(T.ctypes.data), P(nc.ctypes.data), _stream(stream)),
            "gs_get_pixel_state")
     return T, nc
+
+
+class Server:
+    """Serving loop (gs_serve_*): resident scenes, continuous admission by an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes, max_slots, device=None):
+        dev = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        _check(lib.gs_serve_create(C.byref(h), dev, int(hbm_budget_bytes), int(max_slots)),
+               "gs_serve_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib.gs_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gs_serve_add_scene(server, scene):
+    sid = C.c_int()
+    _check(lib.gs_serve_add_scene(server.h, C.byref(scene.c), C.byref(sid)), "gs_serve_add_scene")
+    return int(sid.value)
+
+
+def make_request(scene_id, cam, outputs, grads_in=None, grads_out=None):
+    """gs_request from dicts of device tensors (outputs: rgb/depth/alpha/feat; grads_in:
+    rgb/depth/alpha/feat upstream; grads_out: means/scales/quats/opacities/sh/feats/pose)."""
+    r = gs_request()
+    r.scene_id, r.cam, r.want_bwd = int(scene_id), cam, int(grads_in is not None)
+    for k in ("rgb", "depth", "alpha", "feat"):
+        setattr(r, k, outputs[k].data_ptr() if outputs.get(k) is not None else None)
+    if grads_in is not None:
+        for k in ("rgb", "depth", "alpha", "feat"):
+            v = grads_in.get(k)
+            setattr(r, "g_" + k, v.data_ptr() if v is not None else None)
+        names = dict(means="g_means", scales="g_scales", quats="g_quats", opacities="g_opac",
+                     sh="g_sh", feats="g_feats", pose="g_pose6")
+        for k, f in names.items():
+            v = grads_out.get(k)
+            setattr(r, f, v.data_ptr() if v is not None else None)
+    return r
+
+
+def gs_serve_submit(server, req):
+    """Returns (status, ticket); the status is not raised so callers can see refusals."""
+    t = C.c_uint64()
+    s = lib.gs_serve_submit(server.h, C.byref(req), C.byref(t))
+    return int(s), int(t.value)
+
+
+def gs_serve_poll(server, ticket, timeout_us=-1):
+    """Returns (status, result dict or None); GS_ERR_BUSY when not finished in time."""
+    r = gs_result()
+    s = lib.gs_serve_poll(server.h, C.c_uint64(ticket), int(timeout_us), C.byref(r))
+    if s != GS_OK:
+        return int(s), None
+    return GS_OK, {k: getattr(r, k) for k, _ in gs_result._fields_}
+
+
+def gs_serve_cancel(server, ticket):
+    return int(lib.gs_serve_cancel(server.h, C.c_uint64(ticket)))
+
+
+def gs_serve_info(server):
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    d = C.c_int32()
+    _check(lib.gs_serve_info(server.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "gs_serve_info")
+    return dict(scene_bytes=a.value, in_flight_bytes=b.value, peak_in_flight_bytes=c.value,
+                peak_running=d.value)
 
 
 def gs_render_fwd_noalloc(scene, cam, rgb=None, depth=None, alpha=None, feat=None, stream=None):

@@ -23,10 +23,12 @@ struct DevBuf {
   size_t cap = 0;   // elements
   cudaError_t ensure(size_t n) {
     if (n <= cap) return cudaSuccess;
+    // a buffer that has to grow grows by at least a quarter, so that sizes drifting upwards
+    // (instance counts over a trajectory) do not reallocate (and synchronise) every call
+    const size_t m = std::max<size_t>(std::max<size_t>(n, 16), cap + cap / 4);
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
-    const size_t m = std::max<size_t>(n, 16);
     cudaError_t e = cudaMalloc(&p, m * sizeof(T));
     if (e == cudaSuccess) cap = m;
     return e;
@@ -187,7 +189,7 @@ cudaError_t ensure_gauss(gs_workspace* ws, int64_t n) {
       (e = ws->g2d.ensure(m * kG2D)) ||
       (e = ws->pose_partials.ensure((size_t)project_bwd_blocks(n) * 8)))
     return e;
-  return ensure_status(ws, n);
+  return ensure_status(ws, (int64_t)ws->rec.cap);
 }
 
 cudaError_t ensure_inst(gs_workspace* ws, int64_t cap) {
@@ -196,7 +198,8 @@ cudaError_t ensure_inst(gs_workspace* ws, int64_t cap) {
   if ((e = ws->inst_tile.ensure(m)) || (e = ws->inst_id.ensure(m)) ||
       (e = ws->inst_tile2.ensure(m)) || (e = ws->inst_id2.ensure(m)))
     return e;
-  return ensure_status(ws, cap);
+  // the tile sort may run over every allocated instance slot (no-sync binning)
+  return ensure_status(ws, (int64_t)ws->inst_tile.cap);
 }
 
 cudaError_t ensure_pix(gs_workspace* ws, int64_t npix, int64_t ntiles) {
@@ -223,6 +226,7 @@ const char* gs_status_string(gs_status s) {
     case GS_ERR_BUSY: return "busy";
     case GS_ERR_OVER_BUDGET: return "over memory budget";
     case GS_ERR_STATE: return "calls out of order";
+    case GS_ERR_CANCELLED: return "cancelled";
   }
   return "unknown status";
 }
