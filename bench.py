@@ -39,6 +39,14 @@ WORKLOADS = {
     "memory_3840x2160_3m": dict(make=lambda: S.config_memory(n_poses=10), bf16=False, l1=False,
                                 desc="room 3M Gaussians, SH0, 32 fp32 feats, 3840x2160, fx=3600"),
 }
+# Semantic distillation phase (Sec. 3.2, App. D): grid-sampled rendering with random offsets,
+# region-indexed targets, the masked L1 + cosine loss fused into the forward, and the
+# features-only backward (geometry frozen).  Stride 1 is the same phase at full resolution.
+for _s in (1, 2, 4):
+    WORKLOADS[f"semantic_grid_s{_s}_1200x680_1m"] = dict(
+        make=lambda: S.config_semantic(n_poses=100), bf16=True, l1=False, grid=_s,
+        desc=f"room 1M Gaussians, SH3, 64 bf16 feats, 1200x680, grid stride {_s} (random offsets), "
+             "region targets, fused masked L1+cos loss, features-only backward")
 DEFAULT_WORKLOAD = "slam_640x480_200k"
 METRIC = "Mpix/s fwd+bwd (RGB+D+feat) at 1 GB300"
 L2_FLUSH_BYTES = 256 << 20
@@ -70,6 +78,34 @@ def stage_bytes(st, D, bf, K):
         "fwd": Ie * (44 + D * bf) + pix_io,
         "bwd_raster": pix_io + Ie * (44 + D * bf) + V * (40 + 4 * D),
         "bwd_project": V * (40 + 44 + 12 * K) + V * (44 + 12 * K) + 24,
+    }
+
+
+def stage_bytes_semantic(st, D, bf):
+    """Byte model of the semantic-phase step: the forward reads the target and mask and
+    writes dL/dG_hat instead of images; the features-only backward reads that gradient and
+    adds into the feature gradients."""
+    V, I, Ie, P = st["visible"], st["instances"], st["inst_eff"], st["pixels"]
+    return {
+        "project": st["n"] * 44 + V * (12 * 16 + 48),
+        "bin": I * 36,
+        "fwd": Ie * (44 + D * bf) + P * (4 * D + 4 + 4 * D + 8),
+        "bwd_raster": P * (4 * D + 8) + Ie * (44 + D * bf) + V * 4 * D,
+        "bwd_project": 0,
+    }
+
+
+def stage_flops_semantic(st, D):
+    """FLOP model of the semantic-phase step: per evaluated pair ~12 FLOPs (sigma, alpha,
+    transmittance), per blended pair 2D (feature blend, or the W^T g_F contraction), and
+    ~10D per sample for the fused loss."""
+    V, E, Eb, P = st["visible"], st["pairs_eval"], st["pairs_blend"], st["pixels"]
+    return {
+        "project": V * (150 + 6 * 16),
+        "bin": 0,
+        "fwd": 12 * E + 2 * D * Eb + 10 * D * P,
+        "bwd_raster": 12 * E + 2 * D * Eb,
+        "bwd_project": 0,
     }
 
 
@@ -235,6 +271,41 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 
+def build_roofline(stage, sb_tot, sf_tot, pairs, steps, workload):
+    """Roofline of the dominant stage: algorithmic bytes and FLOPs per launch (summed over
+    the timed poses in sb_tot / sf_tot) against the measured stage time; the binding
+    bound is whichever of the HBM and FP32 times is larger."""
+    stage_ms = {name: stage[name][0] / max(stage[name][1], 1) for name in stage}
+    dom = max(stage_ms, key=stage_ms.get)
+    peaks, src = load_peaks()
+    alg_b = sb_tot[dom] / steps
+    alg_f = sf_tot[dom] / steps
+    p_alu = fp32_peak_tflops(peaks)
+    t_hbm = alg_b / (peaks["hbm_gbs"] * 1e9)
+    t_alu = alg_f / (p_alu * 1e12)
+    t_meas = stage_ms[dom] * 1e-3
+    traffic = captured_traffic(dom, workload)
+    if t_alu > t_hbm:
+        achieved = alg_f / t_meas / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(p_alu, 1),
+                    "unit": "TFLOP/s", "frac": round(achieved / p_alu, 4),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
+    else:
+        achieved = alg_b / t_meas / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                    "peak_source": src}
+    roofline.update({
+        "traffic": traffic, "alg_bytes": int(alg_b), "alg_flops": int(alg_f),
+        "hbm_frac": round(alg_b / t_meas / 1e9 / peaks["hbm_gbs"], 4),
+        "alu_frac": round(alg_f / t_meas / 1e12 / p_alu, 4),
+        "pairs_eval_per_step": int(pairs[0] / steps), "pairs_blend_per_step": int(pairs[1] / steps),
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_alg_mb": {k: round(v / steps / 1e6, 3) for k, v in sb_tot.items()},
+        "stage_alg_gflop": {k: round(v / steps / 1e9, 3) for k, v in sf_tot.items()}})
+    return roofline
+
+
 def run_gpu(args):
     import torch
     from paper_2603_09632_gb300 import _lib as L
@@ -347,34 +418,7 @@ def run_gpu(args):
             sb_tot[name] = sb_tot.get(name, 0.0) + b
         for name, f in stage_flops(st, D, K).items():
             sf_tot[name] = sf_tot.get(name, 0.0) + f
-    stage_ms = {name: stage[name][0] / max(stage[name][1], 1) for name in stage}
-    dom = max(stage_ms, key=stage_ms.get)
-    peaks, src = load_peaks()
-    alg_b = sb_tot[dom] / args.steps
-    alg_f = sf_tot[dom] / args.steps
-    p_alu = fp32_peak_tflops(peaks)
-    t_hbm = alg_b / (peaks["hbm_gbs"] * 1e9)
-    t_alu = alg_f / (p_alu * 1e12)
-    t_meas = stage_ms[dom] * 1e-3
-    traffic = captured_traffic(dom, args.workload)
-    if t_alu > t_hbm:
-        achieved = alg_f / t_meas / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(p_alu, 1),
-                    "unit": "TFLOP/s", "frac": round(achieved / p_alu, 4),
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
-    else:
-        achieved = alg_b / t_meas / 1e9
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                    "peak_source": src}
-    roofline.update({
-        "traffic": traffic, "alg_bytes": int(alg_b), "alg_flops": int(alg_f),
-        "hbm_frac": round(alg_b / t_meas / 1e9 / peaks["hbm_gbs"], 4),
-        "alu_frac": round(alg_f / t_meas / 1e12 / p_alu, 4),
-        "pairs_eval_per_step": int(pairs[0] / args.steps), "pairs_blend_per_step": int(pairs[1] / args.steps),
-        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "stage_alg_mb": {k: round(v / args.steps / 1e6, 3) for k, v in sb_tot.items()},
-        "stage_alg_gflop": {k: round(v / args.steps / 1e9, 3) for k, v in sf_tot.items()}})
+    roofline = build_roofline(stage, sb_tot, sf_tot, pairs, args.steps, args.workload)
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, L, scene_np, gcams, poses, wl, dev, stream, ws, K, D, fdt, H, W)
@@ -447,6 +491,171 @@ def run_e2e(args, L, scene_np, gcams, poses, wl, dev, stream, ws, K, D, fdt, H, 
             "ms_per_step": round(ms / args.steps, 4)}
 
 
+def run_grid(args):
+    """Semantic distillation phase on the sample grid: per step project -> bin (no sync) ->
+    region targets on the grid -> forward with the fused masked L1 + cosine loss ->
+    features-only backward.  Offsets are drawn per step from {0..s-1}^2 (seeded)."""
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    from paper_2603_09632_gb300.render import as_camera, grid_shape
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = WORKLOADS[args.workload]
+    stride = wl["grid"]
+    scene_np, cams = wl["make"]()
+    D = scene_np.n_feat
+    bf = 2 if wl["bf16"] else 4
+    H, W = cams[0].H, cams[0].W
+    fdt = torch.bfloat16 if wl["bf16"] else torch.float32
+
+    def dev_t(a, dtype=torch.float32):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev).to(dtype)
+
+    scene = L.Scene(dev_t(scene_np.means), dev_t(scene_np.scales), dev_t(scene_np.quats),
+                    dev_t(scene_np.opacities), dev_t(scene_np.sh), dev_t(scene_np.feats, fdt))
+    seg_np, table_np = S.region_annotations(H, W, D)
+    seg, table = dev_t(seg_np, torch.int32), dev_t(table_np)
+    nsteps = args.warmup + args.steps
+    offs = S.grid_offsets(nsteps, stride, seed=2 + rank)
+    poses = [(rank * 37 + k) % len(cams) for k in range(nsteps)]
+    gcams = [as_camera(cams[poses[k]], stride, *offs[k]) for k in range(nsteps)]
+    Hs, Ws = grid_shape(gcams[0])
+    P = Hs * Ws
+    tgt = torch.empty((D, Hs, Ws), device=dev)
+    mask = torch.empty((Hs, Ws), device=dev)
+    gF = torch.empty((D, Hs, Ws), device=dev)
+    loss = torch.zeros(3, dtype=torch.float64, device=dev)
+    g_feats = torch.empty((scene.n, D), device=dev)
+    ws = L.Workspace(local)
+    stream = torch.cuda.current_stream()
+    max_inst = 0
+    for c in gcams:
+        L.gs_project(scene, c, ws)
+        max_inst = max(max_inst, L.gs_bin_tiles(ws, sync=True))
+    L.gs_workspace_reserve(ws, scene.n, int(max_inst * 1.25) + 1024, P)
+
+    def step(c):
+        L.gs_project(scene, c, ws, stream)
+        L.gs_bin_tiles(ws, sync=False, stream=stream)
+        L.gs_grid_target_region(seg, table, c.stride, c.off_x, c.off_y, tgt, mask, stream)
+        L.gs_render_fwd_loss(scene, c, ws, tgt, gF, loss, mask=mask, lambda_sem=1.0, stream=stream)
+        L.gs_render_bwd(scene, c, ws, g_feat=gF, g_feats=g_feats, stream=stream)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    for k in range(args.warmup):
+        step(gcams[k])
+        flush.fill_(float(k))
+    torch.cuda.synchronize()
+    if L.gs_workspace_status(ws) != L.GS_OK:
+        raise RuntimeError("instance capacity overflow during warm-up")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    L.gs_timing_enable(ws, True)
+    L.gs_timing_collect(ws)
+    clocks = make_clock_sampler(dev, local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = L.gs_launch_count()
+    torch.cuda.nvtx.range_push("timed")
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step(gcams[args.warmup + k])
+        evs[k][1].record(stream)
+        flush.fill_(float(k))
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = L.gs_launch_count() - n0
+    clk = clocks.stop()
+    stage = L.gs_timing_collect(ws)
+    L.gs_timing_enable(ws, False)
+    status = L.gs_workspace_status(ws)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * args.steps * P / (ms * 1e-3) / 1e6
+    sb_tot, sf_tot, pairs = {}, {}, [0, 0]
+    for k in range(args.steps):
+        c = gcams[args.warmup + k]
+        L.gs_project(scene, c, ws)
+        L.gs_bin_tiles(ws, sync=True)
+        L.gs_render_fwd(scene, c, ws, None, None, None, gF)
+        st = L.gs_get_stats(ws)
+        pairs[0] += st["pairs_eval"]
+        pairs[1] += st["pairs_blend"]
+        for name, b in stage_bytes_semantic(st, D, bf).items():
+            sb_tot[name] = sb_tot.get(name, 0.0) + b
+        for name, f in stage_flops_semantic(st, D).items():
+            sf_tot[name] = sf_tot.get(name, 0.0) + f
+    roofline = build_roofline(stage, sb_tot, sf_tot, pairs, args.steps, args.workload)
+
+    # end to end with host buffers: scene parameters and annotations in, feature
+    # gradients and the loss out
+    pin = lambda t: t.cpu().pin_memory()
+    h_in = [pin(t) for t in (scene.means, scene.scales, scene.quats, scene.opacities, scene.sh,
+                             scene.feats, seg, table)]
+    d_in = [torch.empty_like(t, device=dev) for t in h_in]
+    e_scene = L.Scene(*d_in[:6])
+    h_out = [torch.empty_like(g_feats, device="cpu").pin_memory(),
+             torch.empty(3, dtype=torch.float64).pin_memory()]
+
+    def e2e_step(c):
+        for d, h in zip(d_in, h_in):
+            d.copy_(h, non_blocking=True)
+        L.gs_project(e_scene, c, ws, stream)
+        L.gs_bin_tiles(ws, sync=False, stream=stream)
+        L.gs_grid_target_region(d_in[6], d_in[7], c.stride, c.off_x, c.off_y, tgt, mask, stream)
+        L.gs_render_fwd_loss(e_scene, c, ws, tgt, gF, loss, mask=mask, lambda_sem=1.0, stream=stream)
+        L.gs_render_bwd(e_scene, c, ws, g_feat=gF, g_feats=g_feats, stream=stream)
+        h_out[0].copy_(g_feats, non_blocking=True)
+        h_out[1].copy_(loss, non_blocking=True)
+
+    for k in range(min(3, args.warmup)):
+        e2e_step(gcams[k])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(args.steps):
+        e2e_step(gcams[args.warmup + k])
+    b.record(stream)
+    torch.cuda.synchronize()
+    ems = a.elapsed_time(b)
+    e2e = {"value": round(args.steps * P / (ems * 1e-3) / 1e6, 2), "unit": "Mpix/s",
+           "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_in)),
+           "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_out)),
+           "ms_per_step": round(ems / args.steps, 4)}
+    line = {
+        "metric": "Mpix/s supervised samples, semantic phase fwd+bwd (grid, fused loss, features-only)",
+        "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16 features)", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "gaussians": scene.n,
+                   "stride": stride, "samples_per_step": P, "image": [W, H], "poses": len(cams),
+                   "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
+        "device_status": L.status_string(status),
+    }
+    if rank == 0 and not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, scene_np, [cams[p] for p in poses],
+                                            target_budget_s=args.cpu_budget, stride=stride)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def oracle_step(O, scene_np, cam, pixels):
@@ -458,18 +667,24 @@ def oracle_step(O, scene_np, cam, pixels):
     O.backward(scene_np, cam, gs, "f32", pixels=pixels)
 
 
-def sample_pixels(cam, n_tiles, rng):
-    TX, TY = (cam.W + 15) // 16, (cam.H + 15) // 16
+def sample_pixels(cam, n_tiles, rng, stride=1):
+    """Image pixels of n_tiles random 16x16 tiles of the rendered grid (the image, or the
+    stride-s sample grid with a random offset)."""
+    ox, oy = (int(v) for v in rng.integers(0, stride, size=2))
+    Ws, Hs = -(-cam.W // stride), -(-cam.H // stride)
+    TX, TY = (Ws + 15) // 16, (Hs + 15) // 16
     tiles = rng.choice(TX * TY, size=min(n_tiles, TX * TY), replace=False)
     pix = []
     for t in tiles:
         x0, y0 = (t % TX) * 16, (t // TX) * 16
-        ys, xs = np.mgrid[y0:min(y0 + 16, cam.H), x0:min(x0 + 16, cam.W)]
-        pix.append((ys * cam.W + xs).ravel())
+        ms, ns = np.mgrid[y0:min(y0 + 16, Hs), x0:min(x0 + 16, Ws)]
+        ys, xs = oy + stride * ms, ox + stride * ns
+        ok = (ys < cam.H) & (xs < cam.W)
+        pix.append((ys * cam.W + xs)[ok].ravel())
     return np.concatenate(pix)
 
 
-def cpu_baseline(args, scene_np, cams, target_budget_s=15.0):
+def cpu_baseline(args, scene_np, cams, target_budget_s=15.0, stride=1):
     from oracle import oracle as O
     O.build()
     cores = O.set_threads(os.cpu_count() or 1)
@@ -478,7 +693,7 @@ def cpu_baseline(args, scene_np, cams, target_budget_s=15.0):
     t_tot, px_tot, k = 0.0, 0, 0
     while t_tot < target_budget_s and k < len(cams):
         cam = cams[k]
-        pix = sample_pixels(cam, n_tiles, rng)
+        pix = sample_pixels(cam, n_tiles, rng, stride)
         t0 = time.perf_counter()
         oracle_step(O, scene_np, cam, pix)
         t_tot += time.perf_counter() - t0
@@ -486,8 +701,10 @@ def cpu_baseline(args, scene_np, cams, target_budget_s=15.0):
         k += 1
     return {"value": round(px_tot / t_tot / 1e6, 5), "unit": "Mpix/s", "cores": cores,
             "kind": "oracle",
-            "sample": f"{k} poses x {n_tiles} random 16x16 tiles, FP32 oracle forward + backward "
-                      f"(projection and tile lists of the full scene each pose), {t_tot:.1f} s"}
+            "sample": f"{k} poses x {n_tiles} random 16x16 tiles"
+                      + (f" of the stride-{stride} sample grid" if stride > 1 else "")
+                      + ", FP32 oracle forward + backward (projection and tile lists of the "
+                      f"full scene each pose), {t_tot:.1f} s"}
 
 
 def run_reference(args):
@@ -503,7 +720,7 @@ def run_reference(args):
     times, px = [], 0
     for k in range(args.warmup + args.steps):
         cam = cams[k % len(cams)]
-        pix = sample_pixels(cam, args.cpu_tiles, rng)
+        pix = sample_pixels(cam, args.cpu_tiles, rng, wl.get("grid", 1))
         t0 = time.perf_counter()
         oracle_step(O, scene_np, cam, pix)
         dt = time.perf_counter() - t0
@@ -766,6 +983,8 @@ def main():
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif "grid" in WORKLOADS[args.workload]:
+        run_grid(args)
     else:
         run_gpu(args)
 

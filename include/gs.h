@@ -55,8 +55,14 @@ typedef enum { GS_F32 = 0, GS_BF16 = 1 } gs_dtype;
 
 /* Pinhole camera (App. A: "viewing transformation W" and the Jacobian J of the
  * projection).  cx, cy are free; the synthetic workloads use W/2, H/2.
- * stride/off_x/off_y select grid-sampled rendering (App. D, "Dynamic Grid Sampling"):
- * stride 1 with offsets 0 renders every pixel. */
+ * stride/off_x/off_y select grid-sampled rendering (Sec. 3.2 and App. D, "Dynamic Grid
+ * Sampling"): stride 1 with offsets 0 renders every pixel.  With stride s (1..256) and
+ * offsets 0 <= off_x, off_y < s the renderer computes only the samples (m, n) of the
+ * compact Hs x Ws grid, Hs = ceil(H / s), Ws = ceil(W / s), sample (m, n) being image pixel
+ * (row off_y + m s, column off_x + n s); every image output and upstream gradient of
+ * gs_render_fwd / gs_render_bwd is then a compact [.., Hs, Ws] map.  Each sample equals the
+ * full-resolution render at its pixel; samples beyond the image (large offsets) render
+ * nothing (alpha 0, zero colour, depth and features).  Other values: GS_ERR_ARG. */
 typedef struct {
   int32_t W, H;
   float fx, fy, cx, cy;
@@ -142,6 +148,29 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
 gs_status gs_render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
                         float* rgb, float* depth, float* alpha, float* feat, void* stream);
 
+/* Masked L1 + cosine feature loss of App. D ("Masked Loss Evaluation"), evaluated on the
+ * rendered feature map G_hat (n_feat x rows x cols of the camera's grid, P samples) in
+ * the forward's epilogue.  With a = V G_hat and b = V G* per sample:
+ *   L_1 = sum |a - b| / (n_feat P),   L_cos = sum_p (1 - cos(a_p, b_p)) / P,
+ *   cos(a, b) = a.b / (max(|a|, 1e-8) max(|b|, 1e-8)),   L = lambda_sem (L_cos + L_1);
+ * masked samples add the constant 1 to L_cos's sum and no gradient. */
+typedef struct {
+  const float* target;   /* G* [n_feat][rows][cols], device (e.g. from gs_grid_target_*) */
+  const float* mask;     /* V [rows][cols] (0/1), device; NULL = all ones */
+  float lambda_sem;      /* weight, >= 0 */
+  float* g_feat;         /* out: dL/dG_hat [n_feat][rows][cols], device; pass it to
+                            gs_render_bwd as g_feat */
+  double* loss;          /* out: [3] = (L, L_1, L_cos), device; overwritten */
+} gs_feat_loss;
+
+/* NEXT-2: gs_render_fwd with the feature loss fused into its epilogue: the loss value and
+ * its gradient dL/dG_hat are produced without writing G_hat (feat may be NULL) or running
+ * a separate loss pass.  Requires n_feat > 0.  Errors as gs_render_fwd; GS_ERR_ARG for a
+ * NULL loss, target, g_feat or loss pointer or a negative lambda_sem. */
+gs_status gs_render_fwd_loss(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
+                             float* rgb, float* depth, float* alpha, float* feat,
+                             const gs_feat_loss* loss, void* stream);
+
 /* a4 + a5. Backward of gs_render_fwd (App. B: the rasterizer is differentiable; Eq. 2
  * tracking, Eq. 3 mapping).  Inputs are the upstream gradients of the four images (device,
  * same layout as the outputs; NULL = zero).  Outputs (device, overwritten, zero for culled
@@ -161,6 +190,30 @@ gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
  * pointers, n elements.  May alias grad == pred. */
 gs_status gs_l1_grad(const float* pred, const float* target, int64_t n, float scale,
                      float* grad, void* stream);
+
+/* ---- grid-sampled supervision targets (Sec. 3.2; App. D, "Compact Predictions and
+ * Targets") ------------------------------------------------------------------------
+ * Both fill the compact target G* [D][Hs][Ws] and the validity mask V [Hs][Ws] (floats
+ * 0 / 1; mask may be NULL) of the stride-s sample grid with offsets (off_x, off_y):
+ * Hs = ceil(H / s), Ws = ceil(W / s), sample (m, n) = image pixel (row off_y + m s,
+ * column off_x + n s), the grid gs_render_fwd draws for the same camera fields.  Samples
+ * beyond the image get V = 0 and zero targets.  All pointers are caller-owned device
+ * memory; the calls are asynchronous on `stream`.  Errors: GS_ERR_ARG for non-positive
+ * sizes, a stride outside 1..256 or an offset outside [0, stride). */
+
+/* Region-indexed annotations: seg [H][W] int32 region ids (-1 = background) and a
+ * region-feature table [R][D].  V = 1 where the sampled id lies in [0, R), and G* is that
+ * table row; any other id counts as background (V = 0, G* = 0). */
+gs_status gs_grid_target_region(const int32_t* seg, int32_t H, int32_t W, const float* table,
+                                int32_t R, int32_t D, int32_t stride, int32_t off_x, int32_t off_y,
+                                float* target, float* mask, void* stream);
+
+/* Continuous feature map fmap [D][Hf][Wf] at a lower resolution: sample (u, v) reads the
+ * map at (round(u (Hf - 1) / max(H - 1, 1)), round(v (Wf - 1) / max(W - 1, 1))), halves
+ * rounded away from zero (exact integer arithmetic); V = 1 inside the image. */
+gs_status gs_grid_target_resample(const float* fmap, int32_t D, int32_t Hf, int32_t Wf, int32_t H,
+                                  int32_t W, int32_t stride, int32_t off_x, int32_t off_y,
+                                  float* target, float* mask, void* stream);
 
 /* ---- introspection (synchronous; host pointers) ---------------------------------- */
 

@@ -57,6 +57,11 @@ class gs_result(C.Structure):
                 ("queue_us", C.c_double), ("run_us", C.c_double), ("latency_us", C.c_double)]
 
 
+class gs_feat_loss(C.Structure):
+    _fields_ = [("target", C.c_void_p), ("mask", C.c_void_p), ("lambda_sem", C.c_float),
+                ("g_feat", C.c_void_p), ("loss", C.c_void_p)]
+
+
 class gs_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("visible", C.c_int64), ("instances", C.c_int64),
                 ("inst_eff", C.c_int64), ("pixels", C.c_int64), ("tiles", C.c_int64),
@@ -79,6 +84,7 @@ def _load():
         "gs_bin_tiles": ([P, P, P], st),
         "gs_render_fwd": ([P, P, P, P, P, P, P, P], st),
         "gs_render_bwd": ([P, P, P] + [P] * 4 + [P] * 7 + [P], st),
+        "gs_render_fwd_loss": ([P, P, P, P, P, P, P, P, P], st),
         "gs_l1_grad": ([P, P, i64, C.c_float, P, P], st),
         "gs_get_stats": ([P, P, P], st),
         "gs_get_instances": ([P, P, P, i64, P, P, P], st),
@@ -95,6 +101,8 @@ def _load():
         "gs_serve_poll": ([P, C.c_uint64, i64, P], st),
         "gs_serve_cancel": ([P, C.c_uint64], st),
         "gs_serve_info": ([P, P, P, P, P], st),
+        "gs_grid_target_region": ([P, i32, i32, P, i32, i32, i32, i32, i32, P, P, P], st),
+        "gs_grid_target_resample": ([P, i32, i32, i32, i32, i32, i32, i32, i32, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -241,6 +249,18 @@ def gs_render_fwd(scene, cam, ws, rgb=None, depth=None, alpha=None, feat=None, s
                              _ptr(alpha), _ptr(feat), _stream(stream)), "gs_render_fwd")
 
 
+def gs_render_fwd_loss(scene, cam, ws, target, g_feat, loss, mask=None, lambda_sem=1.0, rgb=None,
+                       depth=None, alpha=None, feat=None, stream=None):
+    """Forward render with the masked L1 + cosine feature loss fused in: writes dL/dG_hat
+    into ``g_feat`` [D,rows,cols] and (L, L_1, L_cos) into ``loss`` (float64 device [3])."""
+    fl = gs_feat_loss()
+    fl.target, fl.mask, fl.lambda_sem = _ptr(target), _ptr(mask), float(lambda_sem)
+    fl.g_feat, fl.loss = _ptr(g_feat), _ptr(loss)
+    _check(lib.gs_render_fwd_loss(C.byref(scene.c), C.byref(cam), ws.h, _ptr(rgb), _ptr(depth),
+                                  _ptr(alpha), _ptr(feat), C.byref(fl), _stream(stream)),
+           "gs_render_fwd_loss")
+
+
 def gs_render_bwd(scene, cam, ws, g_rgb=None, g_depth=None, g_alpha=None, g_feat=None,
                   g_means=None, g_scales=None, g_quats=None, g_opac=None, g_sh=None,
                   g_feats=None, g_pose6=None, stream=None):
@@ -375,6 +395,24 @@ def gs_render_fwd_noalloc(scene, cam, rgb=None, depth=None, alpha=None, feat=Non
     Returns the status code instead of raising, so callers can test GS_ERR_OVER_BUDGET."""
     return lib.gs_render_fwd_noalloc(C.byref(scene.c), C.byref(cam), _ptr(rgb), _ptr(depth),
                                      _ptr(alpha), _ptr(feat), _stream(stream))
+
+
+def gs_grid_target_region(seg, table, stride, off_x, off_y, target, mask=None, stream=None):
+    """Region-indexed grid targets: seg [H,W] int32 (device), table [R,D] float32 -> target
+    [D,Hs,Ws], mask [Hs,Ws] (caller-allocated device tensors)."""
+    H, W = seg.shape
+    R, D = table.shape
+    _check(lib.gs_grid_target_region(_ptr(seg), H, W, _ptr(table), R, D, int(stride), int(off_x),
+                                     int(off_y), _ptr(target), _ptr(mask), _stream(stream)),
+           "gs_grid_target_region")
+
+
+def gs_grid_target_resample(fmap, H, W, stride, off_x, off_y, target, mask=None, stream=None):
+    """Continuous-map grid targets: fmap [D,Hf,Wf] float32 (device) for an H x W image."""
+    D, Hf, Wf = fmap.shape
+    _check(lib.gs_grid_target_resample(_ptr(fmap), D, Hf, Wf, int(H), int(W), int(stride),
+                                       int(off_x), int(off_y), _ptr(target), _ptr(mask),
+                                       _stream(stream)), "gs_grid_target_resample")
 
 
 def gs_launch_count() -> int:

@@ -50,6 +50,7 @@ struct gs_workspace {
   DevBuf<GaussRec> rec;
   DevBuf<uint32_t> depth_key, ntiles, sort_k0, sort_v0, sort_k1, sort_v1;
   DevBuf<uint2> rect;
+  DevBuf<uint2> rect_full;   // image-tile rectangles (sample-grid renders only)
   DevBuf<float> g2d;
   DevBuf<float> pose_partials;
   // per instance
@@ -134,11 +135,22 @@ gs_status make_cam(const gs_camera* c, CamDev* out) {
   if ((int64_t)((c->W + kTile - 1) / kTile) * ((c->H + kTile - 1) / kTile) > (int64_t(1) << 24))
     return GS_ERR_ARG;
   if (!(c->fx > 0.f) || !(c->fy > 0.f) || !(c->near_z > 0.f)) return GS_ERR_ARG;
-  if (c->stride != 1 || c->off_x != 0 || c->off_y != 0) return GS_ERR_ARG;
+  // rendered pixels: the image (stride 1) or the stride-s sample grid with offsets in
+  // [0, s) (App. D), of fixed size ceil(H / s) x ceil(W / s)
+  if (c->stride < 1 || c->stride > kMaxStride || c->off_x < 0 || c->off_x >= c->stride ||
+      c->off_y < 0 || c->off_y >= c->stride)
+    return GS_ERR_ARG;
   out->W = c->W;
   out->H = c->H;
   out->TX = (c->W + kTile - 1) / kTile;
   out->TY = (c->H + kTile - 1) / kTile;
+  out->stride = c->stride;
+  out->ox = c->off_x;
+  out->oy = c->off_y;
+  out->GW = (c->W + c->stride - 1) / c->stride;
+  out->GH = (c->H + c->stride - 1) / c->stride;
+  out->GTX = (out->GW + kTile - 1) / kTile;
+  out->GTY = (out->GH + kTile - 1) / kTile;
   out->fx = c->fx;
   out->fy = c->fy;
   out->cx = c->cx;
@@ -147,6 +159,11 @@ gs_status make_cam(const gs_camera* c, CamDev* out) {
   std::memcpy(out->t, c->t, sizeof(out->t));
   out->near_z = c->near_z;
   return GS_OK;
+}
+
+// Same image and the same rendered grid (a render must use the projection's grid).
+bool same_grid(const CamDev& a, const CamDev& b) {
+  return a.W == b.W && a.H == b.H && a.stride == b.stride && a.ox == b.ox && a.oy == b.oy;
 }
 
 int bits_for(int64_t n_values) {
@@ -259,7 +276,7 @@ void gs_workspace_destroy(gs_workspace* ws) {
     cudaDeviceSynchronize();
     ws->rec.release(); ws->depth_key.release(); ws->ntiles.release();
     ws->sort_k0.release(); ws->sort_v0.release(); ws->sort_k1.release(); ws->sort_v1.release();
-    ws->rect.release(); ws->g2d.release(); ws->pose_partials.release();
+    ws->rect.release(); ws->rect_full.release(); ws->g2d.release(); ws->pose_partials.release();
     ws->inst_tile.release(); ws->inst_id.release(); ws->inst_tile2.release(); ws->inst_id2.release();
     ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
     ws->tile_order.release(); ws->queue.release();
@@ -312,18 +329,21 @@ gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
   GS_TRY(ensure_gauss(ws, scene->n));
-  GS_TRY(ensure_pix(ws, (int64_t)cd.W * cd.H, (int64_t)cd.TX * cd.TY));
+  GS_TRY(ensure_pix(ws, (int64_t)cd.GW * cd.GH, (int64_t)cd.GTX * cd.GTY));
+  const bool grid = cd.stride > 1;
+  if (grid) GS_TRY(ws->rect_full.ensure((size_t)std::max<int64_t>(scene->n, 1)));
   StageTimer tm(ws, GS_TIMER_PROJECT, st);
   GS_TRY(cudaMemsetAsync(ws->counters.p + kCntVisible, 0, 2 * sizeof(uint32_t), st));
-  launch_project(*scene, cd, ws->rec.p, ws->depth_key.p, ws->ntiles.p, ws->rect.p, ws->counters.p,
-                 st);
+  launch_project(*scene, cd, ws->rec.p, ws->depth_key.p, ws->ntiles.p, ws->rect.p,
+                 grid ? ws->rect_full.p : nullptr, ws->counters.p, st);
   GS_TRY(cudaGetLastError());
   ws->n = scene->n;
   ws->cam = cd;
-  ws->W = cd.W;
-  ws->H = cd.H;
-  ws->TX = cd.TX;
-  ws->TY = cd.TY;
+  // the rendered grid (the image itself at stride 1)
+  ws->W = cd.GW;
+  ws->H = cd.GH;
+  ws->TX = cd.GTX;
+  ws->TY = cd.GTY;
   ws->stage = 1;
   return GS_OK;
 }
@@ -378,27 +398,62 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   return GS_OK;
 }
 
-gs_status gs_render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws, float* rgb,
-                        float* depth, float* alpha, float* feat, void* stream) {
+namespace {
+
+gs_status render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws, float* rgb,
+                     float* depth, float* alpha, float* feat, const gs_feat_loss* loss,
+                     void* stream) {
   if (!ws) return GS_ERR_ARG;
   gs_status s = check_scene(scene);
   if (s != GS_OK) return s;
   CamDev cd;
   if ((s = make_cam(cam, &cd)) != GS_OK) return s;
   cd.n_gauss = (int)scene->n;
-  if (ws->stage < 2 || scene->n != ws->n || cd.W != ws->W || cd.H != ws->H) return GS_ERR_STATE;
+  if (ws->stage < 2 || scene->n != ws->n || !same_grid(cd, ws->cam)) return GS_ERR_STATE;
   if (feat && scene->n_feat > 0 && !aligned16(feat)) return GS_ERR_ARG;
+  FeatLoss fl{};
+  if (loss) {
+    if (scene->n_feat <= 0 || !loss->target || !loss->g_feat || !loss->loss ||
+        !(loss->lambda_sem >= 0.f))
+      return GS_ERR_ARG;
+    const double P = (double)cd.GW * cd.GH, D = (double)scene->n_feat;
+    fl.target = loss->target;
+    fl.mask = loss->mask;
+    fl.g_feat = loss->g_feat;
+    fl.loss = loss->loss;
+    fl.lambda = loss->lambda_sem;
+    fl.s_l1 = 1.0 / (D * P);
+    fl.s_cos = 1.0 / P;
+    fl.w_l1 = (float)(fl.lambda * fl.s_l1);
+    fl.w_cos = (float)(fl.lambda * fl.s_cos);
+  }
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
   StageTimer tm(ws, GS_TIMER_FWD, st);
   GS_TRY(cudaMemsetAsync(ws->queue.p, 0, sizeof(uint32_t), st));
-  const TileQueue tq{ws->queue.p, ws->ordered ? ws->tile_order.p : nullptr, cd.TX * cd.TY};
-  launch_raster_fwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, scene->n_feat, ws->ranges.p,
-                    ws->id_sorted, rgb, depth, alpha, scene->n_feat > 0 ? feat : nullptr,
-                    ws->T_final.p, ws->n_contrib.p, st);
+  if (loss) GS_TRY(cudaMemsetAsync(loss->loss, 0, 3 * sizeof(double), st));
+  const TileQueue tq{ws->queue.p, ws->ordered ? ws->tile_order.p : nullptr, cd.GTX * cd.GTY};
+  launch_raster_fwd(cd, tq, ws->rec.p, cd.stride > 1 ? ws->rect_full.p : nullptr, scene->feats,
+                    scene->feat_dtype, scene->n_feat, ws->ranges.p, ws->id_sorted, rgb, depth,
+                    alpha, scene->n_feat > 0 ? feat : nullptr, ws->T_final.p, ws->n_contrib.p,
+                    loss ? &fl : nullptr, st);
   GS_TRY(cudaGetLastError());
   ws->stage = 3;
   return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws, float* rgb,
+                        float* depth, float* alpha, float* feat, void* stream) {
+  return render_fwd(scene, cam, ws, rgb, depth, alpha, feat, nullptr, stream);
+}
+
+gs_status gs_render_fwd_loss(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
+                             float* rgb, float* depth, float* alpha, float* feat,
+                             const gs_feat_loss* loss, void* stream) {
+  if (!loss) return GS_ERR_ARG;
+  return render_fwd(scene, cam, ws, rgb, depth, alpha, feat, loss, stream);
 }
 
 gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
@@ -411,26 +466,33 @@ gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
   CamDev cd;
   if ((s = make_cam(cam, &cd)) != GS_OK) return s;
   cd.n_gauss = (int)scene->n;
-  if (ws->stage < 3 || scene->n != ws->n || cd.W != ws->W || cd.H != ws->H) return GS_ERR_STATE;
+  if (ws->stage < 3 || scene->n != ws->n || !same_grid(cd, ws->cam)) return GS_ERR_STATE;
   if (g_feats && !aligned16(g_feats)) return GS_ERR_ARG;
   if (g_quats && !aligned16(g_quats)) return GS_ERR_ARG;
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = scene->n;
   const int D = scene->n_feat;
+  // Features-only backward (geometry and colour frozen, Sec. 3.2): only g_feats is asked
+  // for, so the rasterizer skips every geometry term and the projection backward is not run.
+  const bool features_only = D > 0 && g_feat && g_feats && !g_means && !g_scales && !g_quats &&
+                             !g_opac && !g_sh && !g_pose6;
   {
     StageTimer tm(ws, GS_TIMER_BWD_RASTER, st);
-    if (n > 0) GS_TRY(cudaMemsetAsync(ws->g2d.p, 0, sizeof(float) * kG2D * (size_t)n, st));
+    if (n > 0 && !features_only)
+      GS_TRY(cudaMemsetAsync(ws->g2d.p, 0, sizeof(float) * kG2D * (size_t)n, st));
     if (g_feats && n > 0 && D > 0)
       GS_TRY(cudaMemsetAsync(g_feats, 0, sizeof(float) * (size_t)n * D, st));
     GS_TRY(cudaMemsetAsync(ws->queue.p + 1, 0, sizeof(uint32_t), st));
-    const TileQueue tq{ws->queue.p + 1, ws->ordered ? ws->tile_order.p : nullptr, cd.TX * cd.TY};
-    launch_raster_bwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, D, ws->ranges.p,
+    const TileQueue tq{ws->queue.p + 1, ws->ordered ? ws->tile_order.p : nullptr, cd.GTX * cd.GTY};
+    launch_raster_bwd(cd, tq, ws->rec.p, cd.stride > 1 ? ws->rect_full.p : nullptr, scene->feats,
+                      scene->feat_dtype, D, ws->ranges.p,
                       ws->id_sorted, ws->T_final.p, ws->n_contrib.p, g_rgb, g_depth, g_alpha,
-                      D > 0 ? g_feat : nullptr, ws->g2d.p, D > 0 ? g_feats : nullptr, st);
+                      D > 0 ? g_feat : nullptr, ws->g2d.p, D > 0 ? g_feats : nullptr,
+                      features_only, st);
     GS_TRY(cudaGetLastError());
   }
-  {
+  if (!features_only) {
     StageTimer tm(ws, GS_TIMER_BWD_PROJECT, st);
     launch_project_bwd(*scene, cd, ws->rec.p, ws->ntiles.p, ws->g2d.p, g_means, g_scales, g_quats,
                        g_opac, g_sh, ws->pose_partials.p, g_pose6, st);
@@ -456,8 +518,8 @@ gs_status gs_get_stats(gs_workspace* ws, gs_stats* out, void* stream) {
   unsigned long long pairs[2] = {0ull, 0ull};
   if (ws->stage >= 3) {
     GS_TRY(ws->stats64.ensure(2));
-    launch_pair_stats(ws->cam, ws->rec.p, ws->ranges.p, ws->id_sorted, ws->n_contrib.p,
-                      ws->stats64.p, st);
+    launch_pair_stats(ws->cam, ws->rec.p, ws->cam.stride > 1 ? ws->rect_full.p : nullptr,
+                      ws->ranges.p, ws->id_sorted, ws->n_contrib.p, ws->stats64.p, st);
     GS_TRY(cudaMemcpyAsync(pairs, ws->stats64.p, sizeof(pairs), cudaMemcpyDeviceToHost, st));
   }
   GS_TRY(cudaMemcpyAsync(ws->h_counters, ws->counters.p, kCntNum * sizeof(uint32_t),

@@ -12,6 +12,7 @@ namespace gs {
 constexpr int kTile = 16;
 constexpr int kTilePix = kTile * kTile;   // 256 pixels, one thread each
 constexpr int kMaxFeat = 64;
+constexpr int kMaxStride = 256;   // largest sample-grid stride
 
 // Per-Gaussian record written by the projection and gathered by the rasterizer:
 // r0 = (u, v, A, B), r1 = (C, opacity, depth, 0), r2 = (r, g, b, 0); 48 bytes.
@@ -20,7 +21,11 @@ struct __align__(16) GaussRec {
   float4 r0, r1, r2;
 };
 
-// Camera as the kernels see it.
+// Camera as the kernels see it.  W, H, TX, TY are the image and its 16x16 tiles (the
+// projection's rectangles live in these tiles).  The rendered pixels form a grid: at
+// stride 1 the image itself; at stride s (grid-sampled supervision, App. D) the compact
+// GW x GH grid whose sample (n, m) is image pixel (ox + n s, oy + m s), binned in 16x16
+// tiles of samples (GTX x GTY).
 struct CamDev {
   int W, H, TX, TY;
   int n_gauss;   // number of Gaussians (bounds check of gathered ids)
@@ -28,7 +33,18 @@ struct CamDev {
   float R[9];
   float t[3];
   float near_z;
+  int stride, ox, oy;
+  int GW, GH, GTX, GTY;
 };
+
+// Image pixel coordinate of compact sample index k along an axis with offset o.
+__host__ __device__ inline int grid_coord(int o, int stride, int k) { return o + k * stride; }
+
+// Is image tile (ftx, fty) inside a packed tile rectangle (x0 | y0 << 16, x1 | y1 << 16)?
+__device__ inline bool rect_has(uint2 rc, int ftx, int fty) {
+  return ftx >= (int)(rc.x & 0xFFFFu) && ftx < (int)(rc.y & 0xFFFFu) &&
+         fty >= (int)(rc.x >> 16) && fty < (int)(rc.y >> 16);
+}
 
 // Device status word bits.
 enum : uint32_t {
@@ -50,8 +66,12 @@ enum : int {
 
 // gs_project_fwd.cu
 // Also adds V (visible Gaussians) and I (tile instances) to counters[kCntVisible/kCntInst].
+// On a sample grid (stride > 1) `rect` and `ntiles` describe the Gaussian's rectangle in
+// tiles of samples and `rect_full` receives its image-tile rectangle (the per-sample
+// membership test of the rasterizer); at stride 1 rect_full is not written.
 void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32_t* depth_key,
-                    uint32_t* ntiles, uint2* rect, uint32_t* counters, cudaStream_t st);
+                    uint32_t* ntiles, uint2* rect, uint2* rect_full, uint32_t* counters,
+                    cudaStream_t st);
 
 // gs_sort.cu
 // Scratch of the binning kernels.  ghist (7 x 256 words) and tickets (4 words) are one
@@ -96,8 +116,8 @@ void launch_inst_eff(const uint32_t* n_contrib, int TX, int TY, int W, int H, ui
 constexpr int kMaxOrderedTiles = 1 << 18;
 bool launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t st);
 // Pair counts for the roofline model (stats only): stats64[0] = evaluated, [1] = blended.
-void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* ranges,
-                       const uint32_t* inst_id, const uint32_t* n_contrib,
+void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* rect_full,
+                       const uint2* ranges, const uint32_t* inst_id, const uint32_t* n_contrib,
                        unsigned long long* stats64, cudaStream_t st);
 
 // Persistent raster scheduling: a CTA takes the next tile index from *queue (zeroed
@@ -109,34 +129,51 @@ struct TileQueue {
 };
 
 // Grid of a persistent kernel: as many CTAs as fit on the device at once (never more than
-// n_items).  Sets the dynamic shared-memory attribute when above the 48 KB default.
+// n_items).  Sets the kernel's dynamic shared-memory limit to `smem`: static plus dynamic
+// shared memory above 48 KB needs it even when the dynamic part alone is below 48 KB.
 template <class Kernel>
 inline int persistent_grid(Kernel kern, int threads, size_t smem, int n_items) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   const int g = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   return n_items < g ? (n_items > 0 ? n_items : 1) : g;
 }
 
 // gs_raster_fwd.cu
+// Masked L1 + cosine feature loss (App. D) fused into the forward's epilogue; inactive
+// when target is null.  Per sample p with a = V_p G_hat[:, p], b = V_p G*[:, p]:
+// L_1 = sum |a - b| / (D P), L_cos = sum_p (1 - cos(a, b)) / P, L = lambda (L_1 + L_cos).
+struct FeatLoss {
+  const float* target;   // G* [D][GH][GW]
+  const float* mask;     // V [GH][GW]; null = all ones
+  float* g_feat;         // out: dL/dG_hat [D][GH][GW]
+  double* loss;          // out: L, L_1, L_cos (accumulated; zeroed by the caller)
+  float w_l1, w_cos;     // lambda / (D P), lambda / P
+  double s_l1, s_cos, lambda;   // 1 / (D P), 1 / P, lambda
+};
+constexpr float kCosEps = 1e-8f;
+
+// rect_full: image-tile rectangles (grid rendering, stride > 1), else null.  loss: the
+// fused feature loss, or null.
 void launch_raster_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-                       const void* feats, int feat_dtype, int D, const uint2* ranges,
+                       const uint2* rect_full, const void* feats, int feat_dtype, int D,
+                       const uint2* ranges,
                        const uint32_t* inst_id, float* rgb, float* depth, float* alpha, float* feat,
-                       float* T_final, uint32_t* n_contrib, cudaStream_t st);
+                       float* T_final, uint32_t* n_contrib, const FeatLoss* loss,
+                       cudaStream_t st);
 
 // gs_raster_bwd.cu
 // Accumulators per Gaussian: g2d[12*i + k], k = u, v, A, B, C, o, r, g, b, z
 constexpr int kG2D = 12;
 void launch_raster_bwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-                       const void* feats, int feat_dtype,
+                       const uint2* rect_full, const void* feats, int feat_dtype,
                        int D, const uint2* ranges, const uint32_t* inst_id, const float* T_final,
                        const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
                        const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,
-                       cudaStream_t st);
+                       bool features_only, cudaStream_t st);
 
 // gs_project_bwd.cu
 int project_bwd_blocks(int64_t n);

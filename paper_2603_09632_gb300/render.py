@@ -16,6 +16,13 @@ def as_camera(cam, stride=1, off_x=0, off_y=0) -> L.gs_camera:
                          np.asarray(cam.t), getattr(cam, "near", 0.2), stride, off_x, off_y)
 
 
+def grid_shape(cam):
+    """(rows, cols) of the rendered pixels: the image, or the compact stride-s sample grid
+    ceil(H / s) x ceil(W / s)."""
+    s = max(int(cam.stride), 1)
+    return (cam.H + s - 1) // s, (cam.W + s - 1) // s
+
+
 class Rasterizer:
     """One workspace on one device.  Not thread-safe; one stream order at a time."""
 
@@ -29,9 +36,10 @@ class Rasterizer:
 
     def forward(self, scene: L.Scene, cam, feat=True, sync=True, stream=None, out=None):
         """Project, bin and render.  Returns dict rgb [3,H,W], depth [H,W], alpha [H,W],
-        feat [D,H,W] (float32 device tensors) and, with ``sync``, the instance count."""
+        feat [D,H,W] (float32 device tensors; H, W = grid_shape(cam) for a sample-grid
+        camera) and, with ``sync``, the instance count."""
         c = as_camera(cam)
-        H, W = c.H, c.W
+        H, W = grid_shape(c)
         dev = self.device
         if out is None:
             out = dict(rgb=torch.empty((3, H, W), device=dev), depth=torch.empty((H, W), device=dev),

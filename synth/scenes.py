@@ -232,6 +232,25 @@ def upstream_grads(H, W, n_feat, seed=SEED_GRADS, scale=1.0):
     )
 
 
+def region_annotations(H, W, n_feat, n_regions=200, seed=SEED_GRADS, block=8, bg_frac=0.2):
+    """Seeded stand-in for precomputed region-indexed semantic annotations (App. D): a
+    segmentation [H, W] int32 of piecewise-constant regions on ``block``-pixel cells
+    (about ``bg_frac`` background, id -1) and a region-feature table [n_regions, n_feat]
+    of N(0, 1) float32 rows."""
+    rng = np.random.default_rng(seed + 2000)
+    coarse = rng.integers(0, n_regions, size=(-(-H // block), -(-W // block)))
+    coarse[rng.uniform(size=coarse.shape) < bg_frac] = -1
+    seg = np.repeat(np.repeat(coarse, block, 0), block, 1)[:H, :W].astype(np.int32)
+    table = rng.normal(size=(n_regions, n_feat)).astype(np.float32)
+    return seg, table
+
+
+def grid_offsets(n, stride, seed=SEED_GRADS):
+    """Per-step grid offsets (o_x, o_y) drawn uniformly from {0..s-1}^2 (App. D)."""
+    rng = np.random.default_rng(seed + 3000)
+    return [tuple(int(v) for v in rng.integers(0, stride, size=2)) for _ in range(n)]
+
+
 def feature_target(H, W, n_feat, seed=SEED_GRADS):
     """Seeded N(0,1) target feature map [D,H,W] for the L1 distillation loss."""
     rng = np.random.default_rng(seed + 1000)
