@@ -50,7 +50,7 @@ struct gs_workspace {
   DevBuf<GaussRec> rec;
   DevBuf<uint32_t> depth_key, ntiles, sort_k0, sort_v0, sort_k1, sort_v1;
   DevBuf<uint2> rect;
-  DevBuf<uint2> rect_full;   // image-tile rectangles (sample-grid renders only)
+  DevBuf<uint32_t> item_max;   // per grid work item, statistics only
   DevBuf<float> g2d;
   DevBuf<float> pose_partials;
   // per instance
@@ -149,8 +149,6 @@ gs_status make_cam(const gs_camera* c, CamDev* out) {
   out->oy = c->off_y;
   out->GW = (c->W + c->stride - 1) / c->stride;
   out->GH = (c->H + c->stride - 1) / c->stride;
-  out->GTX = (out->GW + kTile - 1) / kTile;
-  out->GTY = (out->GH + kTile - 1) / kTile;
   out->fx = c->fx;
   out->fy = c->fy;
   out->cx = c->cx;
@@ -276,7 +274,7 @@ void gs_workspace_destroy(gs_workspace* ws) {
     cudaDeviceSynchronize();
     ws->rec.release(); ws->depth_key.release(); ws->ntiles.release();
     ws->sort_k0.release(); ws->sort_v0.release(); ws->sort_k1.release(); ws->sort_v1.release();
-    ws->rect.release(); ws->rect_full.release(); ws->g2d.release(); ws->pose_partials.release();
+    ws->rect.release(); ws->item_max.release(); ws->g2d.release(); ws->pose_partials.release();
     ws->inst_tile.release(); ws->inst_id.release(); ws->inst_tile2.release(); ws->inst_id2.release();
     ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
     ws->tile_order.release(); ws->queue.release();
@@ -329,21 +327,20 @@ gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
   GS_TRY(ensure_gauss(ws, scene->n));
-  GS_TRY(ensure_pix(ws, (int64_t)cd.GW * cd.GH, (int64_t)cd.GTX * cd.GTY));
-  const bool grid = cd.stride > 1;
-  if (grid) GS_TRY(ws->rect_full.ensure((size_t)std::max<int64_t>(scene->n, 1)));
+  GS_TRY(ensure_pix(ws, (int64_t)cd.GW * cd.GH, (int64_t)cd.TX * cd.TY));
   StageTimer tm(ws, GS_TIMER_PROJECT, st);
   GS_TRY(cudaMemsetAsync(ws->counters.p + kCntVisible, 0, 2 * sizeof(uint32_t), st));
-  launch_project(*scene, cd, ws->rec.p, ws->depth_key.p, ws->ntiles.p, ws->rect.p,
-                 grid ? ws->rect_full.p : nullptr, ws->counters.p, st);
+  launch_project(*scene, cd, ws->rec.p, ws->depth_key.p, ws->ntiles.p, ws->rect.p, ws->counters.p,
+                 st);
   GS_TRY(cudaGetLastError());
   ws->n = scene->n;
   ws->cam = cd;
-  // the rendered grid (the image itself at stride 1)
+  // W, H: the rendered pixels (the compact grid at stride > 1); TX, TY: the image tiles in
+  // which Gaussians are binned
   ws->W = cd.GW;
   ws->H = cd.GH;
-  ws->TX = cd.GTX;
-  ws->TY = cd.GTY;
+  ws->TX = cd.TX;
+  ws->TY = cd.TY;
   ws->stage = 1;
   return GS_OK;
 }
@@ -432,11 +429,16 @@ gs_status render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
   StageTimer tm(ws, GS_TIMER_FWD, st);
   GS_TRY(cudaMemsetAsync(ws->queue.p, 0, sizeof(uint32_t), st));
   if (loss) GS_TRY(cudaMemsetAsync(loss->loss, 0, 3 * sizeof(double), st));
-  const TileQueue tq{ws->queue.p, ws->ordered ? ws->tile_order.p : nullptr, cd.GTX * cd.GTY};
-  launch_raster_fwd(cd, tq, ws->rec.p, cd.stride > 1 ? ws->rect_full.p : nullptr, scene->feats,
-                    scene->feat_dtype, scene->n_feat, ws->ranges.p, ws->id_sorted, rgb, depth,
-                    alpha, scene->n_feat > 0 ? feat : nullptr, ws->T_final.p, ws->n_contrib.p,
-                    loss ? &fl : nullptr, st);
+  const TileQueue tq{ws->queue.p, ws->ordered ? ws->tile_order.p : nullptr, cd.TX * cd.TY};
+  if (cd.stride > 1)
+    launch_grid_fwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, scene->n_feat, ws->ranges.p,
+                    ws->id_sorted, rgb, depth, alpha, scene->n_feat > 0 ? feat : nullptr,
+                    ws->T_final.p, ws->n_contrib.p, loss ? &fl : nullptr, st);
+  else
+    launch_raster_fwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, scene->n_feat,
+                      ws->ranges.p, ws->id_sorted, rgb, depth, alpha,
+                      scene->n_feat > 0 ? feat : nullptr, ws->T_final.p, ws->n_contrib.p,
+                      loss ? &fl : nullptr, st);
   GS_TRY(cudaGetLastError());
   ws->stage = 3;
   return GS_OK;
@@ -484,12 +486,17 @@ gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
     if (g_feats && n > 0 && D > 0)
       GS_TRY(cudaMemsetAsync(g_feats, 0, sizeof(float) * (size_t)n * D, st));
     GS_TRY(cudaMemsetAsync(ws->queue.p + 1, 0, sizeof(uint32_t), st));
-    const TileQueue tq{ws->queue.p + 1, ws->ordered ? ws->tile_order.p : nullptr, cd.GTX * cd.GTY};
-    launch_raster_bwd(cd, tq, ws->rec.p, cd.stride > 1 ? ws->rect_full.p : nullptr, scene->feats,
-                      scene->feat_dtype, D, ws->ranges.p,
-                      ws->id_sorted, ws->T_final.p, ws->n_contrib.p, g_rgb, g_depth, g_alpha,
-                      D > 0 ? g_feat : nullptr, ws->g2d.p, D > 0 ? g_feats : nullptr,
-                      features_only, st);
+    const TileQueue tq{ws->queue.p + 1, ws->ordered ? ws->tile_order.p : nullptr, cd.TX * cd.TY};
+    const float* gf = D > 0 ? g_feat : nullptr;
+    float* gfe = D > 0 ? g_feats : nullptr;
+    if (cd.stride > 1)
+      launch_grid_bwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, D, ws->ranges.p,
+                      ws->id_sorted, ws->T_final.p, ws->n_contrib.p, g_rgb, g_depth, g_alpha, gf,
+                      ws->g2d.p, gfe, features_only, st);
+    else
+      launch_raster_bwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, D, ws->ranges.p,
+                        ws->id_sorted, ws->T_final.p, ws->n_contrib.p, g_rgb, g_depth, g_alpha, gf,
+                        ws->g2d.p, gfe, features_only, st);
     GS_TRY(cudaGetLastError());
   }
   if (!features_only) {
@@ -513,13 +520,21 @@ gs_status gs_get_stats(gs_workspace* ws, gs_stats* out, void* stream) {
   if (!ws || !out) return GS_ERR_ARG;
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
-  if (ws->stage >= 3)
+  const bool grid = ws->cam.stride > 1;
+  if (ws->stage >= 3 && !grid)
     launch_inst_eff(ws->n_contrib.p, ws->TX, ws->TY, ws->W, ws->H, ws->counters.p, st);
   unsigned long long pairs[2] = {0ull, 0ull};
   if (ws->stage >= 3) {
     GS_TRY(ws->stats64.ensure(2));
-    launch_pair_stats(ws->cam, ws->rec.p, ws->cam.stride > 1 ? ws->rect_full.p : nullptr,
-                      ws->ranges.p, ws->id_sorted, ws->n_contrib.p, ws->stats64.p, st);
+    if (grid) {
+      // I_eff and pair counts of the grid's work items (one pass per sample)
+      GS_TRY(ws->item_max.ensure((size_t)ws->TX * ws->TY * grid_chunks_per_tile(ws->cam.stride)));
+      launch_grid_stats(ws->cam, ws->rec.p, ws->ranges.p, ws->id_sorted, ws->n_contrib.p,
+                        ws->item_max.p, ws->counters.p, ws->stats64.p, st);
+    } else {
+      launch_pair_stats(ws->cam, ws->rec.p, ws->ranges.p, ws->id_sorted, ws->n_contrib.p,
+                        ws->stats64.p, st);
+    }
     GS_TRY(cudaMemcpyAsync(pairs, ws->stats64.p, sizeof(pairs), cudaMemcpyDeviceToHost, st));
   }
   GS_TRY(cudaMemcpyAsync(ws->h_counters, ws->counters.p, kCntNum * sizeof(uint32_t),

@@ -21,11 +21,10 @@ struct __align__(16) GaussRec {
   float4 r0, r1, r2;
 };
 
-// Camera as the kernels see it.  W, H, TX, TY are the image and its 16x16 tiles (the
-// projection's rectangles live in these tiles).  The rendered pixels form a grid: at
-// stride 1 the image itself; at stride s (grid-sampled supervision, App. D) the compact
-// GW x GH grid whose sample (n, m) is image pixel (ox + n s, oy + m s), binned in 16x16
-// tiles of samples (GTX x GTY).
+// Camera as the kernels see it.  W, H, TX, TY are the image and its 16x16 tiles, in which
+// Gaussians are always binned.  The rendered pixels are the image itself (stride 1) or,
+// for grid-sampled supervision (App. D), the compact GW x GH grid whose sample (n, m) is
+// image pixel (ox + n s, oy + m s).
 struct CamDev {
   int W, H, TX, TY;
   int n_gauss;   // number of Gaussians (bounds check of gathered ids)
@@ -34,17 +33,11 @@ struct CamDev {
   float t[3];
   float near_z;
   int stride, ox, oy;
-  int GW, GH, GTX, GTY;
+  int GW, GH;
 };
 
 // Image pixel coordinate of compact sample index k along an axis with offset o.
 __host__ __device__ inline int grid_coord(int o, int stride, int k) { return o + k * stride; }
-
-// Is image tile (ftx, fty) inside a packed tile rectangle (x0 | y0 << 16, x1 | y1 << 16)?
-__device__ inline bool rect_has(uint2 rc, int ftx, int fty) {
-  return ftx >= (int)(rc.x & 0xFFFFu) && ftx < (int)(rc.y & 0xFFFFu) &&
-         fty >= (int)(rc.x >> 16) && fty < (int)(rc.y >> 16);
-}
 
 // Device status word bits.
 enum : uint32_t {
@@ -66,12 +59,8 @@ enum : int {
 
 // gs_project_fwd.cu
 // Also adds V (visible Gaussians) and I (tile instances) to counters[kCntVisible/kCntInst].
-// On a sample grid (stride > 1) `rect` and `ntiles` describe the Gaussian's rectangle in
-// tiles of samples and `rect_full` receives its image-tile rectangle (the per-sample
-// membership test of the rasterizer); at stride 1 rect_full is not written.
 void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32_t* depth_key,
-                    uint32_t* ntiles, uint2* rect, uint2* rect_full, uint32_t* counters,
-                    cudaStream_t st);
+                    uint32_t* ntiles, uint2* rect, uint32_t* counters, cudaStream_t st);
 
 // gs_sort.cu
 // Scratch of the binning kernels.  ghist (7 x 256 words) and tickets (4 words) are one
@@ -116,8 +105,8 @@ void launch_inst_eff(const uint32_t* n_contrib, int TX, int TY, int W, int H, ui
 constexpr int kMaxOrderedTiles = 1 << 18;
 bool launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t st);
 // Pair counts for the roofline model (stats only): stats64[0] = evaluated, [1] = blended.
-void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* rect_full,
-                       const uint2* ranges, const uint32_t* inst_id, const uint32_t* n_contrib,
+void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* ranges,
+                       const uint32_t* inst_id, const uint32_t* n_contrib,
                        unsigned long long* stats64, cudaStream_t st);
 
 // Persistent raster scheduling: a CTA takes the next tile index from *queue (zeroed
@@ -156,11 +145,9 @@ struct FeatLoss {
 };
 constexpr float kCosEps = 1e-8f;
 
-// rect_full: image-tile rectangles (grid rendering, stride > 1), else null.  loss: the
-// fused feature loss, or null.
+// loss: the fused feature loss, or null.
 void launch_raster_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-                       const uint2* rect_full, const void* feats, int feat_dtype, int D,
-                       const uint2* ranges,
+                       const void* feats, int feat_dtype, int D, const uint2* ranges,
                        const uint32_t* inst_id, float* rgb, float* depth, float* alpha, float* feat,
                        float* T_final, uint32_t* n_contrib, const FeatLoss* loss,
                        cudaStream_t st);
@@ -169,11 +156,28 @@ void launch_raster_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* r
 // Accumulators per Gaussian: g2d[12*i + k], k = u, v, A, B, C, o, r, g, b, z
 constexpr int kG2D = 12;
 void launch_raster_bwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-                       const uint2* rect_full, const void* feats, int feat_dtype,
+                       const void* feats, int feat_dtype,
                        int D, const uint2* ranges, const uint32_t* inst_id, const float* T_final,
                        const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
                        const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,
                        bool features_only, cudaStream_t st);
+
+// gs_raster_grid.cu: rendering on a stride-s sample grid (stride > 1), one warp per work
+// item = (image tile, chunk of up to 32 of the tile's samples), over the image-tile lists.
+int grid_chunks_per_tile(int stride);
+void launch_grid_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const void* feats,
+                     int feat_dtype, int D, const uint2* ranges, const uint32_t* inst_id, float* rgb,
+                     float* depth, float* alpha, float* feat, float* T_final, uint32_t* n_contrib,
+                     const FeatLoss* loss, cudaStream_t st);
+void launch_grid_bwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const void* feats,
+                     int feat_dtype, int D, const uint2* ranges, const uint32_t* inst_id,
+                     const float* T_final, const uint32_t* n_contrib, const float* g_rgb,
+                     const float* g_depth, const float* g_alpha, const float* g_feat, float* g2d,
+                     float* g_feats, bool features_only, cudaStream_t st);
+// Pair counts and I_eff (sum over work items of the longest list prefix) of a grid render.
+void launch_grid_stats(const CamDev& cam, const GaussRec* rec, const uint2* ranges,
+                       const uint32_t* inst_id, const uint32_t* n_contrib, uint32_t* item_max,
+                       uint32_t* counters, unsigned long long* stats64, cudaStream_t st);
 
 // gs_project_bwd.cu
 int project_bwd_blocks(int64_t n);

@@ -126,8 +126,6 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   cd.ox = cd.oy = 0;
   cd.GW = cd.W;
   cd.GH = cd.H;
-  cd.GTX = cd.TX;
-  cd.GTY = cd.TY;
   const int64_t ntl = (int64_t)cd.TX * cd.TY;
   if (scene->n > kNaMaxGauss || (int64_t)c->W * c->H > kNaMaxPix || ntl > kNaMaxTiles)
     return GS_ERR_OVER_BUDGET;
@@ -159,7 +157,7 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   if (cudaMemsetAsync(cnt, 0, kCntNum * 4, st) != cudaSuccess ||
       cudaMemsetAsync(zero, 0, kBinZeroWords * 4, st) != cudaSuccess)
     return GS_ERR_CUDA;
-  launch_project(*scene, cd, rec, key, nt, rect, nullptr, cnt, st);
+  launch_project(*scene, cd, rec, key, nt, rect, cnt, st);
   // the instance count decides whether the request fits: one synchronisation
   uint32_t h_cnt[kCntNum];
   if (cudaMemcpyAsync(h_cnt, cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -183,7 +181,7 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   const bool ordered = launch_tile_order(ranges, (int)ntl, order, st);
   if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GS_ERR_CUDA;
   const TileQueue tq{queue, ordered ? order : nullptr, (int)ntl};
-  launch_raster_fwd(cd, tq, rec, nullptr, scene->feats, scene->feat_dtype, scene->n_feat, ranges, ids, rgb,
+  launch_raster_fwd(cd, tq, rec, scene->feats, scene->feat_dtype, scene->n_feat, ranges, ids, rgb,
                     depth, alpha, scene->n_feat > 0 ? feat : nullptr, Tf, nc, nullptr, st);
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

@@ -47,24 +47,13 @@ __device__ __forceinline__ float clamp_tile(float f, int hi) {
   return fminf(fmaxf(f, 0.f), (float)hi);
 }
 
-__device__ __forceinline__ int ceil_div_signed(int a, int b) {   // b > 0
-  return a >= 0 ? (a + b - 1) / b : -((-a) / b);
-}
-
-// Samples k (0 <= k < G) of one axis of a stride-s grid with offset o whose image
-// coordinate o + k s lies in [lo, hi): the half-open range [*k0, *k1).
-__device__ __forceinline__ void sample_span(int lo, int hi, int o, int s, int G, int* k0, int* k1) {
-  *k0 = max(0, ceil_div_signed(lo - o, s));
-  *k1 = min(G, ceil_div_signed(hi - o, s));
-}
-
 template <int DEG>
 __global__ void __launch_bounds__(kProjThreads)
 k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* __restrict__ scales,
           const float* __restrict__ quats, const float* __restrict__ opac,
           const float* __restrict__ sh, GaussRec* __restrict__ rec,
           uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ntiles,
-          uint2* __restrict__ rect, uint2* __restrict__ rect_full, uint32_t* __restrict__ counters) {
+          uint2* __restrict__ rect, uint32_t* __restrict__ counters) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ __align__(16) float s_mu[kProjThreads * 3];
   __shared__ __align__(16) float s_sc[kProjThreads * 3];
@@ -90,7 +79,7 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
     const float z = ((R[6] * mx + R[7] * my) + R[8] * mz) + cam.t[2];
 
     uint32_t nt = 0;
-    uint2 rc = make_uint2(0, 0), rc_full = make_uint2(0, 0);
+    uint2 rc = make_uint2(0, 0);
     GaussRec g;
     g.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     g.r1 = g.r0;
@@ -178,23 +167,7 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
           nt = (uint32_t)((x1 - x0) * (y1 - y0));
           rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
         }
-        if (valid && rect_full) {
-          // sample grid: the samples whose image tile lies in the rectangle, binned in
-          // 16x16 tiles of samples (integer arithmetic only)
-          rc_full = rc;
-          int n0, n1, m0, m1;
-          sample_span(16 * x0, 16 * x1, cam.ox, cam.stride, cam.GW, &n0, &n1);
-          sample_span(16 * y0, 16 * y1, cam.oy, cam.stride, cam.GH, &m0, &m1);
-          valid = n1 > n0 && m1 > m0;
-          nt = 0u;
-          rc = make_uint2(0u, 0u);
-          if (valid) {
-            const int cx0 = n0 >> 4, cx1 = ((n1 - 1) >> 4) + 1;
-            const int cy0 = m0 >> 4, cy1 = ((m1 - 1) >> 4) + 1;
-            nt = (uint32_t)((cx1 - cx0) * (cy1 - cy0));
-            rc = make_uint2((uint32_t)cx0 | ((uint32_t)cy0 << 16), (uint32_t)cx1 | ((uint32_t)cy1 << 16));
-          }
-        }
+
       }
     }
     if (valid) {
@@ -247,7 +220,6 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
     depth_key[i] = valid ? __float_as_uint(z) : 0xFFFFFFFFu;
     ntiles[i] = nt;
     rect[i] = rc;
-    if (rect_full) rect_full[i] = rc_full;
     cnt_v = valid ? 1u : 0u;
     cnt_i = nt;
   }
@@ -271,15 +243,14 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
 }  // namespace
 
 void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32_t* depth_key,
-                    uint32_t* ntiles, uint2* rect, uint2* rect_full, uint32_t* counters,
-                    cudaStream_t st) {
+                    uint32_t* ntiles, uint2* rect, uint32_t* counters, cudaStream_t st) {
   if (sc.n <= 0) return;
   const int grid = (int)ceil_div(sc.n, kProjThreads);
   switch (sc.sh_degree) {
-    case 0: k_project<0><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, rect_full, counters); break;
-    case 1: k_project<1><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, rect_full, counters); break;
-    case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, rect_full, counters); break;
-    default: k_project<3><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, rect_full, counters); break;
+    case 0: k_project<0><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
+    case 1: k_project<1><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
+    case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
+    default: k_project<3><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
   }
   note_launch();
 }

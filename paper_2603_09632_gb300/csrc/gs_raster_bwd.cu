@@ -21,13 +21,10 @@
 // The next batch's features are fetched into registers during phase 2.  Two barriers
 // per batch.  Each Gaussian receives one 16-byte vector atomic per 4 quantities per tile.
 //
-// On a stride-s sample grid (App. D) a tile is 16x16 samples s image pixels apart; the
-// blended set of each sample is the forward's (same image-tile membership test), and
-// the pixel moments are taken in image pixels (offsets scaled by s).
-//
 // Features-only variant (FO, the semantic phase of Sec. 3.2 where geometry and colour are
-// frozen): only dL/df_i = sum_p w_i g_F is needed, so phase 1 keeps just the weights,
-// phase 2b and every geometry accumulator are skipped.
+// frozen): only dL/df_i = sum_p w_i g_F is needed, so phase 1 keeps just the weights, the
+// features themselves are not fetched, and phase 2b and every geometry accumulator are
+// skipped.
 #include "gs_blend.cuh"
 #include "gs_internal.cuh"
 
@@ -49,7 +46,7 @@ struct BwdCfg {
   static constexpr size_t smem_floats =
       (size_t)kT * ES           // s_E: upstream feature gradient per pixel
       + (size_t)(FO ? 1 : 3) * B * kWS   // s_W (and s_GS, s_GO unless FO), j-major
-      + (size_t)2 * B * DP      // s_f: batch features, double buffered
+      + (size_t)(FO ? 0 : 2) * B * DP   // s_f: batch features, double buffered (not when FO)
       + (size_t)B * DP;         // s_outF: batch feature-gradient sums
 };
 
@@ -128,10 +125,10 @@ __device__ __forceinline__ void red_add4(float* dst, float a, float b, float c, 
   atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a, b, c, d));
 }
 
-template <int DP, bool BF16, bool GRID, bool FO>
+template <int DP, bool BF16, bool FO>
 __global__ void __launch_bounds__(kT, 2)
 k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
-             const uint2* __restrict__ rect_full, const void* __restrict__ feats, int D,
+             const void* __restrict__ feats, int D,
              const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_id,
              const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
              const float* __restrict__ g_rgb, const float* __restrict__ g_depth,
@@ -142,7 +139,6 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   __shared__ float4 s_r0[kT], s_r1[kT], s_r2[kT];   // compacted records of the chunk
   __shared__ uint32_t s_id[kT];
   __shared__ int s_orig[kT];                        // list position of each compacted entry
-  __shared__ uint2 s_rc[GRID ? kT : 1];             // image-tile rectangles (sample grids)
   __shared__ float4 s_E4[kT];                       // (g_r, g_g, g_b, g_depth) per pixel
   __shared__ int s_wc[8];
   __shared__ unsigned s_live[8];                    // per warp strip: batch entries that can reach it
@@ -153,12 +149,9 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   float* s_GS = s_W + B * kWS;                // (not allocated when FO)
   float* s_GO = s_GS + B * kWS;
   float* s_fb = s_W + (FO ? 1 : 3) * B * kWS; // [2][B][DP]
-  float* s_outF = s_fb + 2 * B * DP;          // [B][DP]
+  float* s_outF = s_fb + (FO ? 0 : 2) * B * DP;   // [B][DP]
 
   const int t = threadIdx.x;
-  // sample-grid geometry (the image itself unless GRID)
-  const int step = GRID ? cam.stride : 1, gox = GRID ? cam.ox : 0, goy = GRID ? cam.oy : 0;
-  const float sf = (float)step;
   __shared__ int s_tile;
   // persistent CTA: tiles from the queue, heaviest first
   for (;;) {
@@ -169,20 +162,16 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     __syncthreads();
     const int tile = s_tile;
     if (tile < 0) break;
-    // sample (sn, sm) of the rendered grid is image pixel (px, py)
-    const int tx0 = (tile % cam.GTX) * kTile, ty0 = (tile / cam.GTX) * kTile;
-    const int sn = tx0 + (t & 15), sm = ty0 + (t >> 4);
-    const int px = grid_coord(gox, step, sn), py = grid_coord(goy, step, sm);
-    const bool inside = sn < cam.GW && sm < cam.GH;
-    const int ftx = px >> 4, fty = py >> 4;
+    const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
+    const int px = tx0 + (t & 15), py = ty0 + (t >> 4);
+    const bool inside = px < cam.W && py < cam.H;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
     const int lane = t & 31;
-    // pixel-centre boxes of the tile and of this warp's 16 x 2 strip of samples
-    const float bx0 = (float)grid_coord(gox, step, tx0) + 0.5f;
-    const float by0 = (float)grid_coord(goy, step, ty0) + 0.5f;
-    const float wbx0 = bx0, wby0 = by0 + (float)(2 * (t >> 5)) * sf;
-    const int64_t HW = (int64_t)cam.GW * cam.GH;
-    const int64_t p = (int64_t)sm * cam.GW + sn;
+    // pixel-centre boxes of the tile and of this warp's 16 x 2 strip
+    const float bx0 = (float)tx0 + 0.5f, by0 = (float)ty0 + 0.5f;
+    const float wbx0 = bx0, wby0 = (float)(ty0 + 2 * (t >> 5)) + 0.5f;
+    const int64_t HW = (int64_t)cam.W * cam.H;
+    const int64_t p = (int64_t)py * cam.W + px;
     const uint2 rg = ranges[tile];
     const int start = (int)rg.x;
 
@@ -235,8 +224,8 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       if (t < c1 - c0 && id < (uint32_t)cam.n_gauss) {
         g = rec[id];
         g.r1.w = sigma_cut(g.r1.y);
-        keep = box_min_sigma(bx0, by0, bx0 + 15.f * sf, by0 + 15.f * sf, g.r0.x, g.r0.y, g.r0.z,
-                             g.r0.w, g.r1.x) <= g.r1.w;
+        keep = box_min_sigma(bx0, by0, bx0 + 15.f, by0 + 15.f, g.r0.x, g.r0.y, g.r0.z, g.r0.w,
+                             g.r1.x) <= g.r1.w;
       }
       int nk;
       const int pos = block_compact_index(keep, s_wc, &nk);
@@ -246,11 +235,10 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         s_r2[pos] = g.r2;
         s_id[pos] = id;
         s_orig[pos] = c0 + t;
-        if (GRID) s_rc[pos] = rect_full[id];
       }
       __syncthreads();
       FeatBatch<DP, BF16, B> fb;
-      if constexpr (DP > 0) {
+      if constexpr (DP > 0 && !FO) {
         fb.fetch(feats, D, s_id, max(0, nk - B), min(B, nk));
         fb.store(D, s_fb);
         __syncthreads();
@@ -265,7 +253,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         bool hit = false;
         if (lane < bc) {
           const float4 q0 = s_r0[jb0 + lane], q1 = s_r1[jb0 + lane];
-          hit = box_min_sigma(wbx0, wby0, wbx0 + 15.f * sf, wby0 + sf, q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
+          hit = box_min_sigma(wbx0, wby0, wbx0 + 15.f, wby0 + 1.f, q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
         }
         const unsigned live = __ballot_sync(0xffffffffu, hit);
         if (lane == 0) s_live[t >> 5] = live;   // phase 2 skips (Gaussian, strip) pairs not live
@@ -273,8 +261,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         // phase 1: per pixel, reverse over the batch
         for (int j = B - 1; j >= 0; --j) {
           float w = 0.f, gs = 0.f, go = 0.f;
-          if ((live >> j & 1u) && s_orig[jb0 + j] < nc &&
-              (!GRID || rect_has(s_rc[jb0 + j], ftx, fty))) {
+          if ((live >> j & 1u) && s_orig[jb0 + j] < nc) {
             const float4 r0 = s_r0[jb0 + j];
             const float4 r1 = s_r1[jb0 + j];
             const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
@@ -322,7 +309,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
 
         // next batch's features: fetch now, store after phase 2
         const bool more = jb0 > 0;
-        if constexpr (DP > 0) {
+        if constexpr (DP > 0 && !FO) {
           if (more) fb.fetch(feats, D, s_id, max(0, jb0 - B), min(B, jb0));
         }
 
@@ -386,7 +373,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             if (!(s_live[q >> 5] >> j & 1u)) continue;   // uniform over the G lanes of j
             const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
             const float4 e = s_E4[q];
-            const float x = ((float)(q & 15) - 7.5f) * sf, y = ((float)(q >> 4) - 7.5f) * sf;
+            const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;
             m1 += gs;
             mx = fmaf(gs, x, mx);
             my = fmaf(gs, y, my);
@@ -417,7 +404,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             const float4 r0 = s_r0[jb0 + j];
             const float4 r1 = s_r1[jb0 + j];
             // moments are about the tile centre: pixel offset dx = x - uc with uc = u - centre
-            const float uc = r0.x - (bx0 + 7.5f * sf), vc = r0.y - (by0 + 7.5f * sf);
+            const float uc = r0.x - ((float)tx0 + 8.f), vc = r0.y - ((float)ty0 + 8.f);
             const float A = r0.z, Bq = r0.w, C = r1.x;
             const float sdx = mx - uc * m1, sdy = my - vc * m1;            // sum gs dx, sum gs dy
             const float sdxx = mxx - 2.f * uc * mx + uc * uc * m1;         // sum gs dx^2
@@ -431,7 +418,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             red_add4(dst + 8, sb, sz, 0.f, 0.f);
           }
         }
-        if constexpr (DP > 0) {
+        if constexpr (DP > 0 && !FO) {
           if (more) fb.store(D, s_fb + ((bi + 1) & 1) * B * DP);
         }
         __syncthreads();
@@ -462,79 +449,61 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   }
 }
 
-template <int DP, bool BF16, bool GRID, bool FO>
-void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const uint2* rect_full,
-              const void* feats, int D, const uint2* ranges, const uint32_t* inst_id,
-              const float* T_final,
-              const uint32_t* n_contrib,
-              const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
-              float* g2d, float* g_feats, cudaStream_t st) {
+template <int DP, bool BF16, bool FO>
+void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const void* feats, int D,
+              const uint2* ranges, const uint32_t* inst_id, const float* T_final,
+              const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
+              const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,
+              cudaStream_t st) {
   const size_t smem = sizeof(float) * BwdCfg<DP, FO>::smem_floats;
-  auto kern = k_raster_bwd<DP, BF16, GRID, FO>;
+  auto kern = k_raster_bwd<DP, BF16, FO>;
   const int grid = persistent_grid(kern, kT, smem, tq.n_tiles);
-  kern<<<grid, kT, smem, st>>>(cam, tq, rec, rect_full, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,
+  kern<<<grid, kT, smem, st>>>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,
                                g_depth, g_alpha, g_feat, g2d, g_feats);
   note_launch();
 }
 
 // Dispatch of the run-time options to the kernel variants (features-only needs features).
-template <int DP, bool BF16, bool GRID>
-void launch_f(bool fo, const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-              const uint2* rect_full, const void* feats, int D, const uint2* ranges,
-              const uint32_t* inst_id, const float* T_final, const uint32_t* n_contrib,
-              const float* g_rgb, const float* g_depth, const float* g_alpha, const float* g_feat,
-              float* g2d, float* g_feats, cudaStream_t st) {
+template <int DP>
+void launch_dp(bool bf, bool fo, const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
+               const void* feats, int D, const uint2* ranges, const uint32_t* inst_id,
+               const float* T_final, const uint32_t* n_contrib, const float* g_rgb,
+               const float* g_depth, const float* g_alpha, const float* g_feat, float* g2d,
+               float* g_feats, cudaStream_t st) {
   if constexpr (DP > 0) {
     if (fo) {
-      launch_t<DP, BF16, GRID, true>(cam, tq, rec, rect_full, feats, D, ranges, inst_id, T_final,
-                                     n_contrib, g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
+      if (bf)
+        launch_t<DP, true, true>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib,
+                                 g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
+      else
+        launch_t<DP, false, true>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib,
+                                  g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
       return;
     }
   }
-  launch_t<DP, BF16, GRID, false>(cam, tq, rec, rect_full, feats, D, ranges, inst_id, T_final,
-                                  n_contrib, g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
-}
-
-template <int DP>
-void launch_dp(bool bf, bool grid, bool fo, const CamDev& cam, const TileQueue& tq,
-               const GaussRec* rec, const uint2* rect_full, const void* feats, int D,
-               const uint2* ranges, const uint32_t* inst_id, const float* T_final,
-               const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
-               const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,
-               cudaStream_t st) {
-  if (bf) {
-    if (grid)
-      launch_f<DP, true, true>(fo, cam, tq, rec, rect_full, feats, D, ranges, inst_id, T_final,
-                               n_contrib, g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
-    else
-      launch_f<DP, true, false>(fo, cam, tq, rec, rect_full, feats, D, ranges, inst_id, T_final,
-                                n_contrib, g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
-  } else {
-    if (grid)
-      launch_f<DP, false, true>(fo, cam, tq, rec, rect_full, feats, D, ranges, inst_id, T_final,
-                                n_contrib, g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
-    else
-      launch_f<DP, false, false>(fo, cam, tq, rec, rect_full, feats, D, ranges, inst_id, T_final,
-                                 n_contrib, g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
-  }
+  if (bf)
+    launch_t<DP, true, false>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,
+                              g_depth, g_alpha, g_feat, g2d, g_feats, st);
+  else
+    launch_t<DP, false, false>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,
+                               g_depth, g_alpha, g_feat, g2d, g_feats, st);
 }
 
 }  // namespace
 
 void launch_raster_bwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-                       const uint2* rect_full, const void* feats, int feat_dtype, int D,
-                       const uint2* ranges, const uint32_t* inst_id, const float* T_final,
-                       const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
-                       const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,
-                       bool features_only, cudaStream_t st) {
-  if (cam.GTX * cam.GTY == 0) return;
+                       const void* feats, int feat_dtype, int D, const uint2* ranges,
+                       const uint32_t* inst_id, const float* T_final, const uint32_t* n_contrib,
+                       const float* g_rgb, const float* g_depth, const float* g_alpha,
+                       const float* g_feat, float* g2d, float* g_feats, bool features_only,
+                       cudaStream_t st) {
+  if (cam.TX * cam.TY == 0) return;
   const bool bf = feat_dtype == GS_BF16;
-  const bool grid = rect_full != nullptr;
   const int DP = g_feat ? padded_feat(D) : 0;
   const bool fo = features_only && DP > 0 && g_feats;
-#define GS_BWD(dp)                                                                              \
-  launch_dp<dp>(bf, grid, fo, cam, tq, rec, rect_full, feats, D, ranges, inst_id, T_final,       \
-                n_contrib, g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st)
+#define GS_BWD(dp)                                                                         \
+  launch_dp<dp>(bf, fo, cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb, \
+                g_depth, g_alpha, g_feat, g2d, g_feats, st)
   switch (DP) {
     case 0: GS_BWD(0); break;
     case 8: GS_BWD(8); break;

@@ -2,11 +2,6 @@
 // Gaussians), depth by substituting c_i -> d_i (App. B) and features by c_i -> f_i
 // (Sec. 3.1).  One 256-thread CTA per 16x16 tile, one thread per pixel.
 //
-// The pixels are the image (stride 1) or a stride-s sample grid (grid-sampled
-// supervision, App. D): a tile is then 16x16 samples spread over 16s x 16s image pixels,
-// and a Gaussian of the tile's list blends only at the samples whose image tile lies in
-// its 3-sigma tile rectangle, so every sample gets exactly its full-resolution value.
-//
 // The tile's sorted list is consumed in batches of 256 Gaussians staged in shared
 // memory (records gathered by id; features converted to fp32 once per batch, so bf16
 // storage costs no per-pixel conversion).  A warp skips the colour/feature update of a
@@ -65,10 +60,9 @@ __device__ __forceinline__ void stage_features(const void* __restrict__ feats, i
   }
 }
 
-template <int DP, bool BF16, bool GRID, bool LOSS>
+template <int DP, bool BF16, bool LOSS>
 __global__ void __launch_bounds__(kB)
 k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
-             const uint2* __restrict__ rect_full,
              const void* __restrict__ feats, int D, const uint2* __restrict__ ranges,
              const uint32_t* __restrict__ inst_id, float* __restrict__ rgb,
              float* __restrict__ depth, float* __restrict__ alpha, float* __restrict__ feat,
@@ -76,13 +70,9 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   __shared__ float4 s_r0[kB], s_r1[kB], s_r2[kB];
   __shared__ uint32_t s_id[kB];
   __shared__ int s_orig[kB];
-  __shared__ uint2 s_rc[GRID ? kB : 1];             // image-tile rectangles (sample grids)
   __shared__ int s_wc[8];
   __shared__ int s_tile;
   extern __shared__ __align__(16) float s_feat[];   // [kB][DP]
-  // sample-grid geometry (the image itself unless GRID)
-  const int step = GRID ? cam.stride : 1, gox = GRID ? cam.ox : 0, goy = GRID ? cam.oy : 0;
-  const float sf = (float)step;
   double l1_sum = 0.0, cos_sum = 0.0;   // fused loss (LOSS): this thread's samples, all tiles
 
   // persistent CTA: tiles from the queue, heaviest first
@@ -95,28 +85,24 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     const int tile = s_tile;
     if (tile < 0) break;
 
-    // sample (sn, sm) of the rendered grid is image pixel (px, py)
-    const int tx0 = (tile % cam.GTX) * kTile, ty0 = (tile / cam.GTX) * kTile;
-    const int sn = tx0 + (threadIdx.x & 15), sm = ty0 + (threadIdx.x >> 4);
-    const int px = grid_coord(gox, step, sn), py = grid_coord(goy, step, sm);
-    const bool inside = sn < cam.GW && sm < cam.GH;
-    const bool in_image = inside && px < cam.W && py < cam.H;
-    const int ftx = px >> 4, fty = py >> 4;
+    const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
+    const int px = tx0 + (threadIdx.x & 15);
+    const int py = ty0 + (threadIdx.x >> 4);
+    const bool inside = px < cam.W && py < cam.H;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
     const uint2 rg = ranges[tile];
     const int start = (int)rg.x, end = (int)rg.y;
     const int lane = threadIdx.x & 31;
-    // pixel-centre boxes of the tile and of this warp's 16 x 2 strip of samples
-    const float bx0 = (float)grid_coord(gox, step, tx0) + 0.5f;
-    const float by0 = (float)grid_coord(goy, step, ty0) + 0.5f;
-    const float wbx0 = bx0, wby0 = by0 + (float)(2 * (threadIdx.x >> 5)) * sf;
+    // pixel-centre boxes of the tile and of this warp's 16 x 2 strip
+    const float bx0 = (float)tx0 + 0.5f, by0 = (float)ty0 + 0.5f;
+    const float wbx0 = bx0, wby0 = (float)(ty0 + 2 * (threadIdx.x >> 5)) + 0.5f;
 
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
     float acc[DP > 0 ? DP : 1];
 #pragma unroll
     for (int c = 0; c < (DP > 0 ? DP : 1); ++c) acc[c] = 0.f;
     int last = 0;
-    bool done = !in_image;
+    bool done = !inside;
 
     for (int b0 = start; b0 < end; b0 += kB) {
       if (__syncthreads_count(done) == kB) break;
@@ -129,8 +115,8 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       if ((int)threadIdx.x < cnt && id < (uint32_t)cam.n_gauss) {
         g = rec[id];
         g.r1.w = sigma_cut(g.r1.y);
-        keep = box_min_sigma(bx0, by0, bx0 + 15.f * sf, by0 + 15.f * sf, g.r0.x, g.r0.y, g.r0.z,
-                             g.r0.w, g.r1.x) <= g.r1.w;
+        keep = box_min_sigma(bx0, by0, bx0 + 15.f, by0 + 15.f, g.r0.x, g.r0.y, g.r0.z, g.r0.w,
+                             g.r1.x) <= g.r1.w;
       }
       int nk;
       const int pos = block_compact_index(keep, s_wc, &nk);
@@ -140,7 +126,6 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         s_r2[pos] = g.r2;
         s_id[pos] = id;
         s_orig[pos] = b0 + (int)threadIdx.x - start;
-        if (GRID) s_rc[pos] = rect_full[id];
       }
       __syncthreads();
       stage_features<DP, BF16>(feats, D, s_id, nk, s_feat);
@@ -152,7 +137,7 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         bool hit = false;
         if (g0 + lane < nk) {
           const float4 q0 = s_r0[g0 + lane], q1 = s_r1[g0 + lane];
-          hit = box_min_sigma(wbx0, wby0, wbx0 + 15.f * sf, wby0 + sf, q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
+          hit = box_min_sigma(wbx0, wby0, wbx0 + 15.f, wby0 + 1.f, q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
         }
         unsigned live = __ballot_sync(0xffffffffu, hit);
       while (live) {
@@ -161,7 +146,7 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         const float4 r0 = s_r0[j];
         const float4 r1 = s_r1[j];
         float w = 0.f;
-        if (!done && (!GRID || rect_has(s_rc[j], ftx, fty))) {
+        if (!done) {
           const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
           if (sigma >= 0.f && sigma <= r1.w) {
             const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
@@ -200,8 +185,8 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       }
     }
     if (inside) {
-      const int64_t HW = (int64_t)cam.GW * cam.GH;
-      const int64_t p = (int64_t)sm * cam.GW + sn;
+      const int64_t HW = (int64_t)cam.W * cam.H;
+      const int64_t p = (int64_t)py * cam.W + px;
       if (rgb) {
         rgb[p] = c0;
         rgb[HW + p] = c1;
@@ -225,8 +210,8 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       // the target nor the rendered features need a second register copy.
       __syncthreads();   // every warp is done with the batch features in s_feat
       if (inside) {
-        const int64_t HW = (int64_t)cam.GW * cam.GH;
-        const int64_t p = (int64_t)sm * cam.GW + sn;
+        const int64_t HW = (int64_t)cam.W * cam.H;
+        const int64_t p = (int64_t)py * cam.W + px;
         const float V = fl.mask ? __ldg(fl.mask + p) : 1.f;
         float dot = 0.f, aa = 0.f, bb = 0.f, l1 = 0.f;
 #pragma unroll
@@ -288,57 +273,42 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   }
 }
 
-template <int DP, bool BF16, bool GRID, bool LOSS>
-void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const uint2* rect_full,
-              const void* feats, int D, const uint2* ranges, const uint32_t* inst_id, float* rgb,
-              float* depth, float* alpha, float* feat, float* T_final, uint32_t* n_contrib,
-              const FeatLoss& fl, cudaStream_t st) {
+template <int DP, bool BF16, bool LOSS>
+void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const void* feats, int D,
+              const uint2* ranges, const uint32_t* inst_id, float* rgb, float* depth, float* alpha,
+              float* feat, float* T_final, uint32_t* n_contrib, const FeatLoss& fl,
+              cudaStream_t st) {
   const size_t smem = sizeof(float) * kB * DP;
-  auto kern = k_raster_fwd<DP, BF16, GRID, LOSS>;
+  auto kern = k_raster_fwd<DP, BF16, LOSS>;
   const int grid = persistent_grid(kern, kB, smem, tq.n_tiles);
-  kern<<<grid, kB, smem, st>>>(cam, tq, rec, rect_full, feats, D, ranges, inst_id, rgb, depth,
-                               alpha, feat, T_final, n_contrib, fl);
+  kern<<<grid, kB, smem, st>>>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
+                               T_final, n_contrib, fl);
   note_launch();
 }
 
 // Dispatch of the run-time options to the kernel variants (the loss needs features).
-template <int DP, bool BF16, bool GRID>
-void launch_l(bool loss, const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-              const uint2* rect_full, const void* feats, int D, const uint2* ranges,
-              const uint32_t* inst_id, float* rgb, float* depth, float* alpha, float* feat,
-              float* T_final, uint32_t* n_contrib, const FeatLoss& fl, cudaStream_t st) {
+template <int DP>
+void launch_dp(bool bf, bool loss, const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
+               const void* feats, int D, const uint2* ranges, const uint32_t* inst_id, float* rgb,
+               float* depth, float* alpha, float* feat, float* T_final, uint32_t* n_contrib,
+               const FeatLoss& fl, cudaStream_t st) {
   if constexpr (DP > 0) {
     if (loss) {
-      launch_t<DP, BF16, GRID, true>(cam, tq, rec, rect_full, feats, D, ranges, inst_id, rgb,
-                                     depth, alpha, feat, T_final, n_contrib, fl, st);
+      if (bf)
+        launch_t<DP, true, true>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
+                                 T_final, n_contrib, fl, st);
+      else
+        launch_t<DP, false, true>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
+                                  T_final, n_contrib, fl, st);
       return;
     }
   }
-  launch_t<DP, BF16, GRID, false>(cam, tq, rec, rect_full, feats, D, ranges, inst_id, rgb, depth,
-                                  alpha, feat, T_final, n_contrib, fl, st);
-}
-
-template <int DP>
-void launch_dp(bool bf, bool grid, bool loss, const CamDev& cam, const TileQueue& tq,
-               const GaussRec* rec, const uint2* rect_full, const void* feats, int D,
-               const uint2* ranges, const uint32_t* inst_id, float* rgb, float* depth,
-               float* alpha, float* feat, float* T_final, uint32_t* n_contrib, const FeatLoss& fl,
-               cudaStream_t st) {
-  if (bf) {
-    if (grid)
-      launch_l<DP, true, true>(loss, cam, tq, rec, rect_full, feats, D, ranges, inst_id, rgb, depth,
-                               alpha, feat, T_final, n_contrib, fl, st);
-    else
-      launch_l<DP, true, false>(loss, cam, tq, rec, rect_full, feats, D, ranges, inst_id, rgb, depth,
-                                alpha, feat, T_final, n_contrib, fl, st);
-  } else {
-    if (grid)
-      launch_l<DP, false, true>(loss, cam, tq, rec, rect_full, feats, D, ranges, inst_id, rgb, depth,
-                                alpha, feat, T_final, n_contrib, fl, st);
-    else
-      launch_l<DP, false, false>(loss, cam, tq, rec, rect_full, feats, D, ranges, inst_id, rgb,
-                                 depth, alpha, feat, T_final, n_contrib, fl, st);
-  }
+  if (bf)
+    launch_t<DP, true, false>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
+                              T_final, n_contrib, fl, st);
+  else
+    launch_t<DP, false, false>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
+                               T_final, n_contrib, fl, st);
 }
 
 }  // namespace
@@ -352,22 +322,20 @@ int padded_feat(int D) {
 }
 
 void launch_raster_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-                       const uint2* rect_full, const void* feats, int feat_dtype, int D,
-                       const uint2* ranges,
+                       const void* feats, int feat_dtype, int D, const uint2* ranges,
                        const uint32_t* inst_id, float* rgb, float* depth, float* alpha, float* feat,
                        float* T_final, uint32_t* n_contrib, const FeatLoss* loss,
                        cudaStream_t st) {
-  if (cam.GTX * cam.GTY == 0) return;
+  if (cam.TX * cam.TY == 0) return;
   const bool bf = feat_dtype == GS_BF16;
-  const bool grid = rect_full != nullptr;
   FeatLoss fl{};
   if (loss && D > 0) fl = *loss;
   // features are blended when written or when the fused loss needs them
   const int DP = (feat || fl.target) ? padded_feat(D) : 0;
   const bool loss_on = fl.target != nullptr;
-#define GS_FWD(dp)                                                                        \
-  launch_dp<dp>(bf, grid, loss_on, cam, tq, rec, rect_full, feats, D, ranges, inst_id, rgb, \
-                depth, alpha, feat, T_final, n_contrib, fl, st)
+#define GS_FWD(dp)                                                                           \
+  launch_dp<dp>(bf, loss_on, cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat, \
+                T_final, n_contrib, fl, st)
   switch (DP) {
     case 0: GS_FWD(0); break;
     case 8: GS_FWD(8); break;

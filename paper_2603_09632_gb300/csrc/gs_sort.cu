@@ -384,21 +384,19 @@ k_tile_order(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict
 // of them it blended, summed over the image into stats64[0..1].  The opacity test is the
 // rasterizer's own (gs_blend.cuh).
 __global__ void __launch_bounds__(kThreads)
-k_pair_stats(CamDev cam, const GaussRec* __restrict__ rec, const uint2* __restrict__ rect_full,
-             const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_id,
-             const uint32_t* __restrict__ n_contrib, unsigned long long* __restrict__ stats64) {
+k_pair_stats(CamDev cam, const GaussRec* __restrict__ rec, const uint2* __restrict__ ranges,
+             const uint32_t* __restrict__ inst_id, const uint32_t* __restrict__ n_contrib,
+             unsigned long long* __restrict__ stats64) {
   const int tile = blockIdx.x;
-  const int sn = (tile % cam.GTX) * 16 + (threadIdx.x & 15), sm = (tile / cam.GTX) * 16 + (threadIdx.x >> 4);
-  const int px = grid_coord(cam.ox, cam.stride, sn), py = grid_coord(cam.oy, cam.stride, sm);
+  const int px = (tile % cam.TX) * 16 + (threadIdx.x & 15), py = (tile / cam.TX) * 16 + (threadIdx.x >> 4);
   uint32_t eval = 0, blend = 0;
-  if (sn < cam.GW && sm < cam.GH && px < cam.W && py < cam.H) {
-    const uint32_t nc = n_contrib[(int64_t)sm * cam.GW + sn];
+  if (px < cam.W && py < cam.H) {
+    const uint32_t nc = n_contrib[(int64_t)py * cam.W + px];
     const uint2 rg = ranges[tile];
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
     for (uint32_t k = 0; k < nc && rg.x + k < rg.y; ++k) {
       const uint32_t id = inst_id[rg.x + k];
       if (id >= (uint32_t)cam.n_gauss) continue;
-      if (rect_full && !rect_has(rect_full[id], px >> 4, py >> 4)) continue;
       const float4 r0 = rec[id].r0, r1 = rec[id].r1;
       ++eval;
       const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
@@ -523,13 +521,12 @@ void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int
   note_launch();
 }
 
-void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* rect_full,
-                       const uint2* ranges, const uint32_t* inst_id, const uint32_t* n_contrib,
+void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* ranges,
+                       const uint32_t* inst_id, const uint32_t* n_contrib,
                        unsigned long long* stats64, cudaStream_t st) {
   cudaMemsetAsync(stats64, 0, 2 * sizeof(unsigned long long), st);
-  if (cam.GTX * cam.GTY == 0) return;
-  k_pair_stats<<<cam.GTX * cam.GTY, kThreads, 0, st>>>(cam, rec, rect_full, ranges, inst_id, n_contrib,
-                                                       stats64);
+  if (cam.TX * cam.TY == 0) return;
+  k_pair_stats<<<cam.TX * cam.TY, kThreads, 0, st>>>(cam, rec, ranges, inst_id, n_contrib, stats64);
   note_launch();
 }
 
