@@ -42,6 +42,12 @@ WORKLOADS = {
 # Semantic distillation phase (Sec. 3.2, App. D): grid-sampled rendering with random offsets,
 # region-indexed targets, the masked L1 + cosine loss fused into the forward, and the
 # features-only backward (geometry frozen).  Stride 1 is the same phase at full resolution.
+# VQ pixel decode (Sec. 3.2, App. E): softmax weights of 64 logits per Gaussian rendered as
+# 64 bf16 channels, then F = E^T w(x) (512-d) and the prompt relevance on the tensor cores.
+WORKLOADS["vq_decode_1200x680_1m"] = dict(
+    make=lambda: S.config_semantic(n_poses=100), bf16=True, l1=False, vq=(64, 512),
+    desc="room 1M Gaussians, 64 VQ logits -> bf16 weights rendered at 1200x680, "
+         "decode F = E^T w(x) to 512-d fp32 + prompt relevance (tcgen05 tf32)")
 for _s in (1, 2, 4):
     WORKLOADS[f"semantic_grid_s{_s}_1200x680_1m"] = dict(
         make=lambda: S.config_semantic(n_poses=100), bf16=True, l1=False, grid=_s,
@@ -133,6 +139,7 @@ KERNEL_SOURCES = {
     "bin": ["gs_sort.cu", "gs_internal.cuh"],
     "project": ["gs_project_fwd.cu", "gs_internal.cuh"],
     "bwd_project": ["gs_project_bwd.cu", "gs_internal.cuh"],
+    "vq_decode": ["gs_vq.cu", "gs_internal.cuh"],
 }
 
 
@@ -656,6 +663,138 @@ def run_grid(args):
         dist.destroy_process_group()
 
 
+def run_vq(args):
+    """VQ decode step: softmax weights (N x L) -> project -> bin (no sync) -> render the
+    weights as L bf16 channels -> tensor-core decode writing F [D, H, W] and the relevance
+    map.  The roofline is the decode kernel's, timed alone with CUDA events."""
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    from paper_2603_09632_gb300.render import as_camera
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = WORKLOADS[args.workload]
+    Lw, Dc = wl["vq"]
+    scene_np, cams = wl["make"]()
+    H, W = cams[0].H, cams[0].W
+    P = H * W
+    rng = np.random.default_rng(11)
+
+    def dev_t(a, dtype=torch.float32):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev).to(dtype)
+
+    n = scene_np.n
+    logits = dev_t(rng.normal(scale=2.0, size=(n, Lw)).astype(np.float32))
+    wts = torch.empty((n, Lw), device=dev, dtype=torch.bfloat16)
+    scene = L.Scene(dev_t(scene_np.means), dev_t(scene_np.scales), dev_t(scene_np.quats),
+                    dev_t(scene_np.opacities), dev_t(scene_np.sh), wts)
+    E = dev_t((rng.normal(size=(Lw, Dc)) / 8.0).astype(np.float32))
+    text = rng.normal(size=(5, Dc))
+    text = dev_t((text / np.linalg.norm(text, axis=1, keepdims=True)).astype(np.float32))
+    wmap = torch.empty((Lw, H, W), device=dev)
+    F = torch.empty((Dc, H, W), device=dev)
+    R = torch.empty((H, W), device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    gcams = [as_camera(c) for c in cams]
+    ws = L.Workspace(local)
+    stream = torch.cuda.current_stream()
+    L.gs_vq_weights(logits, wts)
+    max_inst = 0
+    for c in gcams:
+        L.gs_project(scene, c, ws)
+        max_inst = max(max_inst, L.gs_bin_tiles(ws, sync=True))
+    L.gs_workspace_reserve(ws, n, int(max_inst * 1.25) + 1024, P)
+    dec = []
+
+    def step(c, k):
+        L.gs_vq_weights(logits, wts, stream)
+        L.gs_project(scene, c, ws, stream)
+        L.gs_bin_tiles(ws, sync=False, stream=stream)
+        L.gs_render_fwd(scene, c, ws, None, None, None, wmap, stream)
+        a, b = dec[k]
+        a.record(stream)
+        L.gs_vq_decode(wmap, E, F_out=F, text=text, tau=10.0, relevance=R, err=err, stream=stream)
+        b.record(stream)
+
+    nsteps = args.warmup + args.steps
+    dec = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(nsteps)]
+    poses = [(rank * 37 + k) % len(gcams) for k in range(nsteps)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    for k in range(args.warmup):
+        step(gcams[poses[k]], k)
+        flush.fill_(float(k))
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = make_clock_sampler(dev, local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = L.gs_launch_count()
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step(gcams[poses[args.warmup + k]], args.warmup + k)
+        evs[k][1].record(stream)
+        flush.fill_(float(k))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = L.gs_launch_count() - n0
+    clk = clocks.stop()
+    if int(err.item()) != 0:
+        raise RuntimeError("tensor-core decode reported a timed-out wait")
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    dec_ms = sum(dec[args.warmup + k][0].elapsed_time(dec[args.warmup + k][1])
+                 for k in range(args.steps)) / args.steps
+    value = world * args.steps * P / (ms * 1e-3) / 1e6
+    peaks, src = load_peaks()
+    alg_bytes = P * (Lw * 4 + Dc * 4 + 4)
+    alg_flops = 2.0 * P * Lw * Dc + P * Dc * 2 * 6
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+    achieved_b = alg_bytes / (dec_ms * 1e-3) / 1e9
+    achieved_f = alg_flops / (dec_ms * 1e-3) / 1e12
+    t_hbm = alg_bytes / (peaks["hbm_gbs"] * 1e9)
+    t_tc = alg_flops / (tf32_peak * 1e12)
+    if t_hbm >= t_tc:
+        roofline = {"bound": "hbm", "kernel": "k_vq_decode", "achieved": round(achieved_b, 1),
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": round(achieved_b / peaks["hbm_gbs"], 4), "peak_source": src}
+    else:
+        roofline = {"bound": "tensor", "kernel": "k_vq_decode", "achieved": round(achieved_f, 2),
+                    "peak": round(tf32_peak, 1), "unit": "TFLOP/s",
+                    "frac": round(achieved_f / tf32_peak, 4),
+                    "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+    roofline.update({"traffic": captured_traffic("vq_decode", args.workload),
+                     "alg_bytes": int(alg_bytes), "alg_flops": int(alg_flops),
+                     "decode_ms": round(dec_ms, 4),
+                     "tensor_frac": round(achieved_f / tf32_peak, 4),
+                     "hbm_frac": round(achieved_b / peaks["hbm_gbs"], 4)})
+    line = {
+        "metric": "Mpix/s VQ weights + render + tensor-core decode (F 512-d + relevance)",
+        "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32 decode, f32 accumulate", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "gaussians": n, "L": Lw, "D": Dc,
+                   "pixels_per_step": P, "l2": "flushed (256 MiB write) between steps"},
+        "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def oracle_step(O, scene_np, cam, pixels):
@@ -985,6 +1124,8 @@ def main():
         run_serve(args)
     elif "grid" in WORKLOADS[args.workload]:
         run_grid(args)
+    elif "vq" in WORKLOADS[args.workload]:
+        run_vq(args)
     else:
         run_gpu(args)
 

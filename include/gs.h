@@ -215,6 +215,37 @@ gs_status gs_grid_target_resample(const float* fmap, int32_t D, int32_t Hf, int3
                                   int32_t W, int32_t stride, int32_t off_x, int32_t off_y,
                                   float* target, float* mask, void* stream);
 
+/* ---- VQ semantic parameterisation and decode (NEXT-4; Sec. 3.2 "Online VQ Module",
+ * App. E) ---------------------------------------------------------------------------
+ * Each Gaussian carries logits z_i [L] over a shared codebook E [L][D]; the renderer
+ * splats the mixture weights w_i = softmax(z_i) through the feature path (n_feat = L,
+ * feats = the weights), and a pixel's semantic feature is F(x) = E^T w(x). */
+
+/* w = softmax(z) per Gaussian: logits [n][L] float32 (device) -> w_out [n][L] of
+ * out_dtype (GS_BF16 to render them as bf16 features, or GS_F32).  1 <= L <= 64.
+ * Errors: GS_ERR_ARG. */
+gs_status gs_vq_weights(const float* logits, int64_t n, int32_t L, int32_t out_dtype, void* w_out,
+                        void* stream);
+
+/* Backward of gs_vq_weights: g_logits = w * (g_w - sum_l g_w,l w_l), w recomputed from the
+ * logits.  All [n][L] float32 device arrays. */
+gs_status gs_vq_weights_bwd(const float* logits, const float* g_w, int64_t n, int32_t L,
+                            float* g_logits, void* stream);
+
+/* Decode of a rendered weight map on the tensor cores (tcgen05, TF32 inputs, FP32
+ * accumulation): wmap [L][P] float32 (the channel-major feature output of a render with
+ * the weights as features, P pixels), codebook [L][D] float32.  Writes, when non-NULL:
+ *   F_out [D][P] = E^T w(x) per pixel;
+ *   relevance [P] = max_{n >= 1} 1 / (1 + exp(tau (F~.t_n - F~.t_0))), F~ = F / (|F| + 1e-8),
+ *     the prompt relevance of App. E with text [n_text][D] (row 0 the prompt, rows 1.. the
+ *     negatives, unit vectors; 2 <= n_text <= 8) and tau = 10 in the paper.
+ * L a multiple of 8 in [8, 64]; D a multiple of 16 in [16, 512].  err (device int32, may be
+ * NULL) is set to 1 if a tensor-core completion wait timed out (outputs then invalid).
+ * Errors: GS_ERR_ARG for unsupported sizes or missing pointers. */
+gs_status gs_vq_decode(const float* wmap, int64_t P, int32_t L, const float* codebook, int32_t D,
+                       float* F_out, const float* text, int32_t n_text, float tau,
+                       float* relevance, int32_t* err, void* stream);
+
 /* ---- introspection (synchronous; host pointers) ---------------------------------- */
 
 /* Counts of the last gs_project/gs_bin_tiles/gs_render_fwd.  inst_eff is computed by a

@@ -102,6 +102,9 @@ def _load():
         "gs_serve_cancel": ([P, C.c_uint64], st),
         "gs_serve_info": ([P, P, P, P, P], st),
         "gs_grid_target_region": ([P, i32, i32, P, i32, i32, i32, i32, i32, P, P, P], st),
+        "gs_vq_weights": ([P, i64, i32, i32, P, P], st),
+        "gs_vq_weights_bwd": ([P, P, i64, i32, P, P], st),
+        "gs_vq_decode": ([P, i64, i32, P, i32, P, P, i32, C.c_float, P, P, P], st),
         "gs_grid_target_resample": ([P, i32, i32, i32, i32, i32, i32, i32, i32, P, P, P], st),
     }
     for name, (args, res) in sig.items():
@@ -413,6 +416,32 @@ def gs_grid_target_resample(fmap, H, W, stride, off_x, off_y, target, mask=None,
     _check(lib.gs_grid_target_resample(_ptr(fmap), D, Hf, Wf, int(H), int(W), int(stride),
                                        int(off_x), int(off_y), _ptr(target), _ptr(mask),
                                        _stream(stream)), "gs_grid_target_resample")
+
+
+def gs_vq_weights(logits, out, stream=None):
+    """Softmax mixture weights: logits [n, L] float32 -> out [n, L] (float32 or bfloat16)."""
+    n, L = logits.shape
+    dt = GS_BF16 if out.dtype == torch.bfloat16 else GS_F32
+    _check(lib.gs_vq_weights(_ptr(logits), n, L, dt, _ptr(out), _stream(stream)), "gs_vq_weights")
+
+
+def gs_vq_weights_bwd(logits, g_w, g_logits, stream=None):
+    n, L = logits.shape
+    _check(lib.gs_vq_weights_bwd(_ptr(logits), _ptr(g_w), n, L, _ptr(g_logits), _stream(stream)),
+           "gs_vq_weights_bwd")
+
+
+def gs_vq_decode(wmap, codebook, F_out=None, text=None, tau=10.0, relevance=None, err=None,
+                 stream=None):
+    """F = E^T w(x) and/or prompt relevance from a weight map [L, ...] (channel-major)."""
+    L = wmap.shape[0]
+    P = wmap.numel() // L
+    Lc, D = codebook.shape
+    if Lc != L:
+        raise ValueError("codebook rows must equal the weight channels")
+    n_text = 0 if text is None else text.shape[0]
+    _check(lib.gs_vq_decode(_ptr(wmap), P, L, _ptr(codebook), D, _ptr(F_out), _ptr(text), n_text,
+                            float(tau), _ptr(relevance), _ptr(err), _stream(stream)), "gs_vq_decode")
 
 
 def gs_launch_count() -> int:

@@ -1,0 +1,125 @@
+"""NEXT-4 on the GPU against the VQ oracle (``oracle/vq.py``; Sec. 3.2, App. E): softmax
+weights and their backward, the tensor-core decode F = E^T w(x) of a rendered weight map
+(TF32 inputs, FP32 accumulation: relative 2e-3), structured one-hot maps that expose any
+operand-layout error, and the prompt relevance map."""
+import numpy as np
+import pytest
+
+from synth import scenes as S
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+TOL_TF32 = 2e-3
+
+
+@pytest.fixture(scope="module")
+def VQ(oracle):
+    from oracle import vq
+    return vq
+
+
+def _t(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(U.device())
+    return t if dtype is None else t.to(dtype)
+
+
+def test_weights_and_backward(VQ):
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    rng = np.random.default_rng(1)
+    for n, Lw in [(1000, 64), (333, 16), (17, 40), (5, 1)]:
+        z = rng.normal(scale=2.0, size=(n, Lw)).astype(np.float32)
+        w32 = torch.empty((n, Lw), device=U.device())
+        wbf = torch.empty((n, Lw), device=U.device(), dtype=torch.bfloat16)
+        L.gs_vq_weights(_t(z), w32)
+        L.gs_vq_weights(_t(z), wbf)
+        ref = VQ.weights(z)
+        np.testing.assert_allclose(w32.cpu().numpy(), ref, rtol=2e-5, atol=1e-7)
+        np.testing.assert_allclose(wbf.float().cpu().numpy(), ref, rtol=8e-3, atol=1e-6)
+        g = rng.normal(size=(n, Lw)).astype(np.float32)
+        gz = torch.empty((n, Lw), device=U.device())
+        L.gs_vq_weights_bwd(_t(z), _t(g), gz)
+        assert U.rel_err(gz.cpu().numpy(), VQ.weights_bwd(z, g)) <= 1e-5
+
+
+@pytest.mark.parametrize("Lw,D,P", [(64, 512, 27_200), (16, 48, 1000), (8, 16, 129), (32, 272, 128)])
+def test_decode_one_hot_maps(VQ, Lw, D, P):
+    """Pixel p carries weight 1 on codeword p mod L (and 0.5 on codeword (p // L) mod L):
+    every pixel must reproduce its codewords, so a transposed or shifted operand shows."""
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    rng = np.random.default_rng(2)
+    E = rng.normal(size=(Lw, D)).astype(np.float32)
+    w = np.zeros((Lw, P), np.float32)
+    p = np.arange(P)
+    w[p % Lw, p] = 1.0
+    w[(p // Lw) % Lw, p] += 0.5
+    F = torch.empty((D, P), device=U.device())
+    err = torch.zeros(1, dtype=torch.int32, device=U.device())
+    L.gs_vq_decode(_t(w), _t(E), F_out=F, err=err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ref = VQ.decode(w, E)
+    got = F.cpu().numpy()
+    assert U.rel_err(got, ref) <= TOL_TF32
+    assert np.abs(got - ref).max() <= 5e-3 * np.abs(ref).max()
+
+
+def test_decode_of_rendered_weights_and_relevance(oracle, VQ):
+    """Render the softmax weights of a room scene as 64 bf16 channels, decode on the tensor
+    cores with the relevance epilogue, and compare with the oracle's decode and relevance of
+    the same weight map."""
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    from paper_2603_09632_gb300.render import Rasterizer
+    rng = np.random.default_rng(3)
+    Lw, D = 64, 512
+    sc = S.room_scene(30_000, n_feat=Lw, sh_degree=0, seed=9)
+    cam = S.room_trajectory(8, 203, 139, 180.0)[2]
+    z = rng.normal(scale=2.0, size=(sc.n, Lw)).astype(np.float32)
+    wbf = torch.empty((sc.n, Lw), device=U.device(), dtype=torch.bfloat16)
+    L.gs_vq_weights(_t(z), wbf)
+    scene = U.upload(sc, bf16=True)
+    scene = L.Scene(scene.means, scene.scales, scene.quats, scene.opacities, scene.sh, wbf)
+    out = Rasterizer(U.device()).forward(scene, cam)
+    wmap = out["feat"]                                   # [64, H, W]
+    # the weight map sums to alpha (softmax weights sum to 1 per Gaussian, up to bf16)
+    assert torch.allclose(wmap.sum(0), out["alpha"], atol=2e-2)
+    E = rng.normal(size=(Lw, D)).astype(np.float32) / 8.0
+    text = rng.normal(size=(5, D))
+    text = (text / np.linalg.norm(text, axis=1, keepdims=True)).astype(np.float32)
+    F = torch.empty((D, cam.H, cam.W), device=U.device())
+    R = torch.empty((cam.H, cam.W), device=U.device())
+    err = torch.zeros(1, dtype=torch.int32, device=U.device())
+    L.gs_vq_decode(wmap, _t(E), F_out=F, text=_t(text), tau=10.0, relevance=R, err=err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    wm = wmap.double().cpu().numpy()
+    Fr = VQ.decode(wm, E)
+    assert U.rel_err(F.cpu().numpy(), Fr) <= TOL_TF32
+    Rr = VQ.relevance(Fr, text[0], text[1:])
+    got = R.cpu().numpy()
+    assert np.abs(got - Rr).max() <= 5e-3
+    assert 0.0 <= got.min() and got.max() <= 1.0 and got.std() > 1e-3
+    # relevance alone (no F written) is the same map
+    R2 = torch.empty_like(R)
+    L.gs_vq_decode(wmap, _t(E), text=_t(text), tau=10.0, relevance=R2)
+    torch.cuda.synchronize()
+    assert torch.equal(R, R2)
+
+
+def test_decode_argument_errors():
+    import torch
+    from paper_2603_09632_gb300 import _lib as L
+    dev = U.device()
+    w = torch.zeros((12, 10), device=dev)
+    with pytest.raises(L.GSError):
+        L.gs_vq_decode(w, torch.zeros((12, 16), device=dev), F_out=torch.empty((16, 10), device=dev))
+    w = torch.zeros((16, 10), device=dev)
+    with pytest.raises(L.GSError):
+        L.gs_vq_decode(w, torch.zeros((16, 520), device=dev), F_out=torch.empty((520, 10), device=dev))
+    with pytest.raises(L.GSError):   # relevance needs a prompt and at least one negative
+        L.gs_vq_decode(w, torch.zeros((16, 16), device=dev), text=torch.zeros((1, 16), device=dev),
+                       relevance=torch.empty(10, device=dev))
