@@ -54,9 +54,10 @@ __device__ __forceinline__ bool tile_culled(float x0, float y0, float u, float v
   return box_min_sigma(x0 + 0.5f, y0 + 0.5f, x0 + 15.5f, y0 + 15.5f, u, v, A, B, C) > sigma_cut(o);
 }
 
-// Ordered compaction of one flag per thread over a 256-thread block.  Returns the
+// Ordered compaction of one flag per thread over a block of NW warps.  Returns the
 // position of a kept item (-1 otherwise) and the number kept.  Contains one barrier;
-// s_wc (8 ints) must not be reused before the next barrier.
+// s_wc (NW ints) must not be reused before the next barrier.
+template <int NW = 8>
 __device__ __forceinline__ int block_compact_index(bool keep, int* s_wc, int* total) {
   const unsigned b = __ballot_sync(0xffffffffu, keep);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -64,7 +65,7 @@ __device__ __forceinline__ int block_compact_index(bool keep, int* s_wc, int* to
   __syncthreads();
   int off = 0, tot = 0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < NW; ++k) {
     const int c = s_wc[k];
     off += k < w ? c : 0;
     tot += c;

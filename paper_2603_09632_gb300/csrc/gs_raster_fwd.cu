@@ -1,6 +1,8 @@
 // a3: forward rendering, X-GS Eq. 1 (front-to-back alpha blending over depth-sorted
 // Gaussians), depth by substituting c_i -> d_i (App. B) and features by c_i -> f_i
-// (Sec. 3.1).  One 256-thread CTA per 16x16 tile, one thread per pixel.
+// (Sec. 3.1).  One 128-thread CTA per half tile (16 x 8 pixels), one thread per pixel:
+// both halves walk the tile's list, each culling it against its own pixel box, which
+// halves the longest work item (the tail of the persistent schedule).
 //
 // The tile's sorted list is consumed in batches of 256 Gaussians staged in shared
 // memory (records gathered by id; features converted to fp32 once per batch, so bf16
@@ -13,7 +15,8 @@
 namespace gs {
 namespace {
 
-constexpr int kB = 256;   // batch = threads = pixels per tile
+constexpr int kB = 128;    // batch = threads = pixels per work item (half a tile)
+constexpr int kRowsB = kB / 16;
 
 template <int DP, bool BF16>
 __device__ __forceinline__ void stage_features(const void* __restrict__ feats, int D,
@@ -70,7 +73,7 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   __shared__ float4 s_r0[kB], s_r1[kB], s_r2[kB];
   __shared__ uint32_t s_id[kB];
   __shared__ int s_orig[kB];
-  __shared__ int s_wc[8];
+  __shared__ int s_wc[kB / 32];
   __shared__ int s_tile;
   extern __shared__ __align__(16) float s_feat[];   // [kB][DP]
   double l1_sum = 0.0, cos_sum = 0.0;   // fused loss (LOSS): this thread's samples, all tiles
@@ -78,14 +81,18 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   // persistent CTA: tiles from the queue, heaviest first
   for (;;) {
     if (threadIdx.x == 0) {
+      // work item q: half (q & 1) of the (q >> 1)-th tile in heavy-first order
       const uint32_t q = atomicAdd(tq.head, 1u);
-      s_tile = q < (uint32_t)tq.n_tiles ? (int)(tq.order ? tq.order[q] : q) : -1;
+      s_tile = q < 2u * (uint32_t)tq.n_tiles
+                   ? 2 * (int)(tq.order ? tq.order[q >> 1] : (q >> 1)) + (int)(q & 1u)
+                   : -1;
     }
     __syncthreads();
-    const int tile = s_tile;
-    if (tile < 0) break;
+    const int item = s_tile;
+    if (item < 0) break;
+    const int tile = item >> 1;
 
-    const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
+    const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile + kRowsB * (item & 1);
     const int px = tx0 + (threadIdx.x & 15);
     const int py = ty0 + (threadIdx.x >> 4);
     const bool inside = px < cam.W && py < cam.H;
@@ -115,11 +122,11 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       if ((int)threadIdx.x < cnt && id < (uint32_t)cam.n_gauss) {
         g = rec[id];
         g.r1.w = sigma_cut(g.r1.y);
-        keep = box_min_sigma(bx0, by0, bx0 + 15.f, by0 + 15.f, g.r0.x, g.r0.y, g.r0.z, g.r0.w,
-                             g.r1.x) <= g.r1.w;
+        keep = box_min_sigma(bx0, by0, bx0 + 15.f, by0 + (float)(kRowsB - 1), g.r0.x, g.r0.y,
+                             g.r0.z, g.r0.w, g.r1.x) <= g.r1.w;
       }
       int nk;
-      const int pos = block_compact_index(keep, s_wc, &nk);
+      const int pos = block_compact_index<kB / 32>(keep, s_wc, &nk);
       if (keep) {
         s_r0[pos] = g.r0;
         s_r1[pos] = g.r1;      // r1.w = sigma cut
@@ -280,7 +287,7 @@ void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const
               cudaStream_t st) {
   const size_t smem = sizeof(float) * kB * DP;
   auto kern = k_raster_fwd<DP, BF16, LOSS>;
-  const int grid = persistent_grid(kern, kB, smem, tq.n_tiles);
+  const int grid = persistent_grid(kern, kB, smem, 2 * tq.n_tiles);
   kern<<<grid, kB, smem, st>>>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
                                T_final, n_contrib, fl);
   note_launch();
