@@ -25,7 +25,14 @@ namespace {
 constexpr int kGT = 256;           // threads per CTA: 8 independent warps
 constexpr int kWarps = kGT / 32;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWP = 33;            // row stride of the per-warp weight matrix (floats)
+constexpr int kWT = 32;            // row stride of the per-warp weight matrix [lane][entry]
+
+// Position of entry k in lane l's row of the weight matrix: 16-byte chunks XOR-swizzled by
+// the lane, so that the 32 lanes' stores of one entry spread over 8 banks and a 16-byte
+// read of four consecutive entries stays contiguous.
+__device__ __forceinline__ int w_slot(int l, int k) {
+  return l * kWT + ((((k >> 2) ^ (l & 7)) << 2) | (k & 3));
+}
 
 __device__ __forceinline__ int ceil_div_signed(int a, int b) {   // b > 0
   return a >= 0 ? (a + b - 1) / b : -((-a) / b);
@@ -172,7 +179,7 @@ constexpr int fwd_warp_floats() {
 }
 
 template <int DP, bool BF16, bool LOSS>
-__global__ void __launch_bounds__(kGT)
+__global__ void __launch_bounds__(kGT, 2)
 k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
            const void* __restrict__ feats, int D, const uint2* __restrict__ ranges,
            const uint32_t* __restrict__ inst_id, float* __restrict__ rgb, float* __restrict__ depth,
@@ -409,11 +416,11 @@ __device__ __forceinline__ void red_add4(float* dst, float a, float b, float c, 
 template <int DP, bool FO>
 constexpr int bwd_warp_floats() {
   // records, ids, list positions, features (not when FO), g_F rows, weights
-  return 32 * 12 + 32 + 32 + (FO ? 0 : 32 * DP) + 32 * DP + 32 * kWP;
+  return 32 * 12 + 32 + 32 + (FO ? 0 : 32 * DP) + 32 * DP + 32 * kWT;
 }
 
 template <int DP, bool BF16, bool FO>
-__global__ void __launch_bounds__(kGT)
+__global__ void __launch_bounds__(kGT, 2)
 k_grid_bwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
            const void* __restrict__ feats, int D, const uint2* __restrict__ ranges,
            const uint32_t* __restrict__ inst_id, const float* __restrict__ T_final,
@@ -428,7 +435,7 @@ k_grid_bwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
   int* s_orig = reinterpret_cast<int*>(base + 32 * 12 + 32);
   float* s_f = base + 32 * 12 + 64;                    // [32][DP] (not when FO)
   float* s_E = s_f + (FO ? 0 : 32 * DP);               // [32][DP]: g_F of each lane's sample
-  float* s_W = s_E + 32 * DP;                          // [32 entries][kWP]: w per lane
+  float* s_W = s_E + 32 * DP;                          // [32 lanes][kWT]: w per entry
   const int64_t HW = (int64_t)cam.GW * cam.GH;
   constexpr int CB = DP / 4;
 
@@ -519,7 +526,7 @@ k_grid_bwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
             }
           }
         }
-        s_W[k * kWP + lane] = w;
+        s_W[w_slot(lane, k)] = w;
         const bool any = __any_sync(kFull, w != 0.f);
         if (any) wlive |= 1u << k;
         if constexpr (!FO) {
@@ -548,27 +555,43 @@ k_grid_bwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
       // feature gradients of the batch: out[k][c] = sum over the samples of w g_F
       if constexpr (DP > 0) {
         if (g_feats) {
-          for (int task = lane; task < nk * CB; task += 32) {
-            const int k = task / CB, cb = task - k * CB;
-            if (!(wlive >> k & 1u)) continue;
-            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+          // 4 entries x 4 channels per task: one 16-byte weight load and one 16-byte g_F
+          // load per sample feed 16 FMAs.  Weights of entries >= nk are stale, but only
+          // entries with a wlive bit (all < nk) are written out.
+          const int nkb = (nk + 3) >> 2;
+          for (int task = lane; task < nkb * CB; task += 32) {
+            const int kb = task / CB, cb = task - kb * CB, k0 = 4 * kb;
+            const unsigned live4 = (wlive >> k0) & 15u;
+            if (!live4) continue;
+            float o[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+              for (int y = 0; y < 4; ++y) o[x][y] = 0.f;
 #pragma unroll 8
             for (int l = 0; l < 32; ++l) {
-              const float wl = s_W[k * kWP + l];
+              const float4 w4 = *reinterpret_cast<const float4*>(s_W + w_slot(l, k0));
               const float4 e = *reinterpret_cast<const float4*>(s_E + l * DP + 4 * cb);
-              o.x = fmaf(wl, e.x, o.x);
-              o.y = fmaf(wl, e.y, o.y);
-              o.z = fmaf(wl, e.z, o.z);
-              o.w = fmaf(wl, e.w, o.w);
-            }
-            float* dst = g_feats + (int64_t)s_id[k] * D + 4 * cb;
-            if (D == DP) {
-              atomicAdd(reinterpret_cast<float4*>(dst), o);
-            } else {
-              const float ov[4] = {o.x, o.y, o.z, o.w};
+              const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-              for (int e = 0; e < 4; ++e)
-                if (4 * cb + e < D) atomicAdd(dst + e, ov[e]);
+              for (int x = 0; x < 4; ++x) {
+                o[x][0] = fmaf(wv[x], e.x, o[x][0]);
+                o[x][1] = fmaf(wv[x], e.y, o[x][1]);
+                o[x][2] = fmaf(wv[x], e.z, o[x][2]);
+                o[x][3] = fmaf(wv[x], e.w, o[x][3]);
+              }
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              if (!(live4 >> x & 1u)) continue;
+              float* dst = g_feats + (int64_t)s_id[k0 + x] * D + 4 * cb;
+              if (D == DP) {
+                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(o[x][0], o[x][1], o[x][2], o[x][3]));
+              } else {
+#pragma unroll
+                for (int y = 0; y < 4; ++y)
+                  if (4 * cb + y < D) atomicAdd(dst + y, o[x][y]);
+              }
             }
           }
         }
