@@ -44,6 +44,10 @@ WORKLOADS = {
 # features-only backward (geometry frozen).  Stride 1 is the same phase at full resolution.
 # VQ pixel decode (Sec. 3.2, App. E): softmax weights of 64 logits per Gaussian rendered as
 # 64 bf16 channels, then F = E^T w(x) (512-d) and the prompt relevance on the tensor cores.
+WORKLOADS["vq_decode_640x480_200k"] = dict(
+    make=lambda: S.config_slam(n_poses=100), bf16=True, l1=False, vq=(64, 512),
+    desc="room 200k Gaussians, 64 VQ logits -> bf16 weights rendered at 640x480, "
+         "decode F = E^T w(x) to 512-d fp32 + prompt relevance (tcgen05 tf32); profiling size")
 WORKLOADS["vq_decode_1200x680_1m"] = dict(
     make=lambda: S.config_semantic(n_poses=100), bf16=True, l1=False, vq=(64, 512),
     desc="room 1M Gaussians, 64 VQ logits -> bf16 weights rendered at 1200x680, "
