@@ -48,34 +48,32 @@ struct gs_workspace {
   int device = 0;
   // per Gaussian
   DevBuf<GaussRec> rec;
-  DevBuf<uint32_t> depth_key, ntiles, sort_k0, sort_v0, sort_k1, sort_v1;
+  DevBuf<uint32_t> depth_key, ntiles;
   DevBuf<uint2> rect;
   DevBuf<uint32_t> item_max;   // per grid work item, statistics only
   DevBuf<float> g2d;
   DevBuf<float> pose_partials;
-  // per instance
-  DevBuf<uint32_t> inst_tile, inst_id, inst_tile2, inst_id2;
+  // per instance: sorted depth keys and ids, their ping-pong space, the slot's tile
+  DevBuf<uint32_t> inst_key, inst_id, inst_key2, inst_id2, inst_tile;
   // per tile / pixel
   DevBuf<uint2> ranges;
   DevBuf<uint32_t> tile_order, queue;   // heavy-first tile order; persistent-kernel queue heads
+  DevBuf<uint32_t> tile_count, tile_cursor;   // binning scratch
   bool ordered = false;
   DevBuf<float> T_final;
   DevBuf<uint32_t> n_contrib;
   // scratch
-  DevBuf<uint32_t> bin_zero, counters;   // bin_zero: digit histograms + chunk tickets
-  DevBuf<unsigned long long> bin_status;  // look-back status words
+  DevBuf<uint32_t> counters;
   DevBuf<unsigned long long> stats64;     // pair counts (statistics only)
   CamDev cam{};                           // camera of the last gs_project
-  uint32_t epoch = 0;
   uint32_t* h_counters = nullptr;   // pinned mirror
   // state
   int64_t n = 0;
   int W = 0, H = 0, TX = 0, TY = 0;
   int stage = 0;             // 1 projected, 2 binned, 3 rendered
   int64_t inst_bound = 0;    // host bound on I used for grids
-  const uint32_t* sorted_ids = nullptr;   // depth-sorted visible ids
-  const uint32_t* tile_sorted = nullptr;  // instance tiles after the tile sort
-  const uint32_t* id_sorted = nullptr;    // instance ids after the tile sort
+  const uint32_t* tile_sorted = nullptr;  // tile of every instance slot
+  const uint32_t* id_sorted = nullptr;    // Gaussian id of every instance slot
   // timing
   bool timing = false;
   cudaEvent_t ev[GS_NUM_TIMERS][kTimerRing][2];
@@ -164,12 +162,6 @@ bool same_grid(const CamDev& a, const CamDev& b) {
   return a.W == b.W && a.H == b.H && a.stride == b.stride && a.ox == b.ox && a.oy == b.oy;
 }
 
-int bits_for(int64_t n_values) {
-  int b = 0;
-  while ((int64_t(1) << b) < n_values) ++b;
-  return b;
-}
-
 struct StageTimer {
   gs_workspace* ws;
   int which;
@@ -186,35 +178,23 @@ struct StageTimer {
   }
 };
 
-// Look-back status words: zeroed once when (re)allocated, epoch-tagged afterwards.
-cudaError_t ensure_status(gs_workspace* ws, int64_t elems) {
-  const size_t need = bin_status_words(elems);
-  if (need <= ws->bin_status.cap) return cudaSuccess;
-  cudaError_t e = ws->bin_status.ensure(need);
-  if (e != cudaSuccess) return e;
-  return cudaMemset(ws->bin_status.p, 0, ws->bin_status.cap * sizeof(unsigned long long));
-}
-
 cudaError_t ensure_gauss(gs_workspace* ws, int64_t n) {
   const size_t m = (size_t)std::max<int64_t>(n, 1);
   cudaError_t e;
   if ((e = ws->rec.ensure(m)) || (e = ws->depth_key.ensure(m)) || (e = ws->ntiles.ensure(m)) ||
-      (e = ws->sort_k0.ensure(m)) || (e = ws->sort_v0.ensure(m)) ||
-      (e = ws->sort_k1.ensure(m)) || (e = ws->sort_v1.ensure(m)) || (e = ws->rect.ensure(m)) ||
-      (e = ws->g2d.ensure(m * kG2D)) ||
+      (e = ws->rect.ensure(m)) || (e = ws->g2d.ensure(m * kG2D)) ||
       (e = ws->pose_partials.ensure((size_t)project_bwd_blocks(n) * 8)))
     return e;
-  return ensure_status(ws, (int64_t)ws->rec.cap);
+  return cudaSuccess;
 }
 
 cudaError_t ensure_inst(gs_workspace* ws, int64_t cap) {
   const size_t m = (size_t)std::max<int64_t>(cap, 1);
   cudaError_t e;
-  if ((e = ws->inst_tile.ensure(m)) || (e = ws->inst_id.ensure(m)) ||
-      (e = ws->inst_tile2.ensure(m)) || (e = ws->inst_id2.ensure(m)))
+  if ((e = ws->inst_key.ensure(m)) || (e = ws->inst_id.ensure(m)) ||
+      (e = ws->inst_key2.ensure(m)) || (e = ws->inst_id2.ensure(m)) || (e = ws->inst_tile.ensure(m)))
     return e;
-  // the tile sort may run over every allocated instance slot (no-sync binning)
-  return ensure_status(ws, (int64_t)ws->inst_tile.cap);
+  return cudaSuccess;
 }
 
 cudaError_t ensure_pix(gs_workspace* ws, int64_t npix, int64_t ntiles) {
@@ -222,8 +202,11 @@ cudaError_t ensure_pix(gs_workspace* ws, int64_t npix, int64_t ntiles) {
   if ((e = ws->T_final.ensure((size_t)std::max<int64_t>(npix, 1))) ||
       (e = ws->n_contrib.ensure((size_t)std::max<int64_t>(npix, 1))))
     return e;
-  if ((e = ws->tile_order.ensure((size_t)std::max<int64_t>(ntiles, 1)))) return e;
-  return ws->ranges.ensure((size_t)std::max<int64_t>(ntiles, 1));
+  const size_t t = (size_t)std::max<int64_t>(ntiles, 1);
+  if ((e = ws->tile_order.ensure(t)) || (e = ws->tile_count.ensure(t)) ||
+      (e = ws->tile_cursor.ensure(t)))
+    return e;
+  return ws->ranges.ensure(t);
 }
 
 }  // namespace
@@ -255,9 +238,7 @@ gs_status gs_workspace_create(gs_workspace** out, int device) {
   if (!ws) return GS_ERR_OOM;
   ws->device = device;
   DeviceGuard g(device);
-  if (ws->counters.ensure(kCntNum) != cudaSuccess || ws->bin_zero.ensure(kBinZeroWords) != cudaSuccess ||
-      ws->queue.ensure(4) != cudaSuccess ||
-      cudaMemset(ws->bin_zero.p, 0, kBinZeroWords * sizeof(uint32_t)) != cudaSuccess ||
+  if (ws->counters.ensure(kCntNum) != cudaSuccess || ws->queue.ensure(4) != cudaSuccess ||
       cudaMemset(ws->counters.p, 0, kCntNum * sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ws->h_counters, kCntNum * sizeof(uint32_t)) != cudaSuccess) {
     gs_workspace_destroy(ws);
@@ -273,12 +254,12 @@ void gs_workspace_destroy(gs_workspace* ws) {
     DeviceGuard g(ws->device);
     cudaDeviceSynchronize();
     ws->rec.release(); ws->depth_key.release(); ws->ntiles.release();
-    ws->sort_k0.release(); ws->sort_v0.release(); ws->sort_k1.release(); ws->sort_v1.release();
     ws->rect.release(); ws->item_max.release(); ws->g2d.release(); ws->pose_partials.release();
-    ws->inst_tile.release(); ws->inst_id.release(); ws->inst_tile2.release(); ws->inst_id2.release();
+    ws->inst_key.release(); ws->inst_id.release(); ws->inst_key2.release(); ws->inst_id2.release();
+    ws->inst_tile.release();
     ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
-    ws->tile_order.release(); ws->queue.release();
-    ws->bin_zero.release(); ws->bin_status.release(); ws->counters.release(); ws->stats64.release();
+    ws->tile_order.release(); ws->queue.release(); ws->tile_count.release(); ws->tile_cursor.release();
+    ws->counters.release(); ws->stats64.release();
     if (ws->h_counters) cudaFreeHost(ws->h_counters);
     if (ws->ev_created)
       for (int k = 0; k < GS_NUM_TIMERS; ++k)
@@ -354,13 +335,6 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   const int ntl = ws->TX * ws->TY;
   StageTimer tm(ws, GS_TIMER_BIN, st);
   uint32_t* cnt = ws->counters.p;
-  BinScratch bs;
-  bs.ghist = ws->bin_zero.p;
-  bs.tickets = ws->bin_zero.p + 7 * 256;
-  bs.status = ws->bin_status.p;
-  bs.counters = cnt;
-  bs.epoch = &ws->epoch;
-  GS_TRY(cudaMemsetAsync(ws->bin_zero.p, 0, kBinZeroWords * sizeof(uint32_t), st));
   int64_t bound;
   if (n_instances_out) {
     // I was counted by the projection: one synchronisation, then size the instance buffers
@@ -368,27 +342,34 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
     GS_TRY(cudaStreamSynchronize(st));
     bound = (int64_t)ws->h_counters[kCntInst];
     GS_TRY(ensure_inst(ws, bound));
-    bs.status = ws->bin_status.p;
     *n_instances_out = bound;
   } else {
-    bound = (int64_t)ws->inst_tile.cap;
+    bound = (int64_t)ws->inst_id.cap;
   }
-  const int64_t cap = (int64_t)ws->inst_tile.cap;
-  // 1. depth sort of all Gaussians (culled ones last), 2. emit instances in depth order,
-  // 3. stable sort of the instances by tile, 4. tile ranges
-  launch_depth_sort(ws->depth_key.p, n, ws->sort_k1.p, ws->sort_v1.p, ws->sort_k0.p, ws->sort_v0.p,
-                    bs, st);
-  const uint32_t* sorted_ids = ws->sort_v0.p;
-  // the depth sort's ping-pong key buffer is free now: it holds the tile-count offsets
-  launch_emit_instances(sorted_ids, ws->ntiles.p, ws->rect.p, n, ws->TX, cap, ws->sort_k1.p,
-                        ws->inst_tile.p, ws->inst_id.p, bs, st);
-  const int w2 = launch_tile_sort(min64(bound, cap), bits_for(ntl), ws->inst_tile.p, ws->inst_id.p,
-                                  ws->inst_tile2.p, ws->inst_id2.p, bs, st);
-  ws->tile_sorted = w2 ? ws->inst_tile2.p : ws->inst_tile.p;
-  ws->id_sorted = w2 ? ws->inst_id2.p : ws->inst_id.p;
-  ws->sorted_ids = sorted_ids;
-  launch_tile_ranges(ws->tile_sorted, cnt, min64(bound, cap), cap, ntl, ws->ranges.p, st);
-  ws->ordered = launch_tile_order(ws->ranges.p, ntl, ws->tile_order.p, st);
+  const int64_t cap = (int64_t)ws->inst_id.cap;
+  // count -> scan (ranges, heavy-first order) -> scatter -> per-tile radix sort
+  BinArgs b;
+  b.n = n;
+  b.ntiles = ws->ntiles.p;
+  b.rect = ws->rect.p;
+  b.depth_key = ws->depth_key.p;
+  b.TX = ws->TX;
+  b.n_tiles = ntl;
+  b.cap = cap;
+  b.tile_count = ws->tile_count.p;
+  b.cursor = ws->tile_cursor.p;
+  b.ranges = ws->ranges.p;
+  b.order = ws->tile_order.p;
+  b.queue = ws->queue.p + 2;
+  b.key0 = ws->inst_key.p;
+  b.id0 = ws->inst_id.p;
+  b.key1 = ws->inst_key2.p;
+  b.id1 = ws->inst_id2.p;
+  b.tile_out = ws->inst_tile.p;
+  b.counters = cnt;
+  ws->ordered = launch_bin(b, st);
+  ws->tile_sorted = ws->inst_tile.p;
+  ws->id_sorted = ws->inst_id.p;
   GS_TRY(cudaGetLastError());
   ws->inst_bound = std::min(bound, cap);
   ws->stage = 2;

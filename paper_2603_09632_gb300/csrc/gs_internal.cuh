@@ -43,7 +43,6 @@ __host__ __device__ inline int grid_coord(int o, int stride, int k) { return o +
 enum : uint32_t {
   kErrInstOverflow = 1u,   // instance count above reserved capacity (no-sync binning)
   kErrBadRange = 2u,       // a tile range outside the instance array (guard)
-  kErrLookback = 4u,       // a sort/scan look-back wait ran out (bounded spin)
 };
 
 // Device counters (one small array in the workspace).
@@ -62,48 +61,33 @@ enum : int {
 void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32_t* depth_key,
                     uint32_t* ntiles, uint2* rect, uint32_t* counters, cudaStream_t st);
 
-// gs_sort.cu
-// Scratch of the binning kernels.  ghist (7 x 256 words) and tickets (4 words) are one
-// contiguous block zeroed at the start of every binning; status holds the look-back words
-// (tagged with a launch epoch, so it never needs clearing after allocation).
-constexpr int kBinZeroWords = 7 * 256 + 4;
-struct BinScratch {
-  uint32_t* ghist;              // [7][256]: 4 depth-key digits, 3 tile-key digits
-  uint32_t* tickets;            // [4] chunk tickets (right after ghist)
-  unsigned long long* status;   // look-back status words
-  uint32_t* counters;           // workspace counters (status word for errors)
-  uint32_t* epoch;              // host-side launch epoch, 1 .. 2^30 - 1
-  uint32_t next_epoch() const {
-    *epoch = (*epoch % 0x3FFFFFFFu) + 1u;
-    return *epoch;
-  }
+// gs_sort.cu: binning in tile buckets (count, scan, scatter, per-tile radix sort).
+// After launch_bin, tile t's Gaussians occupy slots [ranges[t].x, ranges[t].y) of id0 in
+// (depth, id) order (key0 holds their depth keys, tile_out their tile); slots are capped
+// at `cap` (an instance count above it sets kErrInstOverflow).  `order` receives the
+// heavy-first tile order when there are at most kMaxOrderedTiles tiles (the return value
+// says whether it was written).  No host synchronisation.
+struct BinArgs {
+  int64_t n;                     // Gaussians
+  const uint32_t* ntiles;        // [n] tiles per Gaussian (0 = culled)
+  const uint2* rect;             // [n] packed tile rectangles
+  const uint32_t* depth_key;     // [n]
+  int TX, n_tiles;
+  int64_t cap;                   // instance slots available
+  uint32_t* tile_count;          // [n_tiles] scratch
+  uint32_t* cursor;              // [n_tiles] scratch
+  uint2* ranges;                 // [n_tiles] out
+  uint32_t* order;               // [n_tiles] out (heavy-first)
+  uint32_t* queue;               // one word (persistent sort queue head)
+  uint32_t *key0, *id0;          // [cap] out: sorted depth keys and Gaussian ids
+  uint32_t *key1, *id1;          // [cap] scratch (ranges longer than shared memory)
+  uint32_t* tile_out;            // [cap] out: tile of every slot
+  uint32_t* counters;            // workspace counters (status word)
 };
-// look-back status words needed for sorts of up to max_elems elements
-size_t bin_status_words(int64_t max_elems);
-// Stable sort of all n Gaussians by depth key (4 onesweep passes; values = ids).  Result
-// in (k0, v0); (k1, v1) is the ping-pong buffer.
-void launch_depth_sort(const uint32_t* depth_key, int64_t n, uint32_t* k1, uint32_t* v1,
-                       uint32_t* k0, uint32_t* v0, const BinScratch& s, cudaStream_t st);
-// Emit (tile, id) instances of the depth-sorted Gaussians: tile-count prefix sum into
-// `offsets` (n words), then emission balanced over output slots, at most cap (overflow
-// flagged), with the tile-key digit histograms.
-void launch_emit_instances(const uint32_t* sorted_ids, const uint32_t* ntiles, const uint2* rect,
-                           int64_t n, int TX, int64_t cap, uint32_t* offsets, uint32_t* inst_tile,
-                           uint32_t* inst_id, const BinScratch& s, cudaStream_t st);
-// Stable sort of min(I, bound) instances by tile id (tile_bits <= 24).  Returns 0 if the
-// result is in (k0, v0), 1 if in (k1, v1).
-int launch_tile_sort(int64_t bound, int tile_bits, uint32_t* k0, uint32_t* v0, uint32_t* k1,
-                     uint32_t* v1, const BinScratch& s, cudaStream_t st);
-// tile ranges [start, end) from tile-sorted instances
-void launch_tile_ranges(const uint32_t* inst_tile, const uint32_t* counters, int64_t bound_i,
-                        int64_t cap, int n_tiles, uint2* ranges, cudaStream_t st);
+constexpr int kMaxOrderedTiles = 1 << 18;
+bool launch_bin(const BinArgs& b, cudaStream_t st);
 void launch_inst_eff(const uint32_t* n_contrib, int TX, int TY, int W, int H, uint32_t* counters,
                      cudaStream_t st);
-// Heavy-first processing order of the tiles (longest lists first).  Returns false (and
-// launches nothing) above kMaxOrderedTiles tiles: the raster kernels then take tiles in
-// index order.
-constexpr int kMaxOrderedTiles = 1 << 18;
-bool launch_tile_order(const uint2* ranges, int n_tiles, uint32_t* order, cudaStream_t st);
 // Pair counts for the roofline model (stats only): stats64[0] = evaluated, [1] = blended.
 void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* ranges,
                        const uint32_t* inst_id, const uint32_t* n_contrib,

@@ -30,23 +30,20 @@ constexpr size_t oRec = 0;
 constexpr size_t oKey = al(oRec + kNaMaxGauss * sizeof(GaussRec));
 constexpr size_t oNt = al(oKey + kNaMaxGauss * 4);
 constexpr size_t oRect = al(oNt + kNaMaxGauss * 4);
-constexpr size_t oK0 = al(oRect + kNaMaxGauss * 8);
-constexpr size_t oV0 = al(oK0 + kNaMaxGauss * 4);
-constexpr size_t oK1 = al(oV0 + kNaMaxGauss * 4);
-constexpr size_t oV1 = al(oK1 + kNaMaxGauss * 4);
-constexpr size_t oIT0 = al(oV1 + kNaMaxGauss * 4);
-constexpr size_t oII0 = al(oIT0 + kNaMaxInst * 4);
-constexpr size_t oIT1 = al(oII0 + kNaMaxInst * 4);
-constexpr size_t oII1 = al(oIT1 + kNaMaxInst * 4);
-constexpr size_t oTf = al(oII1 + kNaMaxInst * 4);
+constexpr size_t oK0 = al(oRect + kNaMaxGauss * 8);        // instance depth keys / ids
+constexpr size_t oI0 = al(oK0 + kNaMaxInst * 4);
+constexpr size_t oK1 = al(oI0 + kNaMaxInst * 4);          // their ping-pong space
+constexpr size_t oI1 = al(oK1 + kNaMaxInst * 4);
+constexpr size_t oTile = al(oI1 + kNaMaxInst * 4);        // tile of every slot
+constexpr size_t oTf = al(oTile + kNaMaxInst * 4);
 constexpr size_t oNc = al(oTf + kNaMaxPix * 4);
 constexpr size_t oRanges = al(oNc + kNaMaxPix * 4);
 constexpr size_t oOrder = al(oRanges + kNaMaxTiles * 8);
-constexpr size_t oZero = al(oOrder + kNaMaxTiles * 4);          // digit histograms + tickets
-constexpr size_t oCnt = al(oZero + kBinZeroWords * 4);           // counters
-constexpr size_t oQueue = al(oCnt + kCntNum * 4);                // raster tile-queue head
-constexpr size_t oStatus = al(oQueue + 4 * 4);                   // look-back status words
-constexpr size_t kNaBytes = al(oStatus + (size_t)kNaMaxInst / 8 * 8 * 8 + 64 * 1024);
+constexpr size_t oTCount = al(oOrder + kNaMaxTiles * 4);    // binning scratch
+constexpr size_t oTCursor = al(oTCount + kNaMaxTiles * 4);
+constexpr size_t oCnt = al(oTCursor + kNaMaxTiles * 4);     // counters
+constexpr size_t oQueue = al(oCnt + kCntNum * 4);           // persistent-kernel queue heads
+constexpr size_t kNaBytes = al(oQueue + 4 * 4);
 
 }  // namespace
 }  // namespace gs
@@ -59,21 +56,14 @@ namespace {
 
 std::mutex g_na_mu;
 unsigned char* g_na_ptr[kNaMaxDevices] = {};
-uint32_t g_na_epoch[kNaMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once per device.
 gs_status na_scratch(int dev, unsigned char** out) {
   if (dev < 0 || dev >= kNaMaxDevices) return GS_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_na_mu);
   if (!g_na_ptr[dev]) {
-    if (bin_status_words(kNaMaxInst) * sizeof(unsigned long long) > kNaBytes - oStatus)
-      return GS_ERR_ARG;   // layout inconsistent with the sort's chunking (build error)
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GS_ERR_CUDA;
-    // the look-back status words must start at zero (they are epoch-tagged afterwards)
-    if (cudaMemset(static_cast<unsigned char*>(p) + oStatus, 0, kNaBytes - oStatus) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess)
-      return GS_ERR_CUDA;
     g_na_ptr[dev] = static_cast<unsigned char*>(p);
   }
   *out = g_na_ptr[dev];
@@ -81,12 +71,6 @@ gs_status na_scratch(int dev, unsigned char** out) {
 }
 
 bool na_aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-int na_bits_for(int64_t n_values) {
-  int b = 0;
-  while ((int64_t(1) << b) < n_values) ++b;
-  return b;
-}
 
 }  // namespace
 }  // namespace gs
@@ -140,23 +124,21 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   uint32_t* key = reinterpret_cast<uint32_t*>(base + oKey);
   uint32_t* nt = reinterpret_cast<uint32_t*>(base + oNt);
   uint2* rect = reinterpret_cast<uint2*>(base + oRect);
-  uint32_t *k0 = reinterpret_cast<uint32_t*>(base + oK0), *v0 = reinterpret_cast<uint32_t*>(base + oV0);
-  uint32_t *k1 = reinterpret_cast<uint32_t*>(base + oK1), *v1 = reinterpret_cast<uint32_t*>(base + oV1);
-  uint32_t *it0 = reinterpret_cast<uint32_t*>(base + oIT0), *ii0 = reinterpret_cast<uint32_t*>(base + oII0);
-  uint32_t *it1 = reinterpret_cast<uint32_t*>(base + oIT1), *ii1 = reinterpret_cast<uint32_t*>(base + oII1);
+  uint32_t *k0 = reinterpret_cast<uint32_t*>(base + oK0), *i0 = reinterpret_cast<uint32_t*>(base + oI0);
+  uint32_t *k1 = reinterpret_cast<uint32_t*>(base + oK1), *i1 = reinterpret_cast<uint32_t*>(base + oI1);
+  uint32_t* tile_of = reinterpret_cast<uint32_t*>(base + oTile);
   float* Tf = reinterpret_cast<float*>(base + oTf);
   uint32_t* nc = reinterpret_cast<uint32_t*>(base + oNc);
   uint2* ranges = reinterpret_cast<uint2*>(base + oRanges);
   uint32_t* order = reinterpret_cast<uint32_t*>(base + oOrder);
-  uint32_t* zero = reinterpret_cast<uint32_t*>(base + oZero);
+  uint32_t* tcount = reinterpret_cast<uint32_t*>(base + oTCount);
+  uint32_t* tcursor = reinterpret_cast<uint32_t*>(base + oTCursor);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base + oCnt);
   uint32_t* queue = reinterpret_cast<uint32_t*>(base + oQueue);
-  unsigned long long* status = reinterpret_cast<unsigned long long*>(base + oStatus);
 
-  // the array keeps the previous call's contents: clear what must start at zero
-  if (cudaMemsetAsync(cnt, 0, kCntNum * 4, st) != cudaSuccess ||
-      cudaMemsetAsync(zero, 0, kBinZeroWords * 4, st) != cudaSuccess)
-    return GS_ERR_CUDA;
+  // the array keeps the previous call's contents: clear what must start at zero (the
+  // binning clears its own tile counters and queue head)
+  if (cudaMemsetAsync(cnt, 0, kCntNum * 4, st) != cudaSuccess) return GS_ERR_CUDA;
   launch_project(*scene, cd, rec, key, nt, rect, cnt, st);
   // the instance count decides whether the request fits: one synchronisation
   uint32_t h_cnt[kCntNum];
@@ -165,23 +147,29 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
     return GS_ERR_CUDA;
   const int64_t I = h_cnt[kCntInst];
   if (I > kNaMaxInst) return GS_ERR_OVER_BUDGET;
-  BinScratch bs;
-  bs.ghist = zero;
-  bs.tickets = zero + 7 * 256;
-  bs.status = status;
-  bs.counters = cnt;
-  bs.epoch = &g_na_epoch[dev];
-  const int64_t n = scene->n;
-  launch_depth_sort(key, n, k1, v1, k0, v0, bs, st);
-  launch_emit_instances(v0, nt, rect, n, cd.TX, kNaMaxInst, k1, it0, ii0, bs, st);
-  const int w2 = launch_tile_sort(I, na_bits_for(ntl), it0, ii0, it1, ii1, bs, st);
-  const uint32_t* tiles = w2 ? it1 : it0;
-  const uint32_t* ids = w2 ? ii1 : ii0;
-  launch_tile_ranges(tiles, cnt, I, kNaMaxInst, (int)ntl, ranges, st);
-  const bool ordered = launch_tile_order(ranges, (int)ntl, order, st);
+  BinArgs b;
+  b.n = scene->n;
+  b.ntiles = nt;
+  b.rect = rect;
+  b.depth_key = key;
+  b.TX = cd.TX;
+  b.n_tiles = (int)ntl;
+  b.cap = kNaMaxInst;
+  b.tile_count = tcount;
+  b.cursor = tcursor;
+  b.ranges = ranges;
+  b.order = order;
+  b.queue = queue + 1;
+  b.key0 = k0;
+  b.id0 = i0;
+  b.key1 = k1;
+  b.id1 = i1;
+  b.tile_out = tile_of;
+  b.counters = cnt;
+  const bool ordered = launch_bin(b, st);
   if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GS_ERR_CUDA;
   const TileQueue tq{queue, ordered ? order : nullptr, (int)ntl};
-  launch_raster_fwd(cd, tq, rec, scene->feats, scene->feat_dtype, scene->n_feat, ranges, ids, rgb,
+  launch_raster_fwd(cd, tq, rec, scene->feats, scene->feat_dtype, scene->n_feat, ranges, i0, rgb,
                     depth, alpha, scene->n_feat > 0 ? feat : nullptr, Tf, nc, nullptr, st);
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
