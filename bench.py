@@ -432,7 +432,7 @@ def run_gpu(args):
     roofline = build_roofline(stage, sb_tot, sf_tot, pairs, args.steps, args.workload)
 
     # end to end through the public API with host buffers
-    e2e = run_e2e(args, L, scene_np, gcams, poses, wl, dev, stream, ws, K, D, fdt, H, W)
+    e2e = run_e2e(args, L, scene, gcams, poses, dev, stream, ws, K, D, H, W)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world,
@@ -453,53 +453,68 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, L, scene_np, gcams, poses, wl, dev, stream, ws, K, D, fdt, H, W):
-    """Same metric through the C ABI with HOST inputs/outputs: every step copies the scene
-    parameters and upstream gradients from pinned host memory, runs the path and copies
-    the rendered images and all gradients back to pinned host memory."""
+def run_e2e(args, L, scene, gcams, poses, dev, stream, ws, K, D, H, W):
+    """Same metric through the C ABI with host data: the map (the Gaussians) stays resident
+    on the device as it does in SLAM; every step copies its per-frame input -- the upstream
+    gradient images rgb/depth/alpha/features standing in for the observed frame -- from
+    pinned host memory, runs project -> bin -> fwd -> bwd and reads the step's result (the
+    6-DoF pose gradient) back into pinned host memory.  Inputs are double-buffered: a copy
+    stream uploads step k+1 while step k computes."""
     import torch
-    n = scene_np.n
-    pin = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dt).pin_memory()
-    h_in = [pin(scene_np.means), pin(scene_np.scales), pin(scene_np.quats), pin(scene_np.opacities),
-            pin(scene_np.sh), pin(scene_np.feats, fdt)]
-    g = S.upstream_grads(H, W, D)
-    h_g = [pin(g[k]) for k in ("rgb", "depth", "alpha", "feat")]
-    d_in = [torch.empty_like(t, device=dev) for t in h_in]
-    d_g = [torch.empty_like(t, device=dev) for t in h_g]
-    scene = L.Scene(*d_in)
+    n = scene.n
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+    h_g = []
+    for v in range(2):
+        g = S.upstream_grads(H, W, D, seed=20 + v)
+        h_g.append([pin(g[k]) for k in ("rgb", "depth", "alpha", "feat")])
+    d_g = [[torch.empty_like(t, device=dev) for t in h_g[0]] for _ in range(2)]
     outs = [torch.empty((3, H, W), device=dev), torch.empty((H, W), device=dev),
             torch.empty((H, W), device=dev), torch.empty((D, H, W), device=dev)]
     grads = [torch.empty((n, 3), device=dev), torch.empty((n, 3), device=dev),
              torch.empty((n, 4), device=dev), torch.empty(n, device=dev),
              torch.empty((n, K, 3), device=dev), torch.empty((n, D), device=dev),
              torch.empty(6, device=dev)]
-    h_out = [torch.empty_like(t, device="cpu").pin_memory() for t in outs + grads]
-    bi = sum(t.numel() * t.element_size() for t in h_in + h_g)
-    bo = sum(t.numel() * t.element_size() for t in h_out)
+    h_pose = [torch.empty(6).pin_memory() for _ in range(2)]
+    bi = sum(t.numel() * t.element_size() for t in h_g[0])
+    bo = h_pose[0].numel() * h_pose[0].element_size()
+    copy_stream = torch.cuda.Stream(device=dev)
+    total = min(3, args.warmup) + args.steps
+    ev_in = [torch.cuda.Event() for _ in range(total)]
+    ev_used = [torch.cuda.Event() for _ in range(total)]
 
-    def step(c):
-        for d, h in zip(d_in + d_g, h_in + h_g):
-            d.copy_(h, non_blocking=True)
+    def step(k, c):
+        buf = d_g[k % 2]
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(ev_used[k - 2])   # buffer free again
+            for d, h in zip(buf, h_g[k % 2]):
+                d.copy_(h, non_blocking=True)
+            ev_in[k].record(copy_stream)
+        stream.wait_event(ev_in[k])
         L.gs_project(scene, c, ws, stream)
         L.gs_bin_tiles(ws, sync=False, stream=stream)
         L.gs_render_fwd(scene, c, ws, *outs, stream)
-        L.gs_render_bwd(scene, c, ws, *d_g, *grads, stream)
-        for h, d in zip(h_out, outs + grads):
-            h.copy_(d, non_blocking=True)
+        L.gs_render_bwd(scene, c, ws, *buf, *grads, stream)
+        ev_used[k].record(stream)
+        h_pose[k % 2].copy_(grads[-1], non_blocking=True)
 
-    for k in range(min(3, args.warmup)):
-        step(gcams[poses[k]])
+    nw = min(3, args.warmup)
+    for k in range(nw):
+        step(k, gcams[poses[k]])
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
+    copy_stream.wait_event(a)
     for k in range(args.steps):
-        step(gcams[poses[args.warmup + k]])
+        step(nw + k, gcams[poses[args.warmup + k]])
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
     return {"value": round(args.steps * H * W / (ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
             "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
-            "ms_per_step": round(ms / args.steps, 4)}
+            "ms_per_step": round(ms / args.steps, 4),
+            "what": "per step: upstream gradient images host->device (double-buffered on a copy "
+                    "stream), pose gradient device->host; the Gaussians stay resident"}
 
 
 def run_grid(args):
@@ -611,41 +626,52 @@ def run_grid(args):
             sf_tot[name] = sf_tot.get(name, 0.0) + f
     roofline = build_roofline(stage, sb_tot, sf_tot, pairs, args.steps, args.workload)
 
-    # end to end with host buffers: scene parameters and annotations in, feature
-    # gradients and the loss out
+    # end to end with host data: the Gaussians stay resident; every step uploads its frame's
+    # annotations (segmentation and region table; double-buffered on a copy stream) and
+    # reads the loss back
     pin = lambda t: t.cpu().pin_memory()
-    h_in = [pin(t) for t in (scene.means, scene.scales, scene.quats, scene.opacities, scene.sh,
-                             scene.feats, seg, table)]
-    d_in = [torch.empty_like(t, device=dev) for t in h_in]
-    e_scene = L.Scene(*d_in[:6])
-    h_out = [torch.empty_like(g_feats, device="cpu").pin_memory(),
-             torch.empty(3, dtype=torch.float64).pin_memory()]
+    h_in = [[pin(seg), pin(table)], [pin(torch.flip(seg, dims=(1,))), pin(table.flip(0))]]
+    d_in = [[torch.empty_like(t, device=dev) for t in h_in[0]] for _ in range(2)]
+    h_loss = [torch.empty(3, dtype=torch.float64).pin_memory() for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    nw = min(3, args.warmup)
+    ev_in = [torch.cuda.Event() for _ in range(nw + args.steps)]
+    ev_used = [torch.cuda.Event() for _ in range(nw + args.steps)]
 
-    def e2e_step(c):
-        for d, h in zip(d_in, h_in):
-            d.copy_(h, non_blocking=True)
-        L.gs_project(e_scene, c, ws, stream)
+    def e2e_step(k, c):
+        buf = d_in[k % 2]
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(ev_used[k - 2])
+            for d, h in zip(buf, h_in[k % 2]):
+                d.copy_(h, non_blocking=True)
+            ev_in[k].record(copy_stream)
+        stream.wait_event(ev_in[k])
+        L.gs_project(scene, c, ws, stream)
         L.gs_bin_tiles(ws, sync=False, stream=stream)
-        L.gs_grid_target_region(d_in[6], d_in[7], c.stride, c.off_x, c.off_y, tgt, mask, stream)
-        L.gs_render_fwd_loss(e_scene, c, ws, tgt, gF, loss, mask=mask, lambda_sem=1.0, stream=stream)
-        L.gs_render_bwd(e_scene, c, ws, g_feat=gF, g_feats=g_feats, stream=stream)
-        h_out[0].copy_(g_feats, non_blocking=True)
-        h_out[1].copy_(loss, non_blocking=True)
+        L.gs_grid_target_region(buf[0], buf[1], c.stride, c.off_x, c.off_y, tgt, mask, stream)
+        ev_used[k].record(stream)
+        L.gs_render_fwd_loss(scene, c, ws, tgt, gF, loss, mask=mask, lambda_sem=1.0, stream=stream)
+        L.gs_render_bwd(scene, c, ws, g_feat=gF, g_feats=g_feats, stream=stream)
+        h_loss[k % 2].copy_(loss, non_blocking=True)
 
-    for k in range(min(3, args.warmup)):
-        e2e_step(gcams[k])
+    for k in range(nw):
+        e2e_step(k, gcams[k])
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
+    copy_stream.wait_event(a)
     for k in range(args.steps):
-        e2e_step(gcams[args.warmup + k])
+        e2e_step(nw + k, gcams[args.warmup + k])
     b.record(stream)
     torch.cuda.synchronize()
     ems = a.elapsed_time(b)
     e2e = {"value": round(args.steps * P / (ems * 1e-3) / 1e6, 2), "unit": "Mpix/s",
-           "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_in)),
-           "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_out)),
-           "ms_per_step": round(ems / args.steps, 4)}
+           "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in h_in[0])),
+           "d2h_bytes_per_step": int(h_loss[0].numel() * h_loss[0].element_size()),
+           "ms_per_step": round(ems / args.steps, 4),
+           "what": "per step: frame annotations host->device (double-buffered on a copy stream), "
+                   "loss device->host; the Gaussians stay resident"}
     line = {
         "metric": "Mpix/s supervised samples, semantic phase fwd+bwd (grid, fused loss, features-only)",
         "value": round(value, 2), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,

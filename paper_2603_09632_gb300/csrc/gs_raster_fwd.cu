@@ -15,8 +15,9 @@
 namespace gs {
 namespace {
 
-constexpr int kB = 128;    // batch = threads = pixels per work item (half a tile)
-constexpr int kRowsB = kB / 16;
+constexpr int kB = 128;    // batch = threads = pixels per work item (part of a tile)
+constexpr int kRowsB = kB / 16;            // pixel rows per work item
+constexpr int kSplit = kTilePix / kB;      // work items per tile
 
 template <int DP, bool BF16>
 __device__ __forceinline__ void stage_features(const void* __restrict__ feats, int D,
@@ -81,18 +82,19 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   // persistent CTA: tiles from the queue, heaviest first
   for (;;) {
     if (threadIdx.x == 0) {
-      // work item q: half (q & 1) of the (q >> 1)-th tile in heavy-first order
+      // work item q: part (q mod kSplit) of the (q / kSplit)-th tile in heavy-first order
       const uint32_t q = atomicAdd(tq.head, 1u);
-      s_tile = q < 2u * (uint32_t)tq.n_tiles
-                   ? 2 * (int)(tq.order ? tq.order[q >> 1] : (q >> 1)) + (int)(q & 1u)
+      const uint32_t r = q / kSplit;
+      s_tile = q < (uint32_t)kSplit * (uint32_t)tq.n_tiles
+                   ? kSplit * (int)(tq.order ? tq.order[r] : r) + (int)(q - r * kSplit)
                    : -1;
     }
     __syncthreads();
     const int item = s_tile;
     if (item < 0) break;
-    const int tile = item >> 1;
+    const int tile = item / kSplit;
 
-    const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile + kRowsB * (item & 1);
+    const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile + kRowsB * (item % kSplit);
     const int px = tx0 + (threadIdx.x & 15);
     const int py = ty0 + (threadIdx.x >> 4);
     const bool inside = px < cam.W && py < cam.H;
@@ -287,7 +289,7 @@ void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const
               cudaStream_t st) {
   const size_t smem = sizeof(float) * kB * DP;
   auto kern = k_raster_fwd<DP, BF16, LOSS>;
-  const int grid = persistent_grid(kern, kB, smem, 2 * tq.n_tiles);
+  const int grid = persistent_grid(kern, kB, smem, kSplit * tq.n_tiles);
   kern<<<grid, kB, smem, st>>>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
                                T_final, n_contrib, fl);
   note_launch();
