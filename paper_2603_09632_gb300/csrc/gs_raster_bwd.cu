@@ -367,10 +367,13 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
           const int j = t / G, pg = t % G;
           float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
           float so = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sz = 0.f;
-  #pragma unroll 4
-          for (int k = 0; k < kT / G; ++k) {
-            const int q = pg + k * G;
-            if (!(s_live[q >> 5] >> j & 1u)) continue;   // uniform over the G lanes of j
+          // strip by strip: the G lanes of Gaussian j skip whole strips it cannot reach
+          constexpr int PPS = 32 / G;   // pixels per strip per lane
+          for (int ws = 0; ws < kT / 32; ++ws) {
+            if (!(s_live[ws] >> j & 1u)) continue;   // uniform over the G lanes of j
+  #pragma unroll
+            for (int u = 0; u < PPS; ++u) {
+            const int q = ws * 32 + pg + u * G;
             const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
             const float4 e = s_E4[q];
             const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;
@@ -385,6 +388,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             sg = fmaf(w, e.y, sg);
             sb = fmaf(w, e.z, sb);
             sz = fmaf(w, e.w, sz);
+            }
           }
   #pragma unroll
           for (int o = G / 2; o > 0; o >>= 1) {
