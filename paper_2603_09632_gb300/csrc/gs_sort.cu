@@ -135,7 +135,8 @@ k_bin_scan(const uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
     for (int j = 0; j < kScanPer; ++j) {
       if (i0 + j < n_tiles) {
         const int64_t s = min64(off, cap), e = min64((int64_t)off + c[j], cap);
-        ranges[i0 + j] = make_uint2((uint32_t)s, (uint32_t)e);
+        // an empty tile reads as [0, 0)
+        ranges[i0 + j] = c[j] ? make_uint2((uint32_t)s, (uint32_t)e) : make_uint2(0u, 0u);
         cursor[i0 + j] = off;
       }
       off += c[j];

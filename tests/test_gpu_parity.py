@@ -292,3 +292,52 @@ def test_argument_errors():
     with pytest.raises(L.GSError) as e:
         L.gs_project(scene, bad, rast.ws)
     assert e.value.status == L.GS_ERR_ARG
+
+
+# ---------------------------------------------------------------- binning edge cases
+
+def _lists_equal(oracle, sc, cam):
+    from paper_2603_09632_gb300 import _lib as L
+    gpu = U.run(sc, cam)
+    TX, TY = oracle.tiles(cam)
+    keys, ids, ranges = oracle.tile_lists(sc, cam)
+    tiles_g, ids_g, ranges_g = L.gs_get_instances(gpu["rast"].ws, TX * TY)
+    depth_g = L.gs_get_projection(gpu["rast"].ws, sc.n)["depth"].view(np.uint32)
+    keys_g = (tiles_g.astype(np.uint64) << np.uint64(32)) | depth_g[ids_g].astype(np.uint64)
+    np.testing.assert_array_equal(ranges_g, ranges)
+    np.testing.assert_array_equal(keys_g, keys)
+    np.testing.assert_array_equal(ids_g, ids)
+    return gpu, ranges
+
+
+def test_crowded_tiles_longer_than_shared_memory(oracle):
+    """Thousands of Gaussians on the same few tiles: their lists exceed the 2048 entries a
+    block sorts in shared memory, so they take the chunked global path of the tile sort."""
+    rng = np.random.default_rng(21)
+    sc = S.cube_scene(7000, n_feat=4, seed=21, log_scale_mu=-5.5, log_scale_sd=0.2)
+    sc.means[:] = np.stack([rng.uniform(-0.01, 0.01, 7000), rng.uniform(-0.01, 0.01, 7000),
+                            rng.uniform(-0.5, 0.5, 7000)], axis=1)
+    cam = S.pinhole(96, 80, 100.0, 100.0, np.eye(3), np.array([0.0, 0.0, 2.0]))
+    gpu, ranges = _lists_equal(oracle, sc, cam)
+    assert (ranges[:, 1] - ranges[:, 0]).max() > 2048
+    ref = oracle.render(sc, cam, "f32")
+    for k in ("rgb", "depth", "alpha", "feat"):
+        assert U.max_abs_unflagged(gpu[k], ref[k], ref["flags"]) <= TOL_FWD, k
+
+
+@pytest.mark.parametrize("crowded", [False, True])
+def test_equal_depths_are_ordered_by_id(oracle, crowded):
+    """A fronto-parallel plane: every Gaussian has the bit-identical camera depth, so each
+    tile's order is decided by the id tie-break alone (short and chunked sort paths)."""
+    rng = np.random.default_rng(22)
+    n = 5000 if crowded else 3000
+    sc = S.cube_scene(n, n_feat=4, seed=22, log_scale_mu=-4.0, log_scale_sd=0.3)
+    half = 0.01 if crowded else 0.6
+    sc.means[:] = np.stack([rng.uniform(-half, half, n), rng.uniform(-half, half, n),
+                            np.zeros(n)], axis=1)
+    cam = S.pinhole(96, 80, 100.0, 100.0, np.eye(3), np.array([0.0, 0.0, 2.0]))
+    proj = oracle.project(sc, cam, "f32")
+    assert len(np.unique(proj["depth"][proj["valid"]])) == 1
+    gpu, ranges = _lists_equal(oracle, sc, cam)
+    if crowded:
+        assert (ranges[:, 1] - ranges[:, 0]).max() > 2048
