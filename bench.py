@@ -84,7 +84,7 @@ def stage_bytes(st, D, bf, K):
     pix_io = P * (20 + 4 * D + 8)
     return {
         "project": N * 44 + V * (12 * K + 48),
-        "bin": I * 36,
+        "bin": I * 24 + N * 8 + V * 20,
         "fwd": Ie * (44 + D * bf) + pix_io,
         "bwd_raster": pix_io + Ie * (44 + D * bf) + V * (40 + 4 * D),
         "bwd_project": V * (40 + 44 + 12 * K) + V * (44 + 12 * K) + 24,
@@ -98,7 +98,7 @@ def stage_bytes_semantic(st, D, bf):
     V, I, Ie, P = st["visible"], st["instances"], st["inst_eff"], st["pixels"]
     return {
         "project": st["n"] * 44 + V * (12 * 16 + 48),
-        "bin": I * 36,
+        "bin": I * 24 + st["n"] * 8 + V * 20,
         "fwd": Ie * (44 + D * bf) + P * (4 * D + 4 + 4 * D + 8),
         "bwd_raster": P * (4 * D + 8) + Ie * (44 + D * bf) + V * 4 * D,
         "bwd_project": 0,
