@@ -54,6 +54,13 @@ __device__ __forceinline__ bool tile_culled(float x0, float y0, float u, float v
   return box_min_sigma(x0 + 0.5f, y0 + 0.5f, x0 + 15.5f, y0 + 15.5f, u, v, A, B, C) > sigma_cut(o);
 }
 
+// Pixel of thread slot t inside a block 16 pixels wide: each warp owns an 8 x 4 strip
+// (warps two to a row), more compact than a 16 x 2 row pair, so fewer Gaussians reach a
+// strip's box and the per-strip culling drops more (Gaussian, strip) pairs.
+constexpr int kStripW = 8, kStripH = 4;
+__device__ __forceinline__ int strip_px(int t) { return ((t >> 5) & 1) * kStripW + (t & 7); }
+__device__ __forceinline__ int strip_py(int t) { return (t >> 6) * kStripH + ((t & 31) >> 3); }
+
 // Ordered compaction of one flag per thread over a block of NW warps.  Returns the
 // position of a kept item (-1 otherwise) and the number kept.  Contains one barrier;
 // s_wc (NW ints) must not be reused before the next barrier.

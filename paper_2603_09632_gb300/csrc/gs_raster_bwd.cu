@@ -163,13 +163,14 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     const int tile = s_tile;
     if (tile < 0) break;
     const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
-    const int px = tx0 + (t & 15), py = ty0 + (t >> 4);
+    const int px = tx0 + strip_px(t), py = ty0 + strip_py(t);
     const bool inside = px < cam.W && py < cam.H;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
     const int lane = t & 31;
-    // pixel-centre boxes of the tile and of this warp's 16 x 2 strip
+    // pixel-centre boxes of the tile and of this warp's 8 x 4 strip
     const float bx0 = (float)tx0 + 0.5f, by0 = (float)ty0 + 0.5f;
-    const float wbx0 = bx0, wby0 = (float)(ty0 + 2 * (t >> 5)) + 0.5f;
+    const float wbx0 = (float)(tx0 + strip_px(t & ~31)) + 0.5f;
+    const float wby0 = (float)(ty0 + strip_py(t & ~31)) + 0.5f;
     const int64_t HW = (int64_t)cam.W * cam.H;
     const int64_t p = (int64_t)py * cam.W + px;
     const uint2 rg = ranges[tile];
@@ -249,11 +250,12 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         const int jb0 = max(0, jb1 - B), bc = jb1 - jb0;
         const float* s_f = s_fb + (bi & 1) * B * DP;
 
-        // entries of the batch that can reach this warp's 16 x 2 pixel strip
+        // entries of the batch that can reach this warp's 8 x 4 pixel strip
         bool hit = false;
         if (lane < bc) {
           const float4 q0 = s_r0[jb0 + lane], q1 = s_r1[jb0 + lane];
-          hit = box_min_sigma(wbx0, wby0, wbx0 + 15.f, wby0 + 1.f, q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
+          hit = box_min_sigma(wbx0, wby0, wbx0 + (float)(kStripW - 1), wby0 + (float)(kStripH - 1),
+                              q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
         }
         const unsigned live = __ballot_sync(0xffffffffu, hit);
         if (lane == 0) s_live[t >> 5] = live;   // phase 2 skips (Gaussian, strip) pairs not live
@@ -376,7 +378,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             const int q = ws * 32 + pg + u * G;
             const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
             const float4 e = s_E4[q];
-            const float x = (float)(q & 15) - 7.5f, y = (float)(q >> 4) - 7.5f;
+            const float x = (float)strip_px(q) - 7.5f, y = (float)strip_py(q) - 7.5f;
             m1 += gs;
             mx = fmaf(gs, x, mx);
             my = fmaf(gs, y, my);

@@ -95,16 +95,17 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     const int tile = item / kSplit;
 
     const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile + kRowsB * (item % kSplit);
-    const int px = tx0 + (threadIdx.x & 15);
-    const int py = ty0 + (threadIdx.x >> 4);
+    const int px = tx0 + strip_px(threadIdx.x);
+    const int py = ty0 + strip_py(threadIdx.x);
     const bool inside = px < cam.W && py < cam.H;
     const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
     const uint2 rg = ranges[tile];
     const int start = (int)rg.x, end = (int)rg.y;
     const int lane = threadIdx.x & 31;
-    // pixel-centre boxes of the tile and of this warp's 16 x 2 strip
+    // pixel-centre boxes of the work item and of this warp's 8 x 4 strip
     const float bx0 = (float)tx0 + 0.5f, by0 = (float)ty0 + 0.5f;
-    const float wbx0 = bx0, wby0 = (float)(ty0 + 2 * (threadIdx.x >> 5)) + 0.5f;
+    const float wbx0 = (float)(tx0 + strip_px(threadIdx.x & ~31)) + 0.5f;
+    const float wby0 = (float)(ty0 + strip_py(threadIdx.x & ~31)) + 0.5f;
 
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
     float acc[DP > 0 ? DP : 1];
@@ -139,14 +140,15 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       __syncthreads();
       stage_features<DP, BF16>(feats, D, s_id, nk, s_feat);
       __syncthreads();
-      // each warp (a 16 x 2 pixel strip) visits only the entries that can reach its strip:
+      // each warp (an 8 x 4 pixel strip) visits only the entries that can reach its strip:
       // the lanes test 32 entries at a time and the ballot lists the survivors
       for (int g0 = 0; g0 < nk; g0 += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         bool hit = false;
         if (g0 + lane < nk) {
           const float4 q0 = s_r0[g0 + lane], q1 = s_r1[g0 + lane];
-          hit = box_min_sigma(wbx0, wby0, wbx0 + 15.f, wby0 + 1.f, q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
+          hit = box_min_sigma(wbx0, wby0, wbx0 + (float)(kStripW - 1), wby0 + (float)(kStripH - 1),
+                              q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
         }
         unsigned live = __ballot_sync(0xffffffffu, hit);
       while (live) {
