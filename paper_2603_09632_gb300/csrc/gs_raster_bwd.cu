@@ -43,11 +43,20 @@ struct BwdCfg {
   static constexpr int TASKS = JB * CB;
   static constexpr int S = TASKS > 0 ? kT / TASKS : 1;  // pixel split per block
   static constexpr int G = kT / B;                      // threads per Gaussian in phase 2b
-  static constexpr size_t smem_floats =
+  static constexpr int NW = kT / 32;                    // warps
+  static constexpr int PW = TASKS > 0 && TASKS < 32 ? 32 / TASKS : 1;   // parts per warp
+  static_assert(PW == 1 || PW == 2 || PW == 4, "parts of a warp merged by one or two shuffles");
+  static constexpr size_t base_floats =
       (size_t)kT * ES           // s_E: upstream feature gradient per pixel
       + (size_t)(FO ? 1 : 3) * B * kWS   // s_W (and s_GS, s_GO unless FO), j-major
-      + (size_t)(FO ? 0 : 2) * B * DP   // s_f: batch features, double buffered (not when FO)
-      + (size_t)B * DP;         // s_outF: batch feature-gradient sums
+      + (size_t)(FO ? 0 : 2) * B * DP;  // s_f: batch features, double buffered (not when FO)
+  // Feature-gradient sums of a batch: one partial [B][DP] per warp, added in warp order by
+  // the flush (no shared-memory atomics, fixed summation order), unless those partials
+  // would cost the second resident CTA; then one [B][DP] buffer accumulated atomically.
+  static constexpr size_t kSM = 228 * 1024, kStatic = 19 * 1024, kReserve = 1024;
+  static constexpr bool fits2(size_t f) { return 2 * (kStatic + 4 * f + kReserve) <= kSM; }
+  static constexpr bool PART = fits2(base_floats + (size_t)NW * B * DP) || !fits2(base_floats + (size_t)B * DP);
+  static constexpr size_t smem_floats = base_floats + (size_t)(PART ? NW : 1) * B * DP;   // + s_outF
 };
 
 // Features of one batch: fetched into registers, stored to shared memory later.
@@ -149,7 +158,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   float* s_GS = s_W + B * kWS;                // (not allocated when FO)
   float* s_GO = s_GS + B * kWS;
   float* s_fb = s_W + (FO ? 1 : 3) * B * kWS; // [2][B][DP]
-  float* s_outF = s_fb + (FO ? 0 : 2) * B * DP;   // [B][DP]
+  float* s_outF = s_fb + (FO ? 0 : 2) * B * DP;   // [NW][B][DP] partials (PART) or [B][DP]
 
   const int t = threadIdx.x;
   __shared__ int s_tile;
@@ -201,7 +210,8 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   #pragma unroll
       for (int c = 0; c < DP; c += 4)
         *reinterpret_cast<float4*>(s_E + t * Cfg::ES + c) = make_float4(gF[c], gF[c + 1], gF[c + 2], gF[c + 3]);
-      for (int e = t; e < B * DP; e += kT) s_outF[e] = 0.f;
+      if constexpr (!Cfg::PART)
+        for (int e = t; e < B * DP; e += kT) s_outF[e] = 0.f;
     }
     s_E4[t] = make_float4(gC0, gC1, gC2, gD);
     if (t == 0) s_maxn = 0;
@@ -350,16 +360,60 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
                 }
               }
             }
+            if constexpr (Cfg::PART) {
+              // merge the PW parts of this warp (lanes TASKS apart) by a reduce-scatter:
+              // first over the rows a, then (PW = 4) over the columns b; each lane then
+              // stores its share of this warp's partial [B][DP]
+              float* dst = s_outF + (t >> 5) * (B * DP) + 4 * cb;
+              if constexpr (Cfg::PW == 1) {
   #pragma unroll
-            for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a)
+                  *reinterpret_cast<float4*>(dst + (4 * jb + a) * DP) =
+                      make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+              } else {
+                const bool hi = lane & Cfg::TASKS;
+                float h[2][4];   // rows 2 hi + r
   #pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                if (Cfg::S > 1) {
-                  if (lv >> a & 1u) atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
+                for (int r = 0; r < 2; ++r)
+  #pragma unroll
+                  for (int b = 0; b < 4; ++b) {
+                    const float send = hi ? acc[r][b] : acc[r + 2][b];
+                    const float keep = hi ? acc[r + 2][b] : acc[r][b];
+                    h[r][b] = keep + __shfl_xor_sync(0xffffffffu, send, Cfg::TASKS);
+                  }
+                if constexpr (Cfg::PW == 2) {
+  #pragma unroll
+                  for (int r = 0; r < 2; ++r)
+                    *reinterpret_cast<float4*>(dst + (4 * jb + 2 * hi + r) * DP) =
+                        make_float4(h[r][0], h[r][1], h[r][2], h[r][3]);
                 } else {
-                  s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
+                  const bool hi2 = lane & (2 * Cfg::TASKS);
+  #pragma unroll
+                  for (int r = 0; r < 2; ++r) {
+                    float q2[2];   // columns 2 hi2 + b
+  #pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                      const float send = hi2 ? h[r][b] : h[r][b + 2];
+                      const float keep = hi2 ? h[r][b + 2] : h[r][b];
+                      q2[b] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * Cfg::TASKS);
+                    }
+                    *reinterpret_cast<float2*>(dst + (4 * jb + 2 * hi + r) * DP + 2 * hi2) =
+                        make_float2(q2[0], q2[1]);
+                  }
                 }
               }
+            } else {
+  #pragma unroll
+              for (int a = 0; a < 4; ++a)
+  #pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                  if (Cfg::S > 1) {
+                    if (lv >> a & 1u) atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
+                  } else {
+                    s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
+                  }
+                }
+            }
           }
         }
 
@@ -429,21 +483,35 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         }
         __syncthreads();
 
-        // flush and clear the batch's feature-gradient sums
+        // flush the batch's feature-gradient sums (the warps' partials added in warp
+        // order; the single atomic buffer is cleared for the next batch)
         if constexpr (DP > 0) {
           if (g_feats) {
+            constexpr int NP = Cfg::PART ? Cfg::NW : 1;
             if (D == DP) {
               for (int e = t; e < bc * (DP / 4); e += kT) {
                 const int j = e / (DP / 4), q = e - j * (DP / 4);
                 float4* so = reinterpret_cast<float4*>(s_outF + j * DP + 4 * q);
-                atomicAdd(reinterpret_cast<float4*>(g_feats + (int64_t)s_id[jb0 + j] * D + 4 * q), *so);
-                *so = make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 v = *so;
+  #pragma unroll
+                for (int w = 1; w < NP; ++w) {
+                  const float4 u = so[w * (B * DP / 4)];
+                  v.x += u.x;
+                  v.y += u.y;
+                  v.z += u.z;
+                  v.w += u.w;
+                }
+                atomicAdd(reinterpret_cast<float4*>(g_feats + (int64_t)s_id[jb0 + j] * D + 4 * q), v);
+                if constexpr (!Cfg::PART) *so = make_float4(0.f, 0.f, 0.f, 0.f);
               }
             } else {
               for (int e = t; e < bc * DP; e += kT) {
                 const int j = e / DP, c = e - j * DP;
-                if (c < D) atomicAdd(g_feats + (int64_t)s_id[jb0 + j] * D + c, s_outF[e]);
-                s_outF[e] = 0.f;
+                float v = s_outF[e];
+  #pragma unroll
+                for (int w = 1; w < NP; ++w) v += s_outF[w * (B * DP) + e];
+                if (c < D) atomicAdd(g_feats + (int64_t)s_id[jb0 + j] * D + c, v);
+                if constexpr (!Cfg::PART) s_outF[e] = 0.f;
               }
             }
           }
