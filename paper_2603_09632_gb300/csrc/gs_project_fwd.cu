@@ -47,8 +47,10 @@ __device__ __forceinline__ float clamp_tile(float f, int hi) {
   return fminf(fmaxf(f, 0.f), (float)hi);
 }
 
+// At most 40 registers: 12 resident CTAs per SM, so that a few hundred thousand Gaussians
+// are projected in one wave (most of them leave at the frustum test).
 template <int DEG>
-__global__ void __launch_bounds__(kProjThreads)
+__global__ void __launch_bounds__(kProjThreads, 12)
 k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* __restrict__ scales,
           const float* __restrict__ quats, const float* __restrict__ opac,
           const float* __restrict__ sh, GaussRec* __restrict__ rec,

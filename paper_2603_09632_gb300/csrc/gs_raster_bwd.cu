@@ -287,18 +287,19 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
                 w = a * T;
                 if constexpr (!FO) {
                 const float4 r2 = s_r2[jb0 + j];
-                float dot = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r1.z;
+                float d0 = gC0 * r2.x, d1 = gC1 * r2.y, d2 = gC2 * r2.z, d3 = gD * r1.z;
                 if constexpr (DP > 0) {
                   const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
   #pragma unroll
                   for (int q = 0; q < DP / 4; ++q) {
                     const float4 f = f4[q];
-                    dot = fmaf(gF[4 * q], f.x, dot);
-                    dot = fmaf(gF[4 * q + 1], f.y, dot);
-                    dot = fmaf(gF[4 * q + 2], f.z, dot);
-                    dot = fmaf(gF[4 * q + 3], f.w, dot);
+                    d0 = fmaf(gF[4 * q], f.x, d0);
+                    d1 = fmaf(gF[4 * q + 1], f.y, d1);
+                    d2 = fmaf(gF[4 * q + 2], f.z, d2);
+                    d3 = fmaf(gF[4 * q + 3], f.w, d3);
                   }
                 }
+                const float dot = (d0 + d1) + (d2 + d3);
                 const float galpha = T * (dot - s_run) + gAT * inv;
                 s_run = a * dot + (1.f - a) * s_run;
                 if (oG <= kAlphaMax) {
