@@ -15,7 +15,8 @@
 // compacted into shared memory.  The compacted chunk is processed in batches of B
 // Gaussians.  Phase 1 (one thread per pixel) writes w, dL/dsigma and dL/do of each
 // (pixel, Gaussian) pair to shared memory.  Phase 2 reduces over the 256 pixels of the
-// tile: the feature gradient is the contraction W^T g_F with 4x4 register blocks, and
+// tile: the feature gradient is the contraction W^T g_F with 4x4 register blocks (pixel
+// parts summed through per-warp partials in shared memory, in a fixed order), and
 // colour/depth/opacity sums and the pixel moments sum_p dL/dsigma * (1, x, y, xx, xy, yy)
 // (from which the conic and mean gradients are formed exactly) are warp reductions.
 // The next batch's features are fetched into registers during phase 2.  Two barriers
@@ -36,27 +37,31 @@ constexpr int kWS = kT + 4;    // row stride of the j-major pair arrays (floats)
 
 template <int DP, bool FO = false>
 struct BwdCfg {
-  static constexpr int B = DP >= 64 ? 8 : 16;          // Gaussians per batch
+  // Gaussians per batch: 8 where a 16-Gaussian batch would leave room for only one
+  // resident CTA (64 channels features-only, 32 channels with every gradient)
+  static constexpr int B = (DP >= 64 && FO) || (DP == 32 && !FO) ? 8 : 16;
   static constexpr int ES = DP + 4;                     // row stride of s_E (floats)
   static constexpr int JB = B / 4;                      // 4x4 blocks of the contraction
   static constexpr int CB = DP / 4;
   static constexpr int TASKS = JB * CB;
   static constexpr int S = TASKS > 0 ? kT / TASKS : 1;  // pixel split per block
+  static constexpr int PP = kT / S;                     // pixels per part
   static constexpr int G = kT / B;                      // threads per Gaussian in phase 2b
   static constexpr int NW = kT / 32;                    // warps
   static constexpr int PW = TASKS > 0 && TASKS < 32 ? 32 / TASKS : 1;   // parts per warp
   static_assert(PW == 1 || PW == 2 || PW == 4, "parts of a warp merged by one or two shuffles");
+  static_assert(TASKS == 0 || TASKS % 32 == 0 || 32 % TASKS == 0, "tasks tile the warps");
   static constexpr size_t base_floats =
       (size_t)kT * ES           // s_E: upstream feature gradient per pixel
       + (size_t)(FO ? 1 : 3) * B * kWS   // s_W (and s_GS, s_GO unless FO), j-major
       + (size_t)(FO ? 0 : 2) * B * DP;  // s_f: batch features, double buffered (not when FO)
-  // Feature-gradient sums of a batch: one partial [B][DP] per warp, added in warp order by
-  // the flush (no shared-memory atomics, fixed summation order), unless those partials
-  // would cost the second resident CTA; then one [B][DP] buffer accumulated atomically.
+  // Feature-gradient sums of a batch: one partial [B][DP] per warp (parts of a warp merged
+  // by shuffles) or per part (a part spanning several warps), added in order by the flush:
+  // no shared-memory atomics, and a fixed summation order.
+  static constexpr int NPART = PW > 1 ? NW : S;
+  static constexpr size_t smem_floats = base_floats + (size_t)NPART * B * DP;   // + s_outF
   static constexpr size_t kSM = 228 * 1024, kStatic = 19 * 1024, kReserve = 1024;
-  static constexpr bool fits2(size_t f) { return 2 * (kStatic + 4 * f + kReserve) <= kSM; }
-  static constexpr bool PART = fits2(base_floats + (size_t)NW * B * DP) || !fits2(base_floats + (size_t)B * DP);
-  static constexpr size_t smem_floats = base_floats + (size_t)(PART ? NW : 1) * B * DP;   // + s_outF
+  static constexpr int CTAS = 2 * (kStatic + 4 * smem_floats + kReserve) <= kSM ? 2 : 1;   // per SM
 };
 
 // Features of one batch: fetched into registers, stored to shared memory later.
@@ -135,7 +140,7 @@ __device__ __forceinline__ void red_add4(float* dst, float a, float b, float c, 
 }
 
 template <int DP, bool BF16, bool FO>
-__global__ void __launch_bounds__(kT, 2)
+__global__ void __launch_bounds__(kT, (BwdCfg<DP, FO>::CTAS))
 k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
              const void* __restrict__ feats, int D,
              const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_id,
@@ -158,7 +163,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   float* s_GS = s_W + B * kWS;                // (not allocated when FO)
   float* s_GO = s_GS + B * kWS;
   float* s_fb = s_W + (FO ? 1 : 3) * B * kWS; // [2][B][DP]
-  float* s_outF = s_fb + (FO ? 0 : 2) * B * DP;   // [NW][B][DP] partials (PART) or [B][DP]
+  float* s_outF = s_fb + (FO ? 0 : 2) * B * DP;   // [NPART][B][DP] partial sums
 
   const int t = threadIdx.x;
   __shared__ int s_tile;
@@ -210,8 +215,6 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   #pragma unroll
       for (int c = 0; c < DP; c += 4)
         *reinterpret_cast<float4*>(s_E + t * Cfg::ES + c) = make_float4(gF[c], gF[c + 1], gF[c + 2], gF[c + 3]);
-      if constexpr (!Cfg::PART)
-        for (int e = t; e < B * DP; e += kT) s_outF[e] = 0.f;
     }
     s_E4[t] = make_float4(gC0, gC1, gC2, gD);
     if (t == 0) s_maxn = 0;
@@ -332,88 +335,83 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             const int cb = t % Cfg::CB;
             const int jb = (t / Cfg::CB) % Cfg::JB;
             const int part = t / Cfg::TASKS;
-            constexpr int PP = kT / Cfg::S;     // pixels per part
+            constexpr int PP = Cfg::PP;
             float acc[4][4];
   #pragma unroll
             for (int a = 0; a < 4; ++a)
   #pragma unroll
               for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-            const int p0 = part * PP;                     // the part lies in one warp strip
-            const unsigned lv = (s_live[p0 >> 5] >> (4 * jb)) & 15u;
+            // a part lies in one warp strip or spans whole strips; W holds values only where
+            // the Gaussian is live for the strip, so liveness is applied strip by strip
+            constexpr int NSP = PP >= 32 ? PP / 32 : 1;   // strips per part
+            constexpr int QS = PP >= 32 ? 32 : PP;        // pixels per (part, strip)
+            const int p0 = part * PP;
+  #pragma unroll
+            for (int ws = 0; ws < NSP; ++ws) {
+              const int q0 = p0 + ws * QS;
+              const unsigned lv = (s_live[q0 >> 5] >> (4 * jb)) & 15u;
   #pragma unroll 2
-            for (int q = p0; q < (lv ? p0 + PP : p0); q += 4) {
-              float4 wv[4], ev[4];
+              for (int q = q0; q < (lv ? q0 + QS : q0); q += 4) {
+                float4 wv[4], ev[4];
   #pragma unroll
-              for (int a = 0; a < 4; ++a)
-                wv[a] = (lv >> a & 1u) ? *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q)
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int a = 0; a < 4; ++a)
+                  wv[a] = (lv >> a & 1u) ? *reinterpret_cast<const float4*>(s_W + (4 * jb + a) * kWS + q)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
   #pragma unroll
-              for (int b = 0; b < 4; ++b) ev[b] = *reinterpret_cast<const float4*>(s_E + (q + b) * Cfg::ES + 4 * cb);
+                for (int b = 0; b < 4; ++b) ev[b] = *reinterpret_cast<const float4*>(s_E + (q + b) * Cfg::ES + 4 * cb);
   #pragma unroll
-              for (int a = 0; a < 4; ++a) {
-                const float wa[4] = {wv[a].x, wv[a].y, wv[a].z, wv[a].w};
+                for (int a = 0; a < 4; ++a) {
+                  const float wa[4] = {wv[a].x, wv[a].y, wv[a].z, wv[a].w};
   #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                  acc[a][0] = fmaf(wa[b], ev[b].x, acc[a][0]);
-                  acc[a][1] = fmaf(wa[b], ev[b].y, acc[a][1]);
-                  acc[a][2] = fmaf(wa[b], ev[b].z, acc[a][2]);
-                  acc[a][3] = fmaf(wa[b], ev[b].w, acc[a][3]);
+                  for (int b = 0; b < 4; ++b) {
+                    acc[a][0] = fmaf(wa[b], ev[b].x, acc[a][0]);
+                    acc[a][1] = fmaf(wa[b], ev[b].y, acc[a][1]);
+                    acc[a][2] = fmaf(wa[b], ev[b].z, acc[a][2]);
+                    acc[a][3] = fmaf(wa[b], ev[b].w, acc[a][3]);
+                  }
                 }
               }
             }
-            if constexpr (Cfg::PART) {
-              // merge the PW parts of this warp (lanes TASKS apart) by a reduce-scatter:
-              // first over the rows a, then (PW = 4) over the columns b; each lane then
-              // stores its share of this warp's partial [B][DP]
-              float* dst = s_outF + (t >> 5) * (B * DP) + 4 * cb;
-              if constexpr (Cfg::PW == 1) {
-  #pragma unroll
-                for (int a = 0; a < 4; ++a)
-                  *reinterpret_cast<float4*>(dst + (4 * jb + a) * DP) =
-                      make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-              } else {
-                const bool hi = lane & Cfg::TASKS;
-                float h[2][4];   // rows 2 hi + r
-  #pragma unroll
-                for (int r = 0; r < 2; ++r)
-  #pragma unroll
-                  for (int b = 0; b < 4; ++b) {
-                    const float send = hi ? acc[r][b] : acc[r + 2][b];
-                    const float keep = hi ? acc[r + 2][b] : acc[r][b];
-                    h[r][b] = keep + __shfl_xor_sync(0xffffffffu, send, Cfg::TASKS);
-                  }
-                if constexpr (Cfg::PW == 2) {
-  #pragma unroll
-                  for (int r = 0; r < 2; ++r)
-                    *reinterpret_cast<float4*>(dst + (4 * jb + 2 * hi + r) * DP) =
-                        make_float4(h[r][0], h[r][1], h[r][2], h[r][3]);
-                } else {
-                  const bool hi2 = lane & (2 * Cfg::TASKS);
-  #pragma unroll
-                  for (int r = 0; r < 2; ++r) {
-                    float q2[2];   // columns 2 hi2 + b
-  #pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                      const float send = hi2 ? h[r][b] : h[r][b + 2];
-                      const float keep = hi2 ? h[r][b + 2] : h[r][b];
-                      q2[b] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * Cfg::TASKS);
-                    }
-                    *reinterpret_cast<float2*>(dst + (4 * jb + 2 * hi + r) * DP + 2 * hi2) =
-                        make_float2(q2[0], q2[1]);
-                  }
-                }
-              }
-            } else {
+            // merge the PW parts of this warp (lanes TASKS apart) by a reduce-scatter: first
+            // over the rows a, then (PW = 4) over the columns b; each lane then stores its
+            // share of this warp's partial [B][DP] (PW = 1: its task's block of its part's)
+            float* dst = s_outF + (Cfg::PW > 1 ? t >> 5 : part) * (B * DP) + 4 * cb;
+            if constexpr (Cfg::PW == 1) {
   #pragma unroll
               for (int a = 0; a < 4; ++a)
+                *reinterpret_cast<float4*>(dst + (4 * jb + a) * DP) =
+                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+            } else {
+              const bool hi = lane & Cfg::TASKS;
+              float h[2][4];   // rows 2 hi + r
+  #pragma unroll
+              for (int r = 0; r < 2; ++r)
   #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                  if (Cfg::S > 1) {
-                    if (lv >> a & 1u) atomicAdd(&s_outF[(4 * jb + a) * DP + 4 * cb + b], acc[a][b]);
-                  } else {
-                    s_outF[(4 * jb + a) * DP + 4 * cb + b] = acc[a][b];
-                  }
+                  const float send = hi ? acc[r][b] : acc[r + 2][b];
+                  const float keep = hi ? acc[r + 2][b] : acc[r][b];
+                  h[r][b] = keep + __shfl_xor_sync(0xffffffffu, send, Cfg::TASKS);
                 }
+              if constexpr (Cfg::PW == 2) {
+  #pragma unroll
+                for (int r = 0; r < 2; ++r)
+                  *reinterpret_cast<float4*>(dst + (4 * jb + 2 * hi + r) * DP) =
+                      make_float4(h[r][0], h[r][1], h[r][2], h[r][3]);
+              } else {
+                const bool hi2 = lane & (2 * Cfg::TASKS);
+  #pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                  float q2[2];   // columns 2 hi2 + b
+  #pragma unroll
+                  for (int b = 0; b < 2; ++b) {
+                    const float send = hi2 ? h[r][b] : h[r][b + 2];
+                    const float keep = hi2 ? h[r][b + 2] : h[r][b];
+                    q2[b] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * Cfg::TASKS);
+                  }
+                  *reinterpret_cast<float2*>(dst + (4 * jb + 2 * hi + r) * DP + 2 * hi2) =
+                      make_float2(q2[0], q2[1]);
+                }
+              }
             }
           }
         }
@@ -484,11 +482,10 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
         }
         __syncthreads();
 
-        // flush the batch's feature-gradient sums (the warps' partials added in warp
-        // order; the single atomic buffer is cleared for the next batch)
+        // flush the batch's feature-gradient sums (the partials added in order)
         if constexpr (DP > 0) {
           if (g_feats) {
-            constexpr int NP = Cfg::PART ? Cfg::NW : 1;
+            constexpr int NP = Cfg::NPART;
             if (D == DP) {
               for (int e = t; e < bc * (DP / 4); e += kT) {
                 const int j = e / (DP / 4), q = e - j * (DP / 4);
@@ -503,7 +500,6 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
                   v.w += u.w;
                 }
                 atomicAdd(reinterpret_cast<float4*>(g_feats + (int64_t)s_id[jb0 + j] * D + 4 * q), v);
-                if constexpr (!Cfg::PART) *so = make_float4(0.f, 0.f, 0.f, 0.f);
               }
             } else {
               for (int e = t; e < bc * DP; e += kT) {
@@ -512,7 +508,6 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   #pragma unroll
                 for (int w = 1; w < NP; ++w) v += s_outF[w * (B * DP) + e];
                 if (c < D) atomicAdd(g_feats + (int64_t)s_id[jb0 + j] * D + c, v);
-                if constexpr (!Cfg::PART) s_outF[e] = 0.f;
               }
             }
           }

@@ -28,6 +28,9 @@ CASES = {
     "tiny": lambda: (S.config_tiny()[0], S.config_tiny()[1][0]),
     "room_ragged": small_room,
     "room_sh1_d8": lambda: small_room(n=20_000, W=97, H=61, D=8, deg=1, pose=5),
+    # 32 and 64 channels: the backward's 8- and 16-Gaussian batch configurations
+    "room_d32": lambda: small_room(n=20_000, W=150, H=100, D=32, deg=0, pose=2),
+    "room_d64": lambda: small_room(n=20_000, W=150, H=100, D=64, deg=2, pose=6),
 }
 
 
