@@ -64,9 +64,10 @@ __device__ __forceinline__ void stage_features(const void* __restrict__ feats, i
   }
 }
 
-// Up to 16 channels the kernel fits 80 registers: six resident CTAs (24 warps) per SM.
+// Resident CTAs per SM by channel count, the most whose register share (80, 96, 128) holds
+// the kernel without spills: 6 up to 16 channels, 5 at 32, 4 at 64.
 template <int DP, bool BF16, bool LOSS>
-__global__ void __launch_bounds__(kB, DP <= 16 ? 6 : 1)
+__global__ void __launch_bounds__(kB, DP <= 16 ? 6 : (DP <= 32 ? 5 : 4))
 k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
              const void* __restrict__ feats, int D, const uint2* __restrict__ ranges,
              const uint32_t* __restrict__ inst_id, float* __restrict__ rgb,
