@@ -131,8 +131,11 @@ gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
                      void* stream);
 
 /* a2. Tile/depth binning ("depth-sorted", Eq. 1).  Produces, per 16x16 tile, the list
- * of Gaussians covering it sorted by (depth, id), with a hand-written LSD radix sort
- * (depth sort of the visible Gaussians, then a stable sort of the instances by tile).
+ * of Gaussians covering it sorted by (depth, id), in tile buckets: the per-tile instance
+ * counts (added by gs_project) are scanned into tile ranges, the instances are scattered
+ * into their tiles' ranges, and each range is sorted by depth with a hand-written LSD
+ * radix sort, equal depths in id order.  Calling it again before the next gs_project
+ * changes nothing.
  * If n_instances_out is non-NULL the call synchronises the stream once to read the
  * instance count I, grows the workspace if needed and stores I there.  If it is NULL
  * the call never synchronises: the reserved instance capacity must be large enough,

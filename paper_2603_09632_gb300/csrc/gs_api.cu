@@ -33,6 +33,12 @@ struct DevBuf {
     if (e == cudaSuccess) cap = m;
     return e;
   }
+  // as ensure(), and a (re)allocated buffer is filled with zeros
+  cudaError_t ensure_zeroed(size_t n) {
+    if (n <= cap) return cudaSuccess;
+    cudaError_t e = ensure(n);
+    return e == cudaSuccess ? cudaMemset(p, 0, cap * sizeof(T)) : e;
+  }
   void release() {
     if (p) cudaFree(p);
     p = nullptr;
@@ -51,13 +57,15 @@ struct gs_workspace {
   DevBuf<uint32_t> depth_key, ntiles;
   DevBuf<uint2> rect;
   DevBuf<uint32_t> item_max;   // per grid work item, statistics only
+  bool tile_counts_dirty = false;   // tile_count holds a projection's counts not yet scanned
   DevBuf<float> g2d;
   DevBuf<float> pose_partials;
   // per instance: sorted depth keys and ids, their ping-pong space, the slot's tile
   DevBuf<uint32_t> inst_key, inst_id, inst_key2, inst_id2, inst_tile;
   // per tile / pixel
   DevBuf<uint2> ranges;
-  DevBuf<uint32_t> tile_order, queue;   // heavy-first tile order; persistent-kernel queue heads
+  DevBuf<uint32_t> tile_order, queue;   // heavy-first tile order; persistent-kernel queues
+                                        // (head, leave count): fwd [0, 1], bwd [2, 3], sort [4, 5]
   DevBuf<uint32_t> tile_count, tile_cursor;   // binning scratch
   bool ordered = false;
   DevBuf<float> T_final;
@@ -203,7 +211,7 @@ cudaError_t ensure_pix(gs_workspace* ws, int64_t npix, int64_t ntiles) {
       (e = ws->n_contrib.ensure((size_t)std::max<int64_t>(npix, 1))))
     return e;
   const size_t t = (size_t)std::max<int64_t>(ntiles, 1);
-  if ((e = ws->tile_order.ensure(t)) || (e = ws->tile_count.ensure(t)) ||
+  if ((e = ws->tile_order.ensure(t)) || (e = ws->tile_count.ensure_zeroed(t)) ||
       (e = ws->tile_cursor.ensure(t)))
     return e;
   return ws->ranges.ensure(t);
@@ -238,8 +246,9 @@ gs_status gs_workspace_create(gs_workspace** out, int device) {
   if (!ws) return GS_ERR_OOM;
   ws->device = device;
   DeviceGuard g(device);
-  if (ws->counters.ensure(kCntNum) != cudaSuccess || ws->queue.ensure(4) != cudaSuccess ||
+  if (ws->counters.ensure(kCntNum) != cudaSuccess || ws->queue.ensure(8) != cudaSuccess ||
       cudaMemset(ws->counters.p, 0, kCntNum * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(ws->queue.p, 0, 8 * sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(&ws->h_counters, kCntNum * sizeof(uint32_t)) != cudaSuccess) {
     gs_workspace_destroy(ws);
     return GS_ERR_OOM;
@@ -311,8 +320,13 @@ gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
   GS_TRY(ensure_pix(ws, (int64_t)cd.GW * cd.GH, (int64_t)cd.TX * cd.TY));
   StageTimer tm(ws, GS_TIMER_PROJECT, st);
   GS_TRY(cudaMemsetAsync(ws->counters.p + kCntVisible, 0, 2 * sizeof(uint32_t), st));
+  // the tile counts are zero unless a projection was not followed by a binning (whose scan
+  // clears them after reading)
+  if (ws->tile_counts_dirty)
+    GS_TRY(cudaMemsetAsync(ws->tile_count.p, 0, sizeof(uint32_t) * ws->tile_count.cap, st));
   launch_project(*scene, cd, ws->rec.p, ws->depth_key.p, ws->ntiles.p, ws->rect.p, ws->counters.p,
-                 st);
+                 ws->tile_count.p, st);
+  ws->tile_counts_dirty = true;
   GS_TRY(cudaGetLastError());
   ws->n = scene->n;
   ws->cam = cd;
@@ -331,6 +345,16 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   if (ws->stage < 1) return GS_ERR_STATE;
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
+  if (ws->stage >= 2 && !ws->tile_counts_dirty) {
+    // this projection is binned already (its scan consumed the tile counts): nothing to redo
+    if (n_instances_out) {
+      GS_TRY(cudaMemcpyAsync(ws->h_counters, ws->counters.p, kCntNum * sizeof(uint32_t),
+                             cudaMemcpyDeviceToHost, st));
+      GS_TRY(cudaStreamSynchronize(st));
+      *n_instances_out = (int64_t)ws->h_counters[kCntInst];
+    }
+    return GS_OK;
+  }
   const int64_t n = ws->n;
   const int ntl = ws->TX * ws->TY;
   StageTimer tm(ws, GS_TIMER_BIN, st);
@@ -360,7 +384,7 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   b.cursor = ws->tile_cursor.p;
   b.ranges = ws->ranges.p;
   b.order = ws->tile_order.p;
-  b.queue = ws->queue.p + 2;
+  b.queue = ws->queue.p + 4;
   b.key0 = ws->inst_key.p;
   b.id0 = ws->inst_id.p;
   b.key1 = ws->inst_key2.p;
@@ -368,6 +392,7 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   b.tile_out = ws->inst_tile.p;
   b.counters = cnt;
   ws->ordered = launch_bin(b, st);
+  ws->tile_counts_dirty = false;   // the scan cleared them
   ws->tile_sorted = ws->inst_tile.p;
   ws->id_sorted = ws->inst_id.p;
   GS_TRY(cudaGetLastError());
@@ -408,9 +433,9 @@ gs_status render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
   DeviceGuard g(ws->device);
   cudaStream_t st = (cudaStream_t)stream;
   StageTimer tm(ws, GS_TIMER_FWD, st);
-  GS_TRY(cudaMemsetAsync(ws->queue.p, 0, sizeof(uint32_t), st));
   if (loss) GS_TRY(cudaMemsetAsync(loss->loss, 0, 3 * sizeof(double), st));
-  const TileQueue tq{ws->queue.p, ws->ordered ? ws->tile_order.p : nullptr, cd.TX * cd.TY};
+  const TileQueue tq{ws->queue.p, ws->queue.p + 1, ws->ordered ? ws->tile_order.p : nullptr,
+                     cd.TX * cd.TY};
   if (cd.stride > 1)
     launch_grid_fwd(cd, tq, ws->rec.p, scene->feats, scene->feat_dtype, scene->n_feat, ws->ranges.p,
                     ws->id_sorted, rgb, depth, alpha, scene->n_feat > 0 ? feat : nullptr,
@@ -466,8 +491,11 @@ gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
       GS_TRY(cudaMemsetAsync(ws->g2d.p, 0, sizeof(float) * kG2D * (size_t)n, st));
     if (g_feats && n > 0 && D > 0)
       GS_TRY(cudaMemsetAsync(g_feats, 0, sizeof(float) * (size_t)n * D, st));
-    GS_TRY(cudaMemsetAsync(ws->queue.p + 1, 0, sizeof(uint32_t), st));
-    const TileQueue tq{ws->queue.p + 1, ws->ordered ? ws->tile_order.p : nullptr, cd.TX * cd.TY};
+    // the backward kernels leave their queue to the host: zeroed before each launch (a
+    // self-resetting queue measured slower in these kernels)
+    GS_TRY(cudaMemsetAsync(ws->queue.p + 2, 0, 8, st));
+    const TileQueue tq{ws->queue.p + 2, ws->queue.p + 3, ws->ordered ? ws->tile_order.p : nullptr,
+                       cd.TX * cd.TY};
     const float* gf = D > 0 ? g_feat : nullptr;
     float* gfe = D > 0 ? g_feats : nullptr;
     if (cd.stride > 1)

@@ -57,12 +57,15 @@ enum : int {
 // ---- launchers (each .cu file defines its own) --------------------------------------
 
 // gs_project_fwd.cu
-// Also adds V (visible Gaussians) and I (tile instances) to counters[kCntVisible/kCntInst].
+// Also adds V (visible Gaussians) and I (tile instances) to counters[kCntVisible/kCntInst]
+// and each Gaussian's tiles to tile_count[cam.TX * cam.TY] (the binning's per-tile counts,
+// zero before the launch; the binning's scan clears them again after reading them).
 void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32_t* depth_key,
-                    uint32_t* ntiles, uint2* rect, uint32_t* counters, cudaStream_t st);
+                    uint32_t* ntiles, uint2* rect, uint32_t* counters, uint32_t* tile_count,
+                    cudaStream_t st);
 
-// gs_sort.cu: binning in tile buckets (count, scan, scatter, per-tile radix sort).
-// After launch_bin, tile t's Gaussians occupy slots [ranges[t].x, ranges[t].y) of id0 in
+// gs_sort.cu: binning in tile buckets (scan, scatter, per-tile radix sort; the count is
+// added by the projection).  After launch_bin, tile t's Gaussians occupy slots [ranges[t].x, ranges[t].y) of id0 in
 // (depth, id) order (key0 holds their depth keys, tile_out their tile); slots are capped
 // at `cap` (an instance count above it sets kErrInstOverflow).  `order` receives the
 // heavy-first tile order when there are at most kMaxOrderedTiles tiles (the return value
@@ -74,11 +77,12 @@ struct BinArgs {
   const uint32_t* depth_key;     // [n]
   int TX, n_tiles;
   int64_t cap;                   // instance slots available
-  uint32_t* tile_count;          // [n_tiles] scratch
+  uint32_t* tile_count;          // [n_tiles] tile instance counts (from the projection; the
+                                 // scan zeroes them after reading)
   uint32_t* cursor;              // [n_tiles] scratch
   uint2* ranges;                 // [n_tiles] out
   uint32_t* order;               // [n_tiles] out (heavy-first)
-  uint32_t* queue;               // one word (persistent sort queue head)
+  uint32_t* queue;               // two words: the persistent sort's queue head and leave count
   uint32_t *key0, *id0;          // [cap] out: sorted depth keys and Gaussian ids
   uint32_t *key1, *id1;          // [cap] scratch (ranges longer than shared memory)
   uint32_t* tile_out;            // [cap] out: tile of every slot
@@ -93,13 +97,76 @@ void launch_pair_stats(const CamDev& cam, const GaussRec* rec, const uint2* rang
                        const uint32_t* inst_id, const uint32_t* n_contrib,
                        unsigned long long* stats64, cudaStream_t st);
 
-// Persistent raster scheduling: a CTA takes the next tile index from *queue (zeroed
-// before each launch) and maps it through `order` (identity when null).
+// Persistent raster scheduling: a CTA (or warp) takes the next item index from *head and
+// maps it through `order` (identity when null).  The forward, sort and grid-forward queues
+// reset themselves: every participant calls queue_leave() once after its last take, and
+// the last one to leave puts head and done back to zero, so a launch finds both at zero
+// without a memset (they are zeroed once when allocated).  The backward kernels' queue is
+// zeroed by the host before each launch.
 struct TileQueue {
   uint32_t* head;
+  uint32_t* done;
   const uint32_t* order;
   int n_tiles;
 };
+
+// The tile instances of the 32 Gaussians of a warp, flattened: lane j of round r handles
+// instance r * 32 + j of the warp (Gaussians in lane order, tiles of a Gaussian in
+// row-major order of its rectangle).  nt and rc are the calling lane's tile count and
+// packed rectangle (x0 | y0 << 16, x1 | y1 << 16); f(owner_lane, tile) is called by every
+// lane in every round, with tile = 0xFFFFFFFF for lanes past the last instance.
+template <class F>
+__device__ __forceinline__ void warp_tile_instances(uint32_t nt, uint2 rc, int TX, F f) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  uint32_t incl = nt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(full, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t excl = incl - nt;
+  const uint32_t total = __shfl_sync(full, incl, 31);
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t k = base + lane;
+    // owner: the last lane whose first instance is <= k (it has at least one instance)
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const int mid = (lo + hi + 1) >> 1;
+      const uint32_t e = __shfl_sync(full, excl, mid);
+      if (e <= k) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t oe = __shfl_sync(full, excl, lo);
+    const uint32_t rx = __shfl_sync(full, rc.x, lo), ry = __shfl_sync(full, rc.y, lo);
+    uint32_t tile = 0xFFFFFFFFu;
+    if (k < total) {
+      const uint32_t x0 = rx & 0xFFFFu, y0 = rx >> 16, w = (ry & 0xFFFFu) - x0;
+      const uint32_t q = k - oe;
+      if (w) tile = (y0 + q / w) * (uint32_t)TX + x0 + q % w;
+    }
+    f(lo, tile);
+  }
+}
+
+// Adds each lane's tile instances to tile_count: one atomic per distinct tile per warp round.
+__device__ __forceinline__ void warp_count_tiles(uint32_t nt, uint2 rc, int TX, int n_tiles,
+                                                 uint32_t* tile_count) {
+  warp_tile_instances(nt, rc, TX, [&](int, uint32_t tile) {
+    const bool ok = tile < (uint32_t)n_tiles;
+    const uint32_t peers = __match_any_sync(0xffffffffu, ok ? tile : 0xFFFFFFFFu);
+    if (ok && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0)
+      atomicAdd(&tile_count[tile], (uint32_t)__popc(peers));
+  });
+}
+
+__device__ __forceinline__ void queue_leave(const TileQueue& tq, unsigned participants) {
+  __threadfence();   // this participant's takes precede its leave
+  if (atomicAdd(tq.done, 1u) == participants - 1u) {
+    atomicExch(tq.head, 0u);
+    atomicExch(tq.done, 0u);
+  }
+}
 
 // Grid of a persistent kernel: as many CTAs as fit on the device at once (never more than
 // n_items).  Sets the kernel's dynamic shared-memory limit to `smem`: static plus dynamic

@@ -42,8 +42,8 @@ constexpr size_t oOrder = al(oRanges + kNaMaxTiles * 8);
 constexpr size_t oTCount = al(oOrder + kNaMaxTiles * 4);    // binning scratch
 constexpr size_t oTCursor = al(oTCount + kNaMaxTiles * 4);
 constexpr size_t oCnt = al(oTCursor + kNaMaxTiles * 4);     // counters
-constexpr size_t oQueue = al(oCnt + kCntNum * 4);           // persistent-kernel queue heads
-constexpr size_t kNaBytes = al(oQueue + 4 * 4);
+constexpr size_t oQueue = al(oCnt + kCntNum * 4);           // persistent-kernel queues
+constexpr size_t kNaBytes = al(oQueue + 8 * 4);
 
 }  // namespace
 }  // namespace gs
@@ -136,10 +136,14 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base + oCnt);
   uint32_t* queue = reinterpret_cast<uint32_t*>(base + oQueue);
 
-  // the array keeps the previous call's contents: clear what must start at zero (the
-  // binning clears its own tile counters and queue head)
-  if (cudaMemsetAsync(cnt, 0, kCntNum * 4, st) != cudaSuccess) return GS_ERR_CUDA;
-  launch_project(*scene, cd, rec, key, nt, rect, cnt, st);
+  // the array keeps the previous call's contents: clear what must start at zero (counters,
+  // the tile counts the projection adds to, and the queues, which reset themselves but are
+  // cleared here as well since nothing else initialises this array)
+  if (cudaMemsetAsync(cnt, 0, kCntNum * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(queue, 0, 4 * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(tcount, 0, ntl * 4, st) != cudaSuccess)
+    return GS_ERR_CUDA;
+  launch_project(*scene, cd, rec, key, nt, rect, cnt, tcount, st);
   // the instance count decides whether the request fits: one synchronisation
   uint32_t h_cnt[kCntNum];
   if (cudaMemcpyAsync(h_cnt, cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -159,7 +163,7 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   b.cursor = tcursor;
   b.ranges = ranges;
   b.order = order;
-  b.queue = queue + 1;
+  b.queue = queue + 2;
   b.key0 = k0;
   b.id0 = i0;
   b.key1 = k1;
@@ -167,8 +171,7 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   b.tile_out = tile_of;
   b.counters = cnt;
   const bool ordered = launch_bin(b, st);
-  if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GS_ERR_CUDA;
-  const TileQueue tq{queue, ordered ? order : nullptr, (int)ntl};
+  const TileQueue tq{queue, queue + 1, ordered ? order : nullptr, (int)ntl};
   launch_raster_fwd(cd, tq, rec, scene->feats, scene->feat_dtype, scene->n_feat, ranges, i0, rgb,
                     depth, alpha, scene->n_feat > 0 ? feat : nullptr, Tf, nc, nullptr, st);
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;

@@ -74,10 +74,8 @@ k_project_bwd(int64_t n, CamDev cam, const float* __restrict__ means,
     for (int k = 0; k < K * 3; ++k) gshv[k] = 0.f;
     float gop = 0.f;
     if (valid) {
-      const float* G2 = g2d + i * kG2D;
-      const float4 ga = *reinterpret_cast<const float4*>(G2);
-      const float4 gb = *reinterpret_cast<const float4*>(G2 + 4);
-      const float4 gc = *reinterpret_cast<const float4*>(G2 + 8);
+      const float4* G2 = reinterpret_cast<const float4*>(g2d + i * kG2D);
+      const float4 ga = G2[0], gb = G2[1], gc = G2[2];
       const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x;
       gop = gb.y;
       const float grgb[3] = {gb.z, gb.w, gc.x};
@@ -291,24 +289,37 @@ k_project_bwd(int64_t n, CamDev cam, const float* __restrict__ means,
   }
 }
 
-__global__ void __launch_bounds__(256)
+// Sum of the per-block pose partials (stride 8 floats, 6 used) in a fixed order: thread t
+// takes blocks t, t + kPR, ... with two 16-byte loads each, then warp and block reductions.
+constexpr int kPR = 512;
+__global__ void __launch_bounds__(kPR)
 k_pose_reduce(const float* __restrict__ partials, int nblocks, float* __restrict__ g_pose6) {
-  // thread t sums a strided subset of blocks for each component; fixed order
-  __shared__ float s[6][256];
   float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int b = threadIdx.x; b < nblocks; b += 256)
-#pragma unroll
-    for (int c = 0; c < 6; ++c) acc[c] += partials[(int64_t)b * 8 + c];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) s[c][threadIdx.x] = acc[c];
-  __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h)
-#pragma unroll
-      for (int c = 0; c < 6; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + h];
-    __syncthreads();
+  const float4* p4 = reinterpret_cast<const float4*>(partials);
+#pragma unroll 4
+  for (int b = threadIdx.x; b < nblocks; b += kPR) {
+    const float4 u = p4[2 * b], v = p4[2 * b + 1];
+    acc[0] += u.x;
+    acc[1] += u.y;
+    acc[2] += u.z;
+    acc[3] += u.w;
+    acc[4] += v.x;
+    acc[5] += v.y;
   }
-  if (threadIdx.x < 6) g_pose6[threadIdx.x] = s[threadIdx.x][0];
+  __shared__ float s[kPR / 32][6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float x = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5][c] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float x = 0.f;
+    for (int w = 0; w < kPR / 32; ++w) x += s[w][threadIdx.x];
+    g_pose6[threadIdx.x] = x;
+  }
 }
 
 __global__ void k_l1_grad(const float* __restrict__ pred, const float* __restrict__ target,
@@ -343,13 +354,12 @@ void launch_project_bwd(const gs_scene& sc, const CamDev& cam, const GaussRec* r
     note_launch();
   }
   if (g_pose6) {
-    if (sc.n > 0)
-    {
-      k_pose_reduce<<<1, 256, 0, st>>>(pose_partials, nb, g_pose6);
+    if (sc.n > 0) {
+      k_pose_reduce<<<1, kPR, 0, st>>>(pose_partials, nb, g_pose6);
       note_launch();
-    }
-    else
+    } else {
       cudaMemsetAsync(g_pose6, 0, 6 * sizeof(float), st);
+    }
   }
 }
 

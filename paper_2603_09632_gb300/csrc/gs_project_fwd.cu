@@ -55,7 +55,8 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
           const float* __restrict__ quats, const float* __restrict__ opac,
           const float* __restrict__ sh, GaussRec* __restrict__ rec,
           uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ntiles,
-          uint2* __restrict__ rect, uint32_t* __restrict__ counters) {
+          uint2* __restrict__ rect, uint32_t* __restrict__ counters,
+          uint32_t* __restrict__ tile_count) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ __align__(16) float s_mu[kProjThreads * 3];
   __shared__ __align__(16) float s_sc[kProjThreads * 3];
@@ -70,6 +71,7 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
   __syncthreads();
   const int l = threadIdx.x;
   uint32_t cnt_v = 0, cnt_i = 0;
+  uint2 rc_l = make_uint2(0u, 0u);   // this lane's rectangle and tile count for the binning
   if (l < rows) {
     const int64_t i = row0 + l;
 
@@ -224,7 +226,10 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
     rect[i] = rc;
     cnt_v = valid ? 1u : 0u;
     cnt_i = nt;
+    rc_l = rc;
   }
+  // per-tile instance counts for the binning (the count step of the tile buckets)
+  if (tile_count) warp_count_tiles(cnt_i, rc_l, cam.TX, cam.TX * cam.TY, tile_count);
   // V and I for the workspace counters: warp sums, then one atomic per block
   __shared__ uint32_t s_cnt[2];
   if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0u;
@@ -245,14 +250,15 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
 }  // namespace
 
 void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32_t* depth_key,
-                    uint32_t* ntiles, uint2* rect, uint32_t* counters, cudaStream_t st) {
+                    uint32_t* ntiles, uint2* rect, uint32_t* counters, uint32_t* tile_count,
+                    cudaStream_t st) {
   if (sc.n <= 0) return;
   const int grid = (int)ceil_div(sc.n, kProjThreads);
   switch (sc.sh_degree) {
-    case 0: k_project<0><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
-    case 1: k_project<1><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
-    case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
-    default: k_project<3><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters); break;
+    case 0: k_project<0><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters, tile_count); break;
+    case 1: k_project<1><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters, tile_count); break;
+    case 2: k_project<2><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters, tile_count); break;
+    default: k_project<3><<<grid, kProjThreads, 0, st>>>(sc.n, cam, sc.means, sc.scales, sc.quats, sc.opacities, sc.sh, rec, depth_key, ntiles, rect, counters, tile_count); break;
   }
   note_launch();
 }

@@ -256,6 +256,7 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     }
     __syncthreads();   // shared memory and s_tile are reused by the next tile
   }
+  if (threadIdx.x == 0) queue_leave(tq, gridDim.x);
   if constexpr (LOSS) {
     {
       // one block reduction and three atomics per CTA for the whole launch

@@ -314,6 +314,7 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
       __syncwarp();
     }
   }
+  if ((threadIdx.x & 31) == 0) queue_leave(tq, gridDim.x * (blockDim.x >> 5));
   if constexpr (LOSS) {
     __shared__ double s_red[2][kWarps];
 #pragma unroll

@@ -5,7 +5,8 @@
 // holding tens to a few thousand instances each, so instead of global radix passes over
 // all instances (each pass a chain of block-to-block dependencies) the binning works in
 // tile buckets:
-//   1. count: every visible Gaussian adds 1 to each tile of its rectangle;
+//   1. count: every visible Gaussian adds 1 to each tile of its rectangle (done by the
+//      projection kernel, which has the rectangles in registers);
 //   2. scan: one block turns the counts into tile ranges [start, end) and a heavy-first
 //      tile order for the persistent raster kernels;
 //   3. scatter: every (Gaussian, tile) instance takes a slot in its tile's range
@@ -15,7 +16,7 @@
 //      skipped), then orders runs of equal depth by id, which makes the order the total
 //      (depth, id) order whatever order the scatter left.  Ranges longer than shared
 //      memory holds are sorted in chunks through global ping-pong buffers.
-// Steps 1 and 3 flatten the instances of a warp's 32 Gaussians and aggregate the atomic
+// Steps 1 and 3 (warp_tile_instances) flatten the instances of a warp's 32 Gaussians and aggregate the atomic
 // additions of equal tiles within a warp, so a Gaussian covering many tiles is spread over
 // the warp instead of serialising one thread.
 #include "gs_blend.cuh"
@@ -34,64 +35,25 @@ constexpr int kScanPer = 16;                    // tiles per scan thread per rou
 constexpr int kSeg = 2048;                      // range size sorted in shared memory
 constexpr int kSegRounds = kSeg / kThreads;     // elements per thread of a chunk
 
-// The instances of the 32 Gaussians of a warp, flattened: lane j of round r handles
-// instance r * 32 + j of the warp (Gaussians in lane order, tiles of a Gaussian in
-// row-major order).  f(gaussian, tile, valid) is called by every lane in every round.
+// The tile instances of a warp's 32 Gaussians (warp_tile_instances), read from the
+// projection's outputs; f(gaussian, tile) is called by every lane in every round.
 template <class F>
 __device__ __forceinline__ void for_warp_instances(int64_t n, const uint32_t* __restrict__ ntiles,
                                                    const uint2* __restrict__ rect, int TX, F f) {
-  const int lane = threadIdx.x & 31;
   const int64_t g0 = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31);
-  const int64_t g = g0 + lane;
+  const int64_t g = g0 + (threadIdx.x & 31);
   const uint32_t nt = g < n ? ntiles[g] : 0u;
-  uint32_t incl = nt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const uint32_t excl = incl - nt;
-  const uint32_t total = __shfl_sync(kFull, incl, 31);
   const uint2 rc = nt ? rect[g] : make_uint2(0u, 0u);
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t k = base + lane;
-    // owner: the last lane whose first instance is <= k (it has at least one instance)
-    int lo = 0, hi = 31;
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {
-      const int mid = (lo + hi + 1) >> 1;
-      const uint32_t e = __shfl_sync(kFull, excl, mid);
-      if (e <= k) lo = mid; else hi = mid - 1;
-    }
-    const uint32_t oe = __shfl_sync(kFull, excl, lo);
-    const uint32_t rx = __shfl_sync(kFull, rc.x, lo), ry = __shfl_sync(kFull, rc.y, lo);
-    uint32_t tile = 0xFFFFFFFFu;
-    if (k < total) {
-      const uint32_t x0 = rx & 0xFFFFu, y0 = rx >> 16, w = (ry & 0xFFFFu) - x0;
-      const uint32_t q = k - oe;
-      if (w) tile = (y0 + q / w) * (uint32_t)TX + x0 + q % w;
-    }
-    f(g0 + lo, tile);
-  }
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_bin_count(int64_t n, const uint32_t* __restrict__ ntiles, const uint2* __restrict__ rect, int TX,
-            int n_tiles, uint32_t* __restrict__ tile_count) {
-  for_warp_instances(n, ntiles, rect, TX, [&](int64_t, uint32_t tile) {
-    const bool ok = tile < (uint32_t)n_tiles;
-    const uint32_t peers = __match_any_sync(kFull, ok ? tile : 0xFFFFFFFFu);
-    if (ok && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0)
-      atomicAdd(&tile_count[tile], (uint32_t)__popc(peers));
-  });
+  warp_tile_instances(nt, rc, TX, [&](int lo, uint32_t tile) { f(g0 + lo, tile); });
 }
 
 // Exclusive scan of the tile counts -> ranges (clamped to the instance capacity), write
 // cursors, the overflow flag, and the heavy-first order (tiles bucketed by the bit length
 // of their count, longest first; order inside a bucket is arbitrary and results do not
-// depend on it).  One block.
+// depend on it).  The counts are zeroed after their last read, ready for the next
+// projection.  One block.
 __global__ void __launch_bounds__(kScanThreads)
-k_bin_scan(const uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
+k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
            uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, uint32_t* __restrict__ order,
            uint32_t* counters) {
   __shared__ uint32_t s_warp[kScanThreads / 32];
@@ -108,8 +70,13 @@ k_bin_scan(const uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
 #pragma unroll
     for (int j = 0; j < kScanPer; ++j) {
       c[j] = i0 + j < n_tiles ? tile_count[i0 + j] : 0u;
+      if (!order && i0 + j < n_tiles) tile_count[i0 + j] = 0u;   // last read without an order
       sum += c[j];
-      if (order && i0 + j < n_tiles) atomicAdd(&s_bcnt[__clz((int)c[j])], 1u);
+      if (order) {   // bucket histogram: one shared atomic per distinct bucket per warp
+        const int key = i0 + j < n_tiles ? __clz((int)c[j]) : 33;
+        const unsigned peers = __match_any_sync(kFull, key);
+        if (key < 33 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_bcnt[key], (uint32_t)__popc(peers));
+      }
     }
     uint32_t x = sum;
 #pragma unroll
@@ -155,8 +122,17 @@ k_bin_scan(const uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
     }
   }
   __syncthreads();
-  for (int i = t; i < n_tiles; i += kScanThreads)
-    order[atomicAdd(&s_bcur[__clz((int)tile_count[i])], 1u)] = (uint32_t)i;
+  for (int i0 = 0; i0 < n_tiles; i0 += kScanThreads) {   // warp-aggregated bucket slots
+    const int i = i0 + t;
+    const int key = i < n_tiles ? __clz((int)tile_count[i]) : 33;
+    if (i < n_tiles) tile_count[i] = 0u;   // last read
+    const unsigned peers = __match_any_sync(kFull, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (key < 33 && lane == leader) base = atomicAdd(&s_bcur[key], (uint32_t)__popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    if (i < n_tiles) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
 }
 
 // Every instance takes a slot in its tile's range (one atomic per distinct tile per warp
@@ -423,6 +399,7 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
     }
     __syncthreads();   // shared memory and s_tile are reused by the next tile
   }
+  if (threadIdx.x == 0) queue_leave(tq, gridDim.x);
 }
 
 // ---------------------------------------------------------------- statistics
@@ -489,12 +466,7 @@ k_inst_eff(const uint32_t* __restrict__ n_contrib, int TX, int W, int H, uint32_
 bool launch_bin(const BinArgs& b, cudaStream_t st) {
   const int T = b.n_tiles;
   if (T <= 0) return false;
-  cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * (size_t)T, st);
   const unsigned gb = (unsigned)max64(ceil_div(b.n, kThreads), 1);
-  if (b.n > 0) {
-    k_bin_count<<<gb, kThreads, 0, st>>>(b.n, b.ntiles, b.rect, b.TX, T, b.tile_count);
-    note_launch();
-  }
   uint32_t* order = T <= kMaxOrderedTiles ? b.order : nullptr;
   k_bin_scan<<<1, kScanThreads, 0, st>>>(b.tile_count, T, b.cap, b.ranges, b.cursor, order,
                                          b.counters);
@@ -505,8 +477,7 @@ bool launch_bin(const BinArgs& b, cudaStream_t st) {
     note_launch();
   }
   // per-tile sort: persistent blocks over the tiles, heaviest first
-  cudaMemsetAsync(b.queue, 0, sizeof(uint32_t), st);
-  const TileQueue tq{b.queue, order, T};
+  const TileQueue tq{b.queue, b.queue + 1, order, T};
   const int grid = persistent_grid(k_bin_sort, kThreads, 0, T);
   k_bin_sort<<<grid, kThreads, 0, st>>>(tq, b.ranges, b.key0, b.id0, b.key1, b.id1, b.tile_out);
   note_launch();
