@@ -147,10 +147,18 @@ KERNEL_SOURCES = {
 }
 
 
-def source_hash(stage):
+# the grid-sampled workloads run the grid kernels for their fwd / bwd_raster stages
+GRID_KERNEL_SOURCES = {"fwd": ["gs_raster_grid.cu", "gs_blend.cuh", "gs_internal.cuh"],
+                       "bwd_raster": ["gs_raster_grid.cu", "gs_blend.cuh", "gs_internal.cuh"]}
+
+
+def source_hash(stage, workload=""):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES[stage]:
+    files = KERNEL_SOURCES[stage]
+    if "grid" in workload and stage in GRID_KERNEL_SOURCES:
+        files = GRID_KERNEL_SOURCES[stage]
+    for f in files:
         with open(os.path.join(ROOT, "paper_2603_09632_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -164,7 +172,7 @@ def captured_traffic(stage, workload):
     with open(p) as f:
         d = json.load(f)
     e = d.get(workload, {}).get(stage)
-    if e and e.get("source_sha") == source_hash(stage):
+    if e and e.get("source_sha") == source_hash(stage, workload):
         return e["dram_bytes_per_launch"]
     return None
 
