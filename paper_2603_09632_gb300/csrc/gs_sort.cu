@@ -47,9 +47,15 @@ __device__ __forceinline__ void for_warp_instances(int64_t n, const uint32_t* __
   warp_tile_instances(nt, rc, TX, [&](int lo, uint32_t tile) { f(g0 + lo, tile); });
 }
 
+// Heavy-first order key of a tile with `count` instances: longest lists first, exact up to
+// 1023 entries (longer lists share the first bucket).
+__device__ __forceinline__ int order_key(uint32_t count) {
+  return kScanThreads - 1 - (int)min(count, (uint32_t)(kScanThreads - 1));
+}
+
 // Exclusive scan of the tile counts -> ranges (clamped to the instance capacity), write
-// cursors, the overflow flag, and the heavy-first order (tiles bucketed by the bit length
-// of their count, longest first; order inside a bucket is arbitrary and results do not
+// cursors, the overflow flag, and the heavy-first order (a counting sort of the tiles by
+// list length, longest first; the order inside a bucket is arbitrary and results do not
 // depend on it).  The counts are zeroed after their last read, ready for the next
 // projection.  One block.
 __global__ void __launch_bounds__(kScanThreads)
@@ -58,10 +64,10 @@ k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
            uint32_t* counters) {
   __shared__ uint32_t s_warp[kScanThreads / 32];
   __shared__ uint32_t s_carry;
-  __shared__ uint32_t s_bcnt[33], s_bcur[33];
+  __shared__ uint32_t s_b[kScanThreads];   // order buckets: tiles per list length
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t == 0) s_carry = 0;
-  if (t < 33) s_bcnt[t] = 0;
+  s_b[t] = 0;
   __syncthreads();
   for (int r0 = 0; r0 < n_tiles; r0 += kScanThreads * kScanPer) {
     const int i0 = r0 + t * kScanPer;
@@ -73,9 +79,9 @@ k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
       if (!order && i0 + j < n_tiles) tile_count[i0 + j] = 0u;   // last read without an order
       sum += c[j];
       if (order) {   // bucket histogram: one shared atomic per distinct bucket per warp
-        const int key = i0 + j < n_tiles ? __clz((int)c[j]) : 33;
+        const int key = i0 + j < n_tiles ? order_key(c[j]) : kScanThreads;
         const unsigned peers = __match_any_sync(kFull, key);
-        if (key < 33 && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_bcnt[key], (uint32_t)__popc(peers));
+        if (key < kScanThreads && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&s_b[key], (uint32_t)__popc(peers));
       }
     }
     uint32_t x = sum;
@@ -114,22 +120,37 @@ k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
   }
   if (t == 0 && (int64_t)s_carry > cap) atomicOr(&counters[kCntStatus], kErrInstOverflow);
   if (!order) return;
-  if (t == 0) {
-    uint32_t acc = 0;
-    for (int b = 0; b < 33; ++b) {
-      s_bcur[b] = acc;
-      acc += s_bcnt[b];
+  {   // exclusive scan of the order buckets, one per thread
+    const uint32_t v = s_b[t];
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
     }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = s_warp[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, w, o);
+        if (lane >= o) w += y;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    s_b[t] = (warp ? s_warp[warp - 1] : 0u) + x - v;
   }
   __syncthreads();
   for (int i0 = 0; i0 < n_tiles; i0 += kScanThreads) {   // warp-aggregated bucket slots
     const int i = i0 + t;
-    const int key = i < n_tiles ? __clz((int)tile_count[i]) : 33;
+    const int key = i < n_tiles ? order_key(tile_count[i]) : kScanThreads;
     if (i < n_tiles) tile_count[i] = 0u;   // last read
     const unsigned peers = __match_any_sync(kFull, key);
     const int leader = __ffs(peers) - 1;
     uint32_t base = 0;
-    if (key < 33 && lane == leader) base = atomicAdd(&s_bcur[key], (uint32_t)__popc(peers));
+    if (key < kScanThreads && lane == leader) base = atomicAdd(&s_b[key], (uint32_t)__popc(peers));
     base = __shfl_sync(kFull, base, leader);
     if (i < n_tiles) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
   }
