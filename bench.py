@@ -67,6 +67,28 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def rank_poses(rank, n_poses, count):
+    """Pose indices a rank renders: a walk over the trajectory offset by 37 poses per rank,
+    so the ranks of a weak-scaling run render different poses and exchange no data."""
+    return [(rank * 37 + k) % n_poses for k in range(count)]
+
+
+def max_over_ranks(ms, dist, device):
+    """Time of the whole job: the slowest rank's time (all_reduce MAX); ms itself at N = 1."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, units_per_step, ms):
+    """Whole-job throughput in millions of units per second: every rank processed
+    steps x units_per_step in at most ms milliseconds."""
+    return world * steps * units_per_step / (ms * 1e-3) / 1e6
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -383,7 +405,7 @@ def run_gpu(args):
                         stream)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
-    poses = [(rank * 37 + k) % len(gcams) for k in range(args.warmup + args.steps)]
+    poses = rank_poses(rank, len(gcams), args.warmup + args.steps)
     for k in range(args.warmup):
         step(gcams[poses[k]], gf)
         flush.fill_(float(k))
@@ -417,11 +439,8 @@ def run_gpu(args):
     L.gs_timing_enable(ws, False)
     status = L.gs_workspace_status(ws)
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * args.steps * P / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, dist, dev)
+    value = job_throughput(world, args.steps, P, ms)
 
     # algorithmic bytes per stage, averaged over the timed poses (untimed recount)
     sb_tot, sf_tot, pairs = {}, {}, [0, 0]
@@ -557,7 +576,7 @@ def run_grid(args):
     seg, table = dev_t(seg_np, torch.int32), dev_t(table_np)
     nsteps = args.warmup + args.steps
     offs = S.grid_offsets(nsteps, stride, seed=2 + rank)
-    poses = [(rank * 37 + k) % len(cams) for k in range(nsteps)]
+    poses = rank_poses(rank, len(cams), nsteps)
     gcams = [as_camera(cams[poses[k]], stride, *offs[k]) for k in range(nsteps)]
     Hs, Ws = grid_shape(gcams[0])
     P = Hs * Ws
@@ -614,11 +633,8 @@ def run_grid(args):
     L.gs_timing_enable(ws, False)
     status = L.gs_workspace_status(ws)
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * args.steps * P / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, dist, dev)
+    value = job_throughput(world, args.steps, P, ms)
     sb_tot, sf_tot, pairs = {}, {}, [0, 0]
     for k in range(args.steps):
         c = gcams[args.warmup + k]
@@ -762,7 +778,7 @@ def run_vq(args):
     nsteps = args.warmup + args.steps
     dec = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(nsteps)]
-    poses = [(rank * 37 + k) % len(gcams) for k in range(nsteps)]
+    poses = rank_poses(rank, len(gcams), nsteps)
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     for k in range(args.warmup):
         step(gcams[poses[k]], k)
@@ -789,13 +805,10 @@ def run_vq(args):
     if int(err.item()) != 0:
         raise RuntimeError("tensor-core decode reported a timed-out wait")
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     dec_ms = sum(dec[args.warmup + k][0].elapsed_time(dec[args.warmup + k][1])
                  for k in range(args.steps)) / args.steps
-    value = world * args.steps * P / (ms * 1e-3) / 1e6
+    value = job_throughput(world, args.steps, P, ms)
     peaks, src = load_peaks()
     alg_bytes = P * (Lw * 4 + Dc * 4 + 4)
     alg_flops = 2.0 * P * Lw * Dc + P * Dc * 2 * 6
