@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -13,6 +14,33 @@ using namespace gs;
 namespace gs {
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int resident_ctas(const void* kern, int threads, size_t smem) {
+  struct Entry {
+    const void* kern;
+    int threads;
+    size_t smem;
+    int dev;
+    int ctas;
+  };
+  static std::mutex mu;   // the serving threads launch concurrently
+  static std::vector<Entry> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& e : cache)
+      if (e.kern == kern && e.threads == threads && e.smem == smem && e.dev == dev) return e.ctas;
+  }
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (smem > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  const int ctas = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  std::lock_guard<std::mutex> lk(mu);
+  cache.push_back(Entry{kern, threads, smem, dev, ctas});
+  return ctas;
+}
 }  // namespace gs
 
 namespace {

@@ -168,17 +168,18 @@ __device__ __forceinline__ void queue_leave(const TileQueue& tq, unsigned partic
   }
 }
 
+// Resident CTAs of a kernel on the current device (SMs x CTAs per SM), computed once per
+// (kernel, block size, dynamic shared memory, device) and cached: the attribute and
+// occupancy queries cost host time on every launch otherwise.  Sets the kernel's dynamic
+// shared-memory limit to `smem` on first use: static plus dynamic shared memory above 48 KB
+// needs it even when the dynamic part alone is below 48 KB.
+int resident_ctas(const void* kern, int threads, size_t smem);
+
 // Grid of a persistent kernel: as many CTAs as fit on the device at once (never more than
-// n_items).  Sets the kernel's dynamic shared-memory limit to `smem`: static plus dynamic
-// shared memory above 48 KB needs it even when the dynamic part alone is below 48 KB.
+// n_items).
 template <class Kernel>
 inline int persistent_grid(Kernel kern, int threads, size_t smem, int n_items) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (smem > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-  const int g = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  const int g = resident_ctas(reinterpret_cast<const void*>(kern), threads, smem);
   return n_items < g ? (n_items > 0 ? n_items : 1) : g;
 }
 
