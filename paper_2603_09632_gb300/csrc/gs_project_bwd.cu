@@ -54,6 +54,29 @@ __device__ __forceinline__ void sh_eval(float x, float y, float z, float* Y, flo
   dY[15] = make_float3(kC3a * (3.f * x * x - 3.f * y * y), -6.f * kC3a * x * y, 0.f);
 }
 
+// Rows of a block's outputs staged in shared memory with an odd row stride P (no bank
+// conflicts when each thread stores its own row), then written to the row-major global
+// array (NF floats per row) with coalesced 16-byte stores when the destination allows.
+template <int NF>
+struct RowStage {
+  static constexpr int P = NF | 1;
+  float v[kPB * P];
+  __device__ __forceinline__ float* row(int r) { return v + r * P; }
+  __device__ __forceinline__ float at(int e) const { return v[(e / NF) * P + e % NF]; }
+  __device__ __forceinline__ void write(float* __restrict__ dst, int64_t row0, int rows) const {
+    float* base = dst + row0 * NF;
+    const int total = rows * NF;
+    int e0 = 0;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) == 0) {
+      const int nv = total >> 2;
+      for (int q = threadIdx.x; q < nv; q += kPB)
+        reinterpret_cast<float4*>(base)[q] = make_float4(at(4 * q), at(4 * q + 1), at(4 * q + 2), at(4 * q + 3));
+      e0 = nv << 2;
+    }
+    for (int e = e0 + threadIdx.x; e < total; e += kPB) base[e] = at(e);
+  }
+};
+
 template <int DEG>
 __global__ void __launch_bounds__(kPB)
 k_project_bwd(int64_t n, CamDev cam, const float* __restrict__ means,
@@ -64,7 +87,12 @@ k_project_bwd(int64_t n, CamDev cam, const float* __restrict__ means,
               float* __restrict__ g_quats, float* __restrict__ g_opac, float* __restrict__ g_sh,
               float* __restrict__ pose_partials) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  const int64_t i = (int64_t)blockIdx.x * kPB + threadIdx.x;
+  const int64_t row0 = (int64_t)blockIdx.x * kPB;
+  const int64_t i = row0 + threadIdx.x;
+  const int rows = (int)min64(kPB, n - row0);
+  // SH gradient rows (3K floats per Gaussian, K > 1) are written coalesced by the whole
+  // block through shared memory; the short rows are stored directly
+  __shared__ RowStage<K == 1 ? 1 : K * 3> s_gsh;
   float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (i < n) {
     const bool valid = ntiles[i] > 0;
@@ -269,8 +297,20 @@ k_project_bwd(int64_t n, CamDev cam, const float* __restrict__ means,
       *reinterpret_cast<float4*>(g_quats + 4 * i) = make_float4(gq[0], gq[1], gq[2], gq[3]);
     if (g_opac) g_opac[i] = gop;
     if (g_sh) {
+      if constexpr (K == 1) {
 #pragma unroll
-      for (int k = 0; k < K * 3; ++k) g_sh[i * (K * 3) + k] = gshv[k];
+        for (int k = 0; k < 3; ++k) g_sh[i * 3 + k] = gshv[k];
+      } else {
+        float* rh = s_gsh.row(threadIdx.x);
+#pragma unroll
+        for (int k = 0; k < K * 3; ++k) rh[k] = gshv[k];
+      }
+    }
+  }
+  if constexpr (K > 1) {
+    if (g_sh) {   // uniform
+      __syncthreads();
+      s_gsh.write(g_sh, row0, rows);
     }
   }
   // block reduction of the pose terms

@@ -61,13 +61,15 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
   __shared__ __align__(16) float s_mu[kProjThreads * 3];
   __shared__ __align__(16) float s_sc[kProjThreads * 3];
   __shared__ __align__(16) float s_q[kProjThreads * 4];
-  __shared__ __align__(16) float s_sh[kProjThreads * K * 3];
+  // SH degree 0 is staged with the geometry; higher degrees (up to 192 B per Gaussian) are
+  // read from global memory by the visible Gaussians only
+  __shared__ __align__(16) float s_sh[K == 1 ? kProjThreads * 3 : 1];
   const int64_t row0 = (int64_t)blockIdx.x * kProjThreads;
   const int rows = (int)min64(kProjThreads, n - row0);
   stage_rows(means, row0, rows, 3, s_mu);
   stage_rows(scales, row0, rows, 3, s_sc);
   stage_rows(quats, row0, rows, 4, s_q);
-  stage_rows(sh, row0, rows, K * 3, s_sh);
+  if (K == 1) stage_rows(sh, row0, rows, 3, s_sh);
   __syncthreads();
   const int l = threadIdx.x;
   uint32_t cnt_v = 0, cnt_i = 0;
@@ -206,13 +208,13 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
         Y[14] = kC3e * dz * (dx * dx - dy * dy);
         Y[15] = kC3a * dx * (dx * dx - 3.f * dy * dy);
       }
-      const float* shl = s_sh + l * K * 3;
+      const float* shl = K == 1 ? s_sh + l * 3 : sh + i * (K * 3);
       float col[3];
   #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         float acc = 0.f;
   #pragma unroll
-        for (int k = 0; k < K; ++k) acc += shl[k * 3 + ch] * Y[k];
+        for (int k = 0; k < K; ++k) acc += (K == 1 ? shl[k * 3 + ch] : __ldg(shl + k * 3 + ch)) * Y[k];
         acc += 0.5f;
         col[ch] = acc > 0.f ? acc : 0.f;
       }
