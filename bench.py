@@ -457,6 +457,14 @@ def run_gpu(args):
         for name, f in stage_flops(st, D, K).items():
             sf_tot[name] = sf_tot.get(name, 0.0) + f
     roofline = build_roofline(stage, sb_tot, sf_tot, pairs, args.steps, args.workload)
+    # device memory of the step: the scene, images and gradients (torch; the L2 flush buffer
+    # excluded) and the library workspace's high-water mark
+    torch_peak = int(torch.cuda.max_memory_allocated(dev)) - flush.numel() * flush.element_size()
+    ws_bytes = L.gs_workspace_bytes(ws)
+    memory = {"torch_peak_bytes": torch_peak, "workspace_bytes": ws_bytes,
+              "total_bytes": torch_peak + ws_bytes,
+              "what": "peak device memory of the timed steps: torch allocations (scene, images, "
+                      "gradients; not the L2 flush buffer) + the library workspace"}
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, L, scene, gcams, poses, dev, stream, ws, K, D, H, W)
@@ -470,7 +478,7 @@ def run_gpu(args):
                    "pixels_per_step": P, "poses": len(gcams), "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
-        "device_status": L.status_string(status),
+        "memory": memory, "device_status": L.status_string(status),
     }
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args, scene_np, cams, target_budget_s=args.cpu_budget)

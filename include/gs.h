@@ -122,6 +122,11 @@ gs_status gs_workspace_reserve(gs_workspace* ws, int64_t n_gauss, int64_t n_inst
  * GS_ERR_DEVICE (e.g. the instance count exceeded the reserved capacity). */
 gs_status gs_workspace_status(gs_workspace* ws, void* stream);
 
+/* Device memory held by the workspace, in bytes, into *bytes (host pointer): the sum of
+ * its buffers' capacities, i.e. its high-water mark, since buffers only grow.  No device
+ * work.  Errors: GS_ERR_ARG (null argument). */
+gs_status gs_workspace_bytes(gs_workspace* ws, int64_t* bytes);
+
 /* a1. EWA projection and SH colour, one thread per Gaussian (App. A, Sigma and Sigma';
  * SH colour along the view direction from the camera centre).  Writes, into the
  * workspace, each Gaussian's 2D mean, conic (inverse of Sigma' + 0.3 I), depth, colour,

@@ -80,6 +80,7 @@ def _load():
         "gs_workspace_destroy": ([P], None),
         "gs_workspace_reserve": ([P, i64, i64, i64], st),
         "gs_workspace_status": ([P, P], st),
+        "gs_workspace_bytes": ([P, C.POINTER(C.c_int64)], st),
         "gs_project": ([P, P, P, P], st),
         "gs_bin_tiles": ([P, P, P], st),
         "gs_render_fwd": ([P, P, P, P, P, P, P, P], st),
@@ -231,6 +232,13 @@ def gs_workspace_reserve(ws, n_gauss, n_instances, n_pixels):
 
 def gs_workspace_status(ws, stream=None):
     return lib.gs_workspace_status(ws.h, _stream(stream))
+
+
+def gs_workspace_bytes(ws) -> int:
+    """Device memory held by the workspace (its high-water mark), in bytes."""
+    b = C.c_int64()
+    _check(lib.gs_workspace_bytes(ws.h, C.byref(b)), "gs_workspace_bytes")
+    return int(b.value)
 
 
 def gs_project(scene, cam, ws, stream=None):

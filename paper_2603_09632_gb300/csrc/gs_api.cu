@@ -335,6 +335,19 @@ gs_status gs_workspace_status(gs_workspace* ws, void* stream) {
   return GS_OK;
 }
 
+gs_status gs_workspace_bytes(gs_workspace* ws, int64_t* bytes) {
+  if (!ws || !bytes) return GS_ERR_ARG;
+  size_t b = 0;
+  auto add = [&b](const auto& buf) { b += buf.cap * sizeof(*buf.p); };
+  add(ws->rec); add(ws->depth_key); add(ws->ntiles); add(ws->rect); add(ws->item_max);
+  add(ws->g2d); add(ws->pose_partials);
+  add(ws->inst_key); add(ws->inst_id); add(ws->inst_key2); add(ws->inst_id2); add(ws->inst_tile);
+  add(ws->ranges); add(ws->tile_order); add(ws->queue); add(ws->tile_count); add(ws->tile_cursor);
+  add(ws->T_final); add(ws->n_contrib); add(ws->counters); add(ws->stats64);
+  *bytes = (int64_t)b;
+  return GS_OK;
+}
+
 gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws, void* stream) {
   if (!ws) return GS_ERR_ARG;
   gs_status s = check_scene(scene);

@@ -53,6 +53,8 @@ def test_null_arguments_rejected(libgs):
     assert libgs.gs_project(None, None, None, None) == 1          # GS_ERR_ARG
     assert libgs.gs_bin_tiles(None, None, None) == 1
     assert libgs.gs_workspace_create(None, 0) == 1
+    libgs.gs_workspace_bytes.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert libgs.gs_workspace_bytes(None, None) == 1
 
 
 def test_binding_names_match_header():
