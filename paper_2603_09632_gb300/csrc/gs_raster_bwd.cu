@@ -220,6 +220,7 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     if (t == 0) s_maxn = 0;
     __syncthreads();
     if (nc > 0) atomicMax(&s_maxn, (uint32_t)nc);
+    const int warp_nc = (int)__reduce_max_sync(0xffffffffu, (unsigned)nc);   // this strip's
     __syncthreads();
     const int maxn = (int)s_maxn;
     if (rg.x + (uint32_t)maxn <= rg.y) {          // always, for consistent inputs
@@ -270,6 +271,9 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
           hit = box_min_sigma(wbx0, wby0, wbx0 + (float)(kStripW - 1), wby0 + (float)(kStripH - 1),
                               q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
         }
+        // ... and that some pixel of the strip still blends (list position below the strip's
+        // largest last-contributor count)
+        if (lane < bc) hit = hit && s_orig[jb0 + lane] < warp_nc;
         const unsigned live = __ballot_sync(0xffffffffu, hit);
         if (lane == 0) s_live[t >> 5] = live;   // phase 2 skips (Gaussian, strip) pairs not live
 
