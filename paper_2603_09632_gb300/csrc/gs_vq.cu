@@ -26,7 +26,7 @@ constexpr int kGroups = kVT / 128;   // threads per row = column groups of the e
 constexpr int kRows = 128;           // tile rows (pixels) = TMEM lanes = MMA M
 constexpr int kMaxL = 64;            // K
 constexpr int kMaxDc = 512;          // N (two MMAs of N = 256)
-constexpr int kMaxText = 8;
+constexpr int kMaxText = 8;                 // prompt + negatives (read as two float4 per codeword)
 constexpr uint32_t kWaitLimit = 1u << 20;   // try_wait polls (each may suspend briefly)
 constexpr int kMaxResident = 2048 / kVT;   // CTAs per SM allowed by the thread count
 
@@ -130,13 +130,14 @@ struct DecodeSmem {
     et = b + (uint32_t)Dc * L * 4;                      // E t_j  [L][kMaxText]
     dot = et + (uint32_t)kMaxL * kMaxText * 4;          // [2 buffers][groups][kMaxText][128]
     text = dot;                                         // prompt embeddings [kMaxText][Dc]
-    nrm = dot + 2u * kGroups * kMaxText * kRows * 4;    // [groups][128]
-    bar = nrm + (uint32_t)kGroups * kRows * 4;
+    nrm = dot + 2u * kGroups * kMaxText * kRows * 4;    // [2 buffers][groups][128]
+    bar = nrm + 2u * kGroups * kRows * 4;
     tmem = bar + 8;
     total = tmem + 8;
   }
 };
 static_assert(2 * kGroups * kMaxText * kRows >= kMaxText * kMaxDc, "text staging must fit");
+static_assert(kMaxText == 8, "E t_j rows are read as two float4");
 
 // One 128-pixel tile per iteration.  The four threads t = r + 128 g (g = 0..3) share row r
 // (pixel p = tile * 128 + r): each loads a quarter of the row's L weights (prefetched during
@@ -218,14 +219,24 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
     for (int k = 0; k < kMaxL / kGroups; ++k)
       wv[k] = (k < LH && live) ? __ldg(a.wmap + (int64_t)(h * LH + k) * a.P + p) : 0.f;
 #pragma unroll
-    for (int j = 0; j < kMaxText; ++j) {
-      float d = 0.f;
-      if (j < nt) {
+    for (int j = 0; j < kMaxText; ++j) dp[j] = 0.f;
+    if (nt > 0) {
+      // E t_j of codeword k: two 16-byte loads for the kMaxText = 8 prompts
+      const float4* et4 = reinterpret_cast<const float4*>(sEt);
 #pragma unroll
-        for (int k = 0; k < kMaxL / kGroups; ++k)
-          if (k < LH) d = fmaf(wv[k], sEt[(h * LH + k) * kMaxText + j], d);
+      for (int k = 0; k < kMaxL / kGroups; ++k) {
+        if (k < LH) {
+          const float4 e0 = et4[(h * LH + k) * 2], e1 = et4[(h * LH + k) * 2 + 1];
+          dp[0] = fmaf(wv[k], e0.x, dp[0]);
+          dp[1] = fmaf(wv[k], e0.y, dp[1]);
+          dp[2] = fmaf(wv[k], e0.z, dp[2]);
+          dp[3] = fmaf(wv[k], e0.w, dp[3]);
+          dp[4] = fmaf(wv[k], e1.x, dp[4]);
+          dp[5] = fmaf(wv[k], e1.y, dp[5]);
+          dp[6] = fmaf(wv[k], e1.z, dp[6]);
+          dp[7] = fmaf(wv[k], e1.w, dp[7]);
+        }
       }
-      dp[j] = d;
     }
   };
   auto store_rows = [&](int buf) {
@@ -256,6 +267,29 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
       if (j < nt) sDot[((buf * kGroups + h) * kMaxText + j) * kRows + r] = dp[j];
   };
 
+  // relevance of a finished tile from its partial norms and prompt dots (buffer it & 1);
+  // run one tile later, while the next tile's MMAs and the other warps' stores proceed
+  auto finish_rel = [&](int64_t tl, int itl) {
+    const int64_t pr = tl * kRows + r;
+    if (pr >= a.P) return;
+    const int buf = itl & 1;
+    float nrm = 0.f;
+    for (int g = 0; g < kGroups; ++g) nrm += sNrm[(buf * kGroups + g) * kRows + r];
+    const float inv = 1.f / (sqrtf(nrm) + a.eps);
+    float d[kMaxText];
+#pragma unroll
+    for (int j = 0; j < kMaxText; ++j) {
+      d[j] = 0.f;
+      if (j < nt)
+        for (int g = 0; g < kGroups; ++g) d[j] += sDot[((buf * kGroups + g) * kMaxText + j) * kRows + r];
+    }
+    float best = 0.f;
+#pragma unroll
+    for (int j = 1; j < kMaxText; ++j)
+      if (j < nt) best = fmaxf(best, 1.f / (1.f + __expf(a.tau * (d[j] - d[0]) * inv)));
+    a.rel[pr] = best;
+  };
+
   int64_t tile = blockIdx.x;
   if (tile < n_tiles) {
     load_rows(tile);
@@ -279,9 +313,11 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
       }
       mma_commit(bar);
     }
-    // prefetch the next tile's weights while the tensor cores run
+    // prefetch the next tile's weights and finish the previous tile's relevance while the
+    // tensor cores run
     const int64_t next = tile + gridDim.x;
     if (next < n_tiles) load_rows(next);
+    if (want_rel && h == 0 && it > 0) finish_rel(tile - gridDim.x, it - 1);
     const bool ok = mbar_wait(bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {   // every thread takes the same branch
@@ -317,30 +353,10 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
         }
       }
     }
-    if (want_rel) sNrm[h * kRows + 32 * (warp & 3) + lane] = (n4[0] + n4[1]) + (n4[2] + n4[3]);
+    if (want_rel)
+      sNrm[((it & 1) * kGroups + h) * kRows + 32 * (warp & 3) + lane] = (n4[0] + n4[1]) + (n4[2] + n4[3]);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();   // MMA done and TMEM read: the A tile and partial norms are free
-    if (want_rel && h == 0) {
-      const int64_t pr = tile * kRows + r;
-      if (pr < a.P) {
-        const int buf = it & 1;
-        float nrm = 0.f;
-        for (int g = 0; g < kGroups; ++g) nrm += sNrm[g * kRows + r];
-        const float inv = 1.f / (sqrtf(nrm) + a.eps);
-        float d[kMaxText];
-#pragma unroll
-        for (int j = 0; j < kMaxText; ++j) {
-          d[j] = 0.f;
-          if (j < nt)
-            for (int g = 0; g < kGroups; ++g) d[j] += sDot[((buf * kGroups + g) * kMaxText + j) * kRows + r];
-        }
-        float best = 0.f;
-#pragma unroll
-        for (int j = 1; j < kMaxText; ++j)
-          if (j < nt) best = fmaxf(best, 1.f / (1.f + __expf(a.tau * (d[j] - d[0]) * inv)));
-        a.rel[pr] = best;
-      }
-    }
+    __syncthreads();   // MMA done, TMEM read, previous relevance done: A and the other buffers free
     if (next < n_tiles) store_rows((it + 1) & 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -349,6 +365,10 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
   if (failed) {
     if (t == 0 && a.err) atomicExch(a.err, 1);
     mbar_wait(bar, phase ^ 1u);   // bounded: let this CTA's own MMAs drain before freeing TMEM
+  } else if (want_rel && h == 0 && blockIdx.x < n_tiles) {
+    // the last tile's relevance (its partials were published by the loop's last barrier)
+    const int64_t last = blockIdx.x + ((n_tiles - 1 - blockIdx.x) / gridDim.x) * gridDim.x;
+    finish_rel(last, (int)((last - blockIdx.x) / gridDim.x));
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
