@@ -639,6 +639,7 @@ gs_status gs_get_projection(gs_workspace* ws, float* mean2d, float* conic, float
   }
   GS_TRY(cudaStreamSynchronize(st));
   for (int64_t i = 0; i < n; ++i) {
+    if (rc[i].x == 0u && rc[i].y == 0u) rec[i] = GaussRec{};   // culled: no record was written
     const GaussRec& r = rec[i];
     if (mean2d) { mean2d[2 * i] = r.r0.x; mean2d[2 * i + 1] = r.r0.y; }
     if (conic) { conic[3 * i] = r.r0.z; conic[3 * i + 1] = r.r0.w; conic[3 * i + 2] = r.r1.x; }

@@ -222,8 +222,10 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
       g.r1 = make_float4(a / det, __ldg(opac + i), z, 0.f);
       g.r2 = make_float4(col[0], col[1], col[2], 0.f);
     }
-    rec[i] = g;
-    depth_key[i] = valid ? __float_as_uint(z) : 0xFFFFFFFFu;
+    if (valid) {   // records and keys are read only for Gaussians with tiles
+      rec[i] = g;
+      depth_key[i] = __float_as_uint(z);
+    }
     ntiles[i] = nt;
     rect[i] = rc;
     cnt_v = valid ? 1u : 0u;
