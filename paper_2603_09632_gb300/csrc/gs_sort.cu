@@ -368,12 +368,19 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += kThreads) atomicAdd(&s_cnt[(ka[i] >> (8 * p)) & 0xFFu], 1u);
         __syncthreads();
-        if (threadIdx.x == 0) {
-          uint32_t acc = 0;
-          for (int d = 0; d < kRadix; ++d) {
-            s_run[d] = acc;
-            acc += s_cnt[d];
+        {   // exclusive scan of the 256 digit counts, one per thread
+          const uint32_t c = s_cnt[threadIdx.x];
+          uint32_t x = c;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
           }
+          if (lane == 31) s_warp[warp] = x;
+          __syncthreads();
+          uint32_t before = 0;
+          for (int w = 0; w < warp; ++w) before += s_warp[w];
+          s_run[threadIdx.x] = before + x - c;
         }
         __syncthreads();
         for (int c0 = 0; c0 < n; c0 += kSeg) {
