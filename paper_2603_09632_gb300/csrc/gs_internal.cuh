@@ -110,41 +110,56 @@ struct TileQueue {
   int n_tiles;
 };
 
-// The tile instances of the 32 Gaussians of a warp, flattened: lane j of round r handles
-// instance r * 32 + j of the warp (Gaussians in lane order, tiles of a Gaussian in
-// row-major order of its rectangle).  nt and rc are the calling lane's tile count and
-// packed rectangle (x0 | y0 << 16, x1 | y1 << 16); f(owner_lane, tile) is called by every
-// lane in every round, with tile = 0xFFFFFFFF for lanes past the last instance.
-template <class F>
-__device__ __forceinline__ void warp_tile_instances(uint32_t nt, uint2 rc, int TX, F f) {
-  const unsigned full = 0xffffffffu;
+// The tile instances of the 32 Gaussians of a warp, flattened: instance k of the warp
+// (Gaussians in lane order, tiles of a Gaussian in row-major order of its rectangle).
+// warp_instances_begin takes the calling lane's tile count nt and packed rectangle rc
+// (x0 | y0 << 16, x1 | y1 << 16); warp_instance_tile returns the tile of instance k
+// (0xFFFFFFFF for k >= total) and its owner lane.  Every lane of the warp must call both.
+struct WarpInstances {
+  uint32_t excl, total;
+  uint2 rc;
+};
+__device__ __forceinline__ WarpInstances warp_instances_begin(uint32_t nt, uint2 rc) {
   const int lane = threadIdx.x & 31;
   uint32_t incl = nt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(full, incl, o);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += y;
   }
-  const uint32_t excl = incl - nt;
-  const uint32_t total = __shfl_sync(full, incl, 31);
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t k = base + lane;
-    // owner: the last lane whose first instance is <= k (it has at least one instance)
-    int lo = 0, hi = 31;
+  return WarpInstances{incl - nt, __shfl_sync(0xffffffffu, incl, 31), rc};
+}
+__device__ __forceinline__ uint32_t warp_instance_tile(const WarpInstances& wi, uint32_t k, int TX,
+                                                       int* owner) {
+  const unsigned full = 0xffffffffu;
+  // owner: the last lane whose first instance is <= k (it has at least one instance)
+  int lo = 0, hi = 31;
 #pragma unroll
-    for (int it = 0; it < 5; ++it) {
-      const int mid = (lo + hi + 1) >> 1;
-      const uint32_t e = __shfl_sync(full, excl, mid);
-      if (e <= k) lo = mid; else hi = mid - 1;
-    }
-    const uint32_t oe = __shfl_sync(full, excl, lo);
-    const uint32_t rx = __shfl_sync(full, rc.x, lo), ry = __shfl_sync(full, rc.y, lo);
-    uint32_t tile = 0xFFFFFFFFu;
-    if (k < total) {
-      const uint32_t x0 = rx & 0xFFFFu, y0 = rx >> 16, w = (ry & 0xFFFFu) - x0;
-      const uint32_t q = k - oe;
-      if (w) tile = (y0 + q / w) * (uint32_t)TX + x0 + q % w;
-    }
+  for (int it = 0; it < 5; ++it) {
+    const int mid = (lo + hi + 1) >> 1;
+    const uint32_t e = __shfl_sync(full, wi.excl, mid);
+    if (e <= k) lo = mid; else hi = mid - 1;
+  }
+  const uint32_t oe = __shfl_sync(full, wi.excl, lo);
+  const uint32_t rx = __shfl_sync(full, wi.rc.x, lo), ry = __shfl_sync(full, wi.rc.y, lo);
+  uint32_t tile = 0xFFFFFFFFu;
+  if (k < wi.total) {
+    const uint32_t x0 = rx & 0xFFFFu, y0 = rx >> 16, w = (ry & 0xFFFFu) - x0;
+    const uint32_t q = k - oe;
+    if (w) tile = (y0 + q / w) * (uint32_t)TX + x0 + q % w;
+  }
+  *owner = lo;
+  return tile;
+}
+
+// Calls f(owner_lane, tile) for the warp's instances, 32 per round (lane j takes instance
+// round * 32 + j; tile = 0xFFFFFFFF past the last); every lane calls it in every round.
+template <class F>
+__device__ __forceinline__ void warp_tile_instances(uint32_t nt, uint2 rc, int TX, F f) {
+  const WarpInstances wi = warp_instances_begin(nt, rc);
+  for (uint32_t base = 0; base < wi.total; base += 32) {
+    int lo;
+    const uint32_t tile = warp_instance_tile(wi, base + (threadIdx.x & 31), TX, &lo);
     f(lo, tile);
   }
 }

@@ -35,18 +35,6 @@ constexpr int kScanPer = 16;                    // tiles per scan thread per rou
 constexpr int kSeg = 2048;                      // range size sorted in shared memory
 constexpr int kSegRounds = kSeg / kThreads;     // elements per thread of a chunk
 
-// The tile instances of a warp's 32 Gaussians (warp_tile_instances), read from the
-// projection's outputs; f(gaussian, tile) is called by every lane in every round.
-template <class F>
-__device__ __forceinline__ void for_warp_instances(int64_t n, const uint32_t* __restrict__ ntiles,
-                                                   const uint2* __restrict__ rect, int TX, F f) {
-  const int64_t g0 = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31);
-  const int64_t g = g0 + (threadIdx.x & 31);
-  const uint32_t nt = g < n ? ntiles[g] : 0u;
-  const uint2 rc = nt ? rect[g] : make_uint2(0u, 0u);
-  warp_tile_instances(nt, rc, TX, [&](int lo, uint32_t tile) { f(g0 + lo, tile); });
-}
-
 // Heavy-first order key of a tile with `count` instances: longest lists first, exact up to
 // 1023 entries (longer lists share the first bucket).
 __device__ __forceinline__ int order_key(uint32_t count) {
@@ -157,29 +145,51 @@ k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
 }
 
 // Every instance takes a slot in its tile's range (one atomic per distinct tile per warp
-// round) and stores the Gaussian's depth key and id.  Slots at or beyond the capacity are
-// not written.
+// round) and stores the Gaussian's depth key and id.  The slot atomics of up to kScatterR
+// rounds are issued before their stores, so their latencies overlap.  Slots at or beyond
+// the capacity are not written.
+constexpr int kScatterR = 4;
 __global__ void __launch_bounds__(kThreads)
 k_bin_scatter(int64_t n, const uint32_t* __restrict__ ntiles, const uint2* __restrict__ rect,
               const uint32_t* __restrict__ depth_key, int TX, int n_tiles, int64_t cap,
               uint32_t* __restrict__ cursor, uint32_t* __restrict__ inst_key,
               uint32_t* __restrict__ inst_id) {
-  for_warp_instances(n, ntiles, rect, TX, [&](int64_t g, uint32_t tile) {
-    const int lane = threadIdx.x & 31;
-    const bool ok = tile < (uint32_t)n_tiles;
-    const uint32_t peers = __match_any_sync(kFull, ok ? tile : 0xFFFFFFFFu);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (ok && lane == leader) base = atomicAdd(&cursor[tile], (uint32_t)__popc(peers));
-    base = __shfl_sync(kFull, base, leader);
-    if (ok) {
-      const uint32_t pos = base + __popc(peers & ((1u << lane) - 1u));
-      if ((int64_t)pos < cap) {
-        inst_key[pos] = depth_key[g];
-        inst_id[pos] = (uint32_t)g;
+  const int lane = threadIdx.x & 31;
+  const int64_t g0 = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31);
+  const int64_t gl = g0 + lane;
+  const uint32_t nt = gl < n ? ntiles[gl] : 0u;
+  const WarpInstances wi = warp_instances_begin(nt, nt ? rect[gl] : make_uint2(0u, 0u));
+  for (uint32_t b0 = 0; b0 < wi.total; b0 += 32 * kScatterR) {
+    uint32_t tile[kScatterR], peers[kScatterR], base[kScatterR];
+    int owner[kScatterR];
+#pragma unroll
+    for (int r = 0; r < kScatterR; ++r) {
+      tile[r] = 0xFFFFFFFFu;
+      peers[r] = 0u;
+      base[r] = 0u;
+      owner[r] = 0;
+      if (b0 + 32u * r < wi.total) {   // uniform over the warp
+        tile[r] = warp_instance_tile(wi, b0 + 32u * r + lane, TX, &owner[r]);
+        const bool ok = tile[r] < (uint32_t)n_tiles;
+        peers[r] = __match_any_sync(kFull, ok ? tile[r] : 0xFFFFFFFFu);
+        if (ok && lane == __ffs(peers[r]) - 1) base[r] = atomicAdd(&cursor[tile[r]], (uint32_t)__popc(peers[r]));
       }
     }
-  });
+#pragma unroll
+    for (int r = 0; r < kScatterR; ++r) {
+      if (b0 + 32u * r < wi.total) {
+        const uint32_t bs = __shfl_sync(kFull, base[r], __ffs(peers[r]) - 1);
+        if (tile[r] < (uint32_t)n_tiles) {
+          const uint32_t pos = bs + __popc(peers[r] & ((1u << lane) - 1u));
+          if ((int64_t)pos < cap) {
+            const int64_t g = g0 + owner[r];
+            inst_key[pos] = depth_key[g];
+            inst_id[pos] = (uint32_t)g;
+          }
+        }
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------- per-tile radix sort
