@@ -113,7 +113,8 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
     float acc[DP > 0 ? DP : 1];
 #pragma unroll
     for (int c = 0; c < (DP > 0 ? DP : 1); ++c) acc[c] = 0.f;
-    int last = 0;
+    int last = 0;     // 1 + list position of the last blended entry
+    int lastj = -1;   // its batch slot, resolved to a list position once per batch
     bool done = !inside;
 
     for (int b0 = start; b0 < end; b0 += kB) {
@@ -170,7 +171,7 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
               } else {
                 w = __fmul_rn(a, T);
                 T = Tn;
-                last = s_orig[j] + 1;
+                lastj = j;
               }
             }
           }
@@ -193,9 +194,9 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             }
           }
         }
-        if (__all_sync(0xffffffffu, done)) live = 0u;
       }
       }
+      if (lastj >= 0) { last = s_orig[lastj] + 1; lastj = -1; }
     }
     if (inside) {
       const int64_t HW = (int64_t)cam.W * cam.H;

@@ -208,7 +208,8 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
     float acc[DP > 0 ? DP : 1];
 #pragma unroll
     for (int c = 0; c < (DP > 0 ? DP : 1); ++c) acc[c] = 0.f;
-    int last = 0;
+    int last = 0;     // 1 + list position of the last blended entry
+    int lastk = -1;   // its batch slot, resolved once per batch
     bool done = !it.in_img;
 
     for (int b0 = start; b0 < end; b0 += 32) {
@@ -232,7 +233,7 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
               } else {
                 w = __fmul_rn(a, T);
                 T = Tn;
-                last = s_orig[k] + 1;
+                lastk = k;
               }
             }
           }
@@ -255,8 +256,8 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
             }
           }
         }
-        if (__all_sync(kFull, done)) break;
       }
+      if (lastk >= 0) { last = s_orig[lastk] + 1; lastk = -1; }
       __syncwarp();   // the staging slots are refilled by the next batch
     }
 

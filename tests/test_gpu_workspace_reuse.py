@@ -1,8 +1,11 @@
-"""One workspace across calls, on the GPU: the binning's tile counts, the persistent kernels'
-queue words and the backward's per-Gaussian accumulators are kept at zero between calls by
-the kernels themselves (no memsets), so calls in any valid order and on cameras of
-different sizes must give the results of a fresh workspace.  Checked against a fresh
-workspace (bit-exact lists, images and gradients up to the order of float atomics)."""
+"""One workspace across calls, on the GPU: the binning's tile counts and the forward and
+sort queues are put back to zero by the kernels that use them (the scan clears the counts
+after reading them, the last CTA to leave a queue resets it), the backward's accumulators
+and queue are cleared by the host before each backward, and the host clears the counts
+itself when a projection was not followed by a binning.  Calls in any valid order and on
+cameras of different sizes must therefore give the results of a fresh workspace.  Checked
+against a fresh workspace (bit-exact lists, images and gradients up to the order of float
+atomics)."""
 import numpy as np
 import pytest
 
