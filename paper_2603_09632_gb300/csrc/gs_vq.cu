@@ -11,8 +11,9 @@
 // canonical K-major core-matrix layout, completion signalled through an mbarrier, and the
 // epilogue (optional F write, |F|^2, relevance) reading the accumulator with tcgen05.ld.
 // The next tile's weights are fetched while the tensor cores and the epilogue run.  One
-// persistent CTA per SM holds the codebook in shared memory for all its tiles.  Every wait is bounded; on a timeout the kernel records an
-// error, waits (bounded) for its own MMAs, frees its tensor memory and returns.
+// persistent CTA per SM holds the codebook in shared memory for its range of tiles.  Every
+// wait is bounded; on a timeout the kernel records an error, waits (bounded) for its own
+// MMAs, frees its tensor memory and returns.
 #include <algorithm>
 #include <cstdint>
 
@@ -140,8 +141,8 @@ static_assert(2 * kGroups * kMaxText * kRows >= kMaxText * kMaxDc, "text staging
 static_assert(kMaxText == 8, "E t_j rows are read as two float4");
 
 // One 128-pixel tile per iteration.  The four threads t = r + 128 g (g = 0..3) share row r
-// (pixel p = tile * 128 + r): each loads a quarter of the row's L weights (prefetched during
-// the previous tile's epilogue), and in the epilogue warp w reads TMEM lanes 32 (w mod 4) ..
+// (pixel p = tile * 128 + r): each loads a quarter of the row's L weights (issued before
+// the previous tile's epilogue and consumed after it), and in the epilogue warp w reads TMEM lanes 32 (w mod 4) ..
 // and every fourth 32-column chunk of F starting at chunk w / 4.  The prompt dot products
 // use F.t_j = w.(E t_j) with E t_j formed once per CTA, so the epilogue only adds |F|^2.
 __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
   const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
   const int64_t n_tiles = (a.P + kRows - 1) / kRows;
 
-  // this thread's quarter row of weights for one tile, and its partial prompt dot products
+  // this thread's quarter row of weights for one tile (load_rows), and its partial prompt
+  // dot products (row_dots, formed when the row is staged)
   float wv[kMaxL / kGroups];
   float dp[kMaxText];
   auto load_rows = [&](int64_t tile) {
@@ -218,6 +220,8 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
 #pragma unroll
     for (int k = 0; k < kMaxL / kGroups; ++k)
       wv[k] = (k < LH && live) ? __ldg(a.wmap + (int64_t)(h * LH + k) * a.P + p) : 0.f;
+  };
+  auto row_dots = [&]() {
 #pragma unroll
     for (int j = 0; j < kMaxText; ++j) dp[j] = 0.f;
     if (nt > 0) {
@@ -290,9 +294,13 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
     a.rel[pr] = best;
   };
 
-  int64_t tile = blockIdx.x;
-  if (tile < n_tiles) {
+  // each CTA decodes one contiguous range of tiles
+  const int64_t t_per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t_begin = min(n_tiles, (int64_t)blockIdx.x * t_per), t_end = min(n_tiles, t_begin + t_per);
+  int64_t tile = t_begin;
+  if (tile < t_end) {
     load_rows(tile);
+    row_dots();
     store_rows(0);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -300,7 +308,7 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
   __syncthreads();
   uint32_t phase = 0;
   bool failed = false;
-  for (int it = 0; tile < n_tiles; tile += gridDim.x, ++it) {
+  for (int it = 0; tile < t_end; ++tile, ++it) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (t == 0) {
       for (int ks = 0; ks < L / 8; ++ks) {
@@ -313,11 +321,12 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
       }
       mma_commit(bar);
     }
-    // prefetch the next tile's weights and finish the previous tile's relevance while the
+    // issue the next tile's weight loads (first used after this tile's epilogue, so their
+    // latency hides behind its stores) and finish the previous tile's relevance while the
     // tensor cores run
-    const int64_t next = tile + gridDim.x;
-    if (next < n_tiles) load_rows(next);
-    if (want_rel && h == 0 && it > 0) finish_rel(tile - gridDim.x, it - 1);
+    const int64_t next = tile + 1;
+    if (next < t_end) load_rows(next);
+    if (want_rel && h == 0 && it > 0) finish_rel(tile - 1, it - 1);
     const bool ok = mbar_wait(bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {   // every thread takes the same branch
@@ -357,7 +366,10 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
       sNrm[((it & 1) * kGroups + h) * kRows + 32 * (warp & 3) + lane] = (n4[0] + n4[1]) + (n4[2] + n4[3]);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();   // MMA done, TMEM read, previous relevance done: A and the other buffers free
-    if (next < n_tiles) store_rows((it + 1) & 1);
+    if (next < t_end) {
+      row_dots();
+      store_rows((it + 1) & 1);
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();   // next A tile staged; norms and dots consumed
@@ -365,10 +377,10 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
   if (failed) {
     if (t == 0 && a.err) atomicExch(a.err, 1);
     mbar_wait(bar, phase ^ 1u);   // bounded: let this CTA's own MMAs drain before freeing TMEM
-  } else if (want_rel && h == 0 && blockIdx.x < n_tiles) {
+  } else if (want_rel && h == 0 && t_begin < t_end) {
     // the last tile's relevance (its partials were published by the loop's last barrier)
-    const int64_t last = blockIdx.x + ((n_tiles - 1 - blockIdx.x) / gridDim.x) * gridDim.x;
-    finish_rel(last, (int)((last - blockIdx.x) / gridDim.x));
+    const int64_t last = t_end - 1;
+    finish_rel(last, (int)(last - t_begin));
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
