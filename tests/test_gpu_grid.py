@@ -42,6 +42,7 @@ def _render(rast, scene, cam, s, ox, oy):
 @pytest.mark.parametrize("grid", GRIDS)
 def test_grid_forward_matches_oracle_and_full_render(oracle, OG, room, grid):
     import torch
+    from paper_2603_09632_gb300 import _lib as L
     from paper_2603_09632_gb300.render import Rasterizer
     s, ox, oy = grid
     sc, cam = room
@@ -49,6 +50,8 @@ def test_grid_forward_matches_oracle_and_full_render(oracle, OG, room, grid):
     scene = U.upload(sc)
     full = rast.forward(scene, cam)
     full = {k: v.clone() for k, v in full.items() if isinstance(v, torch.Tensor)}
+    torch.cuda.synchronize()
+    T_full, nc_full = L.gs_get_pixel_state(rast.ws, cam.H, cam.W)
     c, got = _render(rast, scene, cam, s, ox, oy)
     Hs, Ws = OG.grid_shape(cam.H, cam.W, s)
     assert got["alpha"].shape == (Hs, Ws) and got["feat"].shape == (16, Hs, Ws)
@@ -70,6 +73,17 @@ def test_grid_forward_matches_oracle_and_full_render(oracle, OG, room, grid):
         else:
             assert torch.equal(a[mi], b[uu, vv]), k
             assert (a[~mi] == 0).all(), k
+    # per-sample final transmittance and last-contributor count (the backward's replay
+    # bound) of the samples inside the image: the oracle's on unflagged samples, and the
+    # full-resolution render's at the sample's pixel, bit for bit
+    T_g, nc_g = L.gs_get_pixel_state(rast.ws, Hs, Ws)
+    ok = inb & (flags == 0)
+    np.testing.assert_array_equal(nc_g[ok], ref["n_contrib"][ok])
+    assert np.abs(T_g - ref["T_final"])[ok].max() <= TOL_FWD
+    ui = np.broadcast_to(u[:, None], inb.shape)[inb]
+    vi = np.broadcast_to(v[None, :], inb.shape)[inb]
+    np.testing.assert_array_equal(nc_g[inb], nc_full[ui, vi])
+    np.testing.assert_array_equal(T_g[inb], T_full[ui, vi])
 
 
 @pytest.mark.parametrize("grid", [(2, 1, 0), (3, 2, 2), (16, 15, 4)])
