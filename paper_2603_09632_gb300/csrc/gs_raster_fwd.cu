@@ -4,11 +4,13 @@
 // both halves walk the tile's list, each culling it against its own pixel box, which
 // halves the longest work item (the tail of the persistent schedule).
 //
-// The tile's sorted list is consumed in batches of 256 Gaussians staged in shared
+// The tile's sorted list is consumed in batches of 128 Gaussians staged in shared
 // memory (records gathered by id; features converted to fp32 once per batch, so bf16
-// storage costs no per-pixel conversion).  A warp skips the colour/feature update of a
-// Gaussian when none of its 32 pixels blends it (ballot), a warp stops when all its
-// pixels have terminated, and the CTA stops when all 256 pixels have.
+// storage costs no per-pixel conversion).  Each warp owns an 8 x 4 pixel strip and visits
+// only the batch entries that can reach it.  A warp skips the colour/feature update of a
+// Gaussian when none of its 32 pixels blends it (ballot), stops when all its pixels have
+// terminated (checked before each group of 32 candidates), and the CTA stops when all
+// 128 pixels have.
 #include "gs_blend.cuh"
 #include "gs_internal.cuh"
 
