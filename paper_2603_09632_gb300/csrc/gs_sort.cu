@@ -16,9 +16,9 @@
 //      skipped), then orders runs of equal depth by id, which makes the order the total
 //      (depth, id) order whatever order the scatter left.  Ranges longer than shared
 //      memory holds are sorted in chunks through global ping-pong buffers.
-// Steps 1 and 3 (warp_tile_instances) flatten the instances of a warp's 32 Gaussians and aggregate the atomic
-// additions of equal tiles within a warp, so a Gaussian covering many tiles is spread over
-// the warp instead of serialising one thread.
+// Steps 1 and 3 (warp_tile_instances) flatten the instances of a warp's 32 Gaussians and
+// aggregate the atomic additions of equal tiles within a warp, so a Gaussian covering many
+// tiles is spread over the warp instead of serialising one thread.
 #include "gs_blend.cuh"
 #include "gs_internal.cuh"
 
