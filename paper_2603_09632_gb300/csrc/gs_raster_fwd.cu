@@ -7,10 +7,9 @@
 // The tile's sorted list is consumed in batches of 128 Gaussians staged in shared
 // memory (records gathered by id; features converted to fp32 once per batch, so bf16
 // storage costs no per-pixel conversion).  Each warp owns an 8 x 4 pixel strip and visits
-// only the batch entries that can reach it.  A warp skips the colour/feature update of a
-// Gaussian when none of its 32 pixels blends it (ballot), stops when all its pixels have
-// terminated (checked before each group of 32 candidates), and the CTA stops when all
-// 128 pixels have.
+// only the batch entries that can reach it (ballot over a per-strip box test), stops when
+// all its pixels have terminated (checked before each group of 32 candidates), and the
+// CTA stops when all 128 pixels have.
 #include "gs_blend.cuh"
 #include "gs_internal.cuh"
 
@@ -178,7 +177,7 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             }
           }
         }
-        if (__any_sync(0xffffffffu, w != 0.f)) {
+        {   // accumulate unconditionally: w = 0 adds nothing, and live entries almost always blend
           const float4 r2 = s_r2[j];
           c0 = fmaf(w, r2.x, c0);
           c1 = fmaf(w, r2.y, c1);
