@@ -202,7 +202,7 @@ def captured_traffic(stage, workload):
 # ---------------------------------------------------------------- clocks
 
 class NvmlClockSampler:
-    """SM clock and clock-event reasons every ~1 ms through the driver's NVML library
+    """SM clock and clock-event reasons every ~1 ms through NVML (libnvidia-ml)
     (read-only queries), for timed regions far shorter than nvidia-smi's sampling period."""
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
