@@ -143,6 +143,39 @@ def test_sh_basis_orthonormal(oracle):
     assert Y[0, 0] == pytest.approx(1 / math.sqrt(4 * math.pi))
 
 
+def _real_sh_from_scipy(deg, dirs):
+    """Real SH of degree <= deg, ordered (l, m = -l..l), built from SciPy's complex
+    spherical harmonics (which carry the Condon-Shortley phase (-1)^m) by the textbook
+    construction sqrt(2) (-1)^m Im Y_l^|m| (m < 0), Y_l^0, sqrt(2) (-1)^m Re Y_l^m (m > 0);
+    the (-1)^m cancels the phase."""
+    from scipy import special
+    theta = np.arccos(np.clip(dirs[:, 2], -1.0, 1.0))   # polar angle from +z
+    phi = np.arctan2(dirs[:, 1], dirs[:, 0])             # azimuth from +x
+    if hasattr(special, "sph_harm_y"):
+        Ylm = lambda l, m: special.sph_harm_y(l, m, theta, phi)   # noqa: E731
+    else:
+        Ylm = lambda l, m: special.sph_harm(m, l, phi, theta)     # noqa: E731
+    cols = []
+    for l in range(deg + 1):
+        for m in range(-l, l + 1):
+            if m < 0:
+                cols.append(math.sqrt(2) * (-1) ** m * Ylm(l, -m).imag)
+            elif m == 0:
+                cols.append(Ylm(l, 0).real)
+            else:
+                cols.append(math.sqrt(2) * (-1) ** m * Ylm(l, m).real)
+    return np.stack(cols, -1)
+
+
+def test_sh_basis_equals_the_textbook_real_harmonics(oracle):
+    # orthonormality cannot tell a sign flip or a swap inside a degree; the basis itself can
+    pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(12)
+    d = rng.normal(size=(200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    np.testing.assert_allclose(oracle.sh_basis(3, d), _real_sh_from_scipy(3, d), atol=1e-12)
+
+
 def test_sh_colour_uses_view_direction_from_camera_centre(oracle):
     # Camera centre c placed explicitly (t = -R c); colour = 0.5 + sum_k sh_k Y_k(dir).
     rng = np.random.default_rng(3)
