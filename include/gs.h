@@ -131,7 +131,12 @@ gs_status gs_workspace_bytes(gs_workspace* ws, int64_t* bytes);
  * SH colour along the view direction from the camera centre).  Writes, into the
  * workspace, each Gaussian's 2D mean, conic (inverse of Sigma' + 0.3 I), depth, colour,
  * tile rectangle (3-sigma bound) and tile count.  Culled Gaussians (depth <= near_z,
- * degenerate Sigma', empty rectangle) get no tiles.  Grows the workspace if needed. */
+ * degenerate Sigma', empty rectangle) get no tiles.  Grows the workspace if needed.
+ * Errors: GS_ERR_ARG for a NULL scene, camera or workspace, n outside [0, 2^31), sh_degree
+ * outside [0, 3], n_feat outside [0, 64], an unknown feat_dtype, a missing or not
+ * 16-byte-aligned parameter array, a camera with W or H <= 0 (or above 65535 tiles), a
+ * tile size other than 16, fx, fy or near_z not > 0, or a stride outside [1, 256] or
+ * offsets outside [0, stride); GS_ERR_OOM if the workspace cannot grow; GS_ERR_CUDA. */
 gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
                      void* stream);
 
@@ -144,7 +149,9 @@ gs_status gs_project(const gs_scene* scene, const gs_camera* cam, gs_workspace* 
  * If n_instances_out is non-NULL the call synchronises the stream once to read the
  * instance count I, grows the workspace if needed and stores I there.  If it is NULL
  * the call never synchronises: the reserved instance capacity must be large enough,
- * otherwise the excess is dropped and the device status word records the overflow. */
+ * otherwise the excess is dropped and the device status word records the overflow.
+ * Errors: GS_ERR_ARG (NULL workspace), GS_ERR_STATE (no gs_project before it), GS_ERR_OOM
+ * (the instance buffers cannot grow), GS_ERR_CUDA. */
 gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream);
 
 /* a3. Forward rendering (Eq. 1 front-to-back alpha blending; depth, App. B; features,
@@ -152,7 +159,10 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
  * at 0.99 and stops before a Gaussian that would take transmittance below 1e-4;
  * alpha = 1 - T_final.  Outputs are device pointers (see conventions), any may be NULL.
  * The per-pixel final transmittance and contributor count are kept for gs_render_bwd.
- * scene and cam must be those given to gs_project. */
+ * scene and cam must be those given to gs_project.
+ * Errors: GS_ERR_ARG as gs_project, and for a feat pointer that is not 16-byte aligned;
+ * GS_ERR_STATE if the workspace holds no binned projection of a scene of this size with
+ * this camera grid; GS_ERR_CUDA. */
 gs_status gs_render_fwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
                         float* rgb, float* depth, float* alpha, float* feat, void* stream);
 
@@ -186,7 +196,10 @@ gs_status gs_render_fwd_loss(const gs_scene* scene, const gs_camera* cam, gs_wor
  * g_opac [n], g_sh [n][K][3], g_feats [n][n_feat] (float32 whatever feat_dtype is), and
  * g_pose6 [6] = dL/dxi of the left twist perturbation T <- Exp(xi) T, xi = (rho, phi).
  * Any output may be NULL (not written).  Must follow gs_render_fwd on the same
- * workspace with the same scene and camera. */
+ * workspace with the same scene and camera.
+ * Errors: GS_ERR_ARG as gs_project, and for g_feats or g_quats not 16-byte aligned;
+ * GS_ERR_STATE if no gs_render_fwd of a scene of this size with this camera grid precedes
+ * it on the workspace; GS_ERR_CUDA. */
 gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspace* ws,
                         const float* g_rgb, const float* g_depth, const float* g_alpha,
                         const float* g_feat, float* g_means, float* g_scales, float* g_quats,
