@@ -109,7 +109,8 @@ const char* gs_status_string(gs_status s);
  * Errors: GS_ERR_ARG (ws NULL), GS_ERR_CUDA (bad device). */
 gs_status gs_workspace_create(gs_workspace** ws, int device);
 
-/* Free the workspace and all its device memory (synchronises the device). */
+/* Free the workspace and all its device memory (synchronises the device).  NULL is a
+ * no-op. */
 void gs_workspace_destroy(gs_workspace* ws);
 
 /* Pre-allocate capacity for n_gauss Gaussians, n_instances tile instances, n_pixels pixels
@@ -208,7 +209,8 @@ gs_status gs_render_bwd(const gs_scene* scene, const gs_camera* cam, gs_workspac
 
 /* Upstream gradient of the L1 loss scale * sum|pred - target| (the distillation loss of
  * the semantic workload): grad = scale * sign(pred - target), 0 where equal.  Device
- * pointers, n elements.  May alias grad == pred. */
+ * pointers, n elements.  May alias grad == pred.
+ * Errors: GS_ERR_ARG (n < 0, or a NULL pointer with n > 0), GS_ERR_CUDA. */
 gs_status gs_l1_grad(const float* pred, const float* target, int64_t n, float scale,
                      float* grad, void* stream);
 
@@ -231,7 +233,9 @@ gs_status gs_grid_target_region(const int32_t* seg, int32_t H, int32_t W, const 
 
 /* Continuous feature map fmap [D][Hf][Wf] at a lower resolution: sample (u, v) reads the
  * map at (round(u (Hf - 1) / max(H - 1, 1)), round(v (Wf - 1) / max(W - 1, 1))), halves
- * rounded away from zero (exact integer arithmetic); V = 1 inside the image. */
+ * rounded away from zero (exact integer arithmetic); V = 1 inside the image.
+ * Errors: GS_ERR_ARG (grid arguments as in gs_camera, D < 0, Hf or Wf <= 0, or a NULL fmap
+ * or target with D > 0), GS_ERR_CUDA. */
 gs_status gs_grid_target_resample(const float* fmap, int32_t D, int32_t Hf, int32_t Wf, int32_t H,
                                   int32_t W, int32_t stride, int32_t off_x, int32_t off_y,
                                   float* target, float* mask, void* stream);
@@ -249,7 +253,8 @@ gs_status gs_vq_weights(const float* logits, int64_t n, int32_t L, int32_t out_d
                         void* stream);
 
 /* Backward of gs_vq_weights: g_logits = w * (g_w - sum_l g_w,l w_l), w recomputed from the
- * logits.  All [n][L] float32 device arrays. */
+ * logits.  All [n][L] float32 device arrays.
+ * Errors: GS_ERR_ARG (n < 0, L outside [1, 64], or a NULL array with n > 0), GS_ERR_CUDA. */
 gs_status gs_vq_weights_bwd(const float* logits, const float* g_w, int64_t n, int32_t L,
                             float* g_logits, void* stream);
 
@@ -270,23 +275,28 @@ gs_status gs_vq_decode(const float* wmap, int64_t P, int32_t L, const float* cod
 /* ---- introspection (synchronous; host pointers) ---------------------------------- */
 
 /* Counts of the last gs_project/gs_bin_tiles/gs_render_fwd.  inst_eff is computed by a
- * small reduction over the per-pixel contributor counts.  Synchronises `stream`. */
+ * small reduction over the per-pixel contributor counts.  Synchronises `stream`.
+ * Errors: GS_ERR_ARG (NULL argument), GS_ERR_OOM, GS_ERR_CUDA. */
 gs_status gs_get_stats(gs_workspace* ws, gs_stats* out, void* stream);
 
 /* Copy the sorted instance list to host: tile id and Gaussian id per instance, at most
  * cap entries; *n_out receives I.  ranges_out (may be NULL) receives 2*T uint32
- * [start, end) per tile.  Synchronises `stream`. */
+ * [start, end) per tile.  Synchronises `stream`.
+ * Errors: GS_ERR_ARG (NULL workspace, cap < 0), GS_ERR_STATE (nothing binned yet),
+ * GS_ERR_CUDA. */
 gs_status gs_get_instances(gs_workspace* ws, uint32_t* tiles_out, uint32_t* ids_out,
                            int64_t cap, int64_t* n_out, uint32_t* ranges_out, void* stream);
 
 /* Copy the projection of the last gs_project to host (arrays of n entries; any NULL):
  * mean2d [n][2], conic [n][3], depth [n], rgb [n][3], rect [n][4] = (x0, y0, x1, y1)
- * tiles, all zero for culled Gaussians.  Synchronises `stream`. */
+ * tiles, all zero for culled Gaussians.  Synchronises `stream`.
+ * Errors: GS_ERR_ARG (NULL workspace), GS_ERR_STATE (no gs_project yet), GS_ERR_CUDA. */
 gs_status gs_get_projection(gs_workspace* ws, float* mean2d, float* conic, float* depth,
                             float* rgb, int32_t* rect, void* stream);
 
 /* Copy the per-pixel final transmittance and contributor count of the last forward
- * render to host ([H][W] each; either may be NULL).  Synchronises `stream`. */
+ * render to host ([H][W] each; either may be NULL).  Synchronises `stream`.
+ * Errors: GS_ERR_ARG (NULL workspace), GS_ERR_STATE (no render yet), GS_ERR_CUDA. */
 gs_status gs_get_pixel_state(gs_workspace* ws, float* T_final, uint32_t* n_contrib,
                              void* stream);
 
@@ -296,12 +306,14 @@ enum { GS_TIMER_PROJECT = 0, GS_TIMER_BIN = 1, GS_TIMER_FWD = 2, GS_TIMER_BWD_RA
        GS_TIMER_BWD_PROJECT = 4, GS_NUM_TIMERS = 5 };
 
 /* Enable (1) or disable (0) event timing of the stages above.  While enabled, each stage
- * records a CUDA event pair around its kernels on the caller's stream. */
+ * records a CUDA event pair around its kernels on the caller's stream.
+ * Errors: GS_ERR_ARG (NULL workspace), GS_ERR_CUDA (event creation). */
 gs_status gs_timing_enable(gs_workspace* ws, int enable);
 
 /* Synchronise, add up the elapsed times of all recorded event pairs and reset them.
  * ms_out[GS_NUM_TIMERS] receives total milliseconds, count_out[GS_NUM_TIMERS] (may be
- * NULL) the number of timed launches of each stage. */
+ * NULL) the number of timed launches of each stage.
+ * Errors: GS_ERR_ARG (NULL workspace or ms_out), GS_ERR_CUDA. */
 gs_status gs_timing_collect(gs_workspace* ws, double* ms_out, int64_t* count_out);
 
 /* Number of CUDA kernels this library has launched in the process so far (all
@@ -347,7 +359,7 @@ typedef struct {
  * Errors: GS_ERR_ARG, GS_ERR_CUDA. */
 gs_status gs_serve_create(gs_server** server, int device, int64_t hbm_budget_bytes, int max_slots);
 
-/* Cancel pending requests, wait for running ones, free everything. */
+/* Cancel pending requests, wait for running ones, free everything.  NULL is a no-op. */
 void gs_serve_destroy(gs_server* server);
 
 /* Copy a scene (device pointers, as for gs_project) into server-owned device memory.
@@ -370,7 +382,8 @@ gs_status gs_serve_poll(gs_server* server, uint64_t ticket, int64_t timeout_us, 
 gs_status gs_serve_cancel(gs_server* server, uint64_t ticket);
 
 /* Memory held by resident scenes, admission estimate of the requests running now and
- * its peak, and the peak number of requests running at once (any may be NULL). */
+ * its peak, and the peak number of requests running at once (any may be NULL).
+ * Errors: GS_ERR_ARG (NULL server). */
 gs_status gs_serve_info(gs_server* server, int64_t* scene_bytes, int64_t* in_flight_bytes,
                         int64_t* peak_in_flight_bytes, int32_t* peak_running);
 
