@@ -120,7 +120,8 @@ gs_status gs_workspace_reserve(gs_workspace* ws, int64_t n_gauss, int64_t n_inst
                                int64_t n_pixels);
 
 /* Synchronise `stream`, read and clear the device status word.  Returns GS_OK or
- * GS_ERR_DEVICE (e.g. the instance count exceeded the reserved capacity). */
+ * GS_ERR_DEVICE (e.g. the instance count exceeded the reserved capacity).
+ * Errors: GS_ERR_ARG (NULL workspace), GS_ERR_CUDA. */
 gs_status gs_workspace_status(gs_workspace* ws, void* stream);
 
 /* Device memory held by the workspace, in bytes, into *bytes (host pointer): the sum of
