@@ -227,7 +227,9 @@ gs_status gs_l1_grad(const float* pred, const float* target, int64_t n, float sc
 
 /* Region-indexed annotations: seg [H][W] int32 region ids (-1 = background) and a
  * region-feature table [R][D].  V = 1 where the sampled id lies in [0, R), and G* is that
- * table row; any other id counts as background (V = 0, G* = 0). */
+ * table row; any other id counts as background (V = 0, G* = 0).
+ * Errors: GS_ERR_ARG (grid arguments as in gs_camera, R or D < 0, or a NULL seg, table or
+ * target where needed), GS_ERR_CUDA. */
 gs_status gs_grid_target_region(const int32_t* seg, int32_t H, int32_t W, const float* table,
                                 int32_t R, int32_t D, int32_t stride, int32_t off_x, int32_t off_y,
                                 float* target, float* mask, void* stream);
