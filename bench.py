@@ -2,9 +2,12 @@
 
 One step = one camera pose of the workload through the whole path: gs_project ->
 gs_bin_tiles -> gs_render_fwd -> gs_render_bwd (gradients to every Gaussian parameter and
-the 6-DoF pose), inputs resident in HBM.  The default workload is the SLAM frame: 200k
-room Gaussians, SH 0, 16 fp32 feature channels, 640x480, fx = fy = 600, cycling over a
-100-pose trajectory.  L2 is flushed (a 256 MiB write) between timed steps.
+the 6-DoF pose), inputs resident in HBM.  The default workload is the largest
+single-GPU configuration, the memory form: 3M room Gaussians, SH 0, 32 fp32 feature
+channels, 3840x2160, fx = fy = 3600, per-tile recomputation in the backward (no stored
+blend lists), cycling over a 10-pose trajectory.  The SLAM frame (200k, 640x480, 16
+channels) and the semantic frame (1M, SH 3, 64 bf16 channels, 1200x680) are selected with
+--workload.  L2 is flushed (a 256 MiB write) between timed steps.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead (the
 reference arm: there is no runnable reference implementation of this path).
@@ -37,7 +40,9 @@ WORKLOADS = {
     "tiny_128x96_2k": dict(make=S.config_tiny, bf16=False, l1=False,
                            desc="cube 2k Gaussians, SH0, 8 fp32 feats, 128x96, fx=100"),
     "memory_3840x2160_3m": dict(make=lambda: S.config_memory(n_poses=10), bf16=False, l1=False,
-                                desc="room 3M Gaussians, SH0, 32 fp32 feats, 3840x2160, fx=3600"),
+                                desc="room 3M Gaussians, SH0, 32 fp32 feats, 3840x2160, fx=3600, "
+                                     "per-tile recomputation (no stored blend lists)",
+                                cpu_mode=0, cpu_tiles=64),
 }
 # Semantic distillation phase (Sec. 3.2, App. D): grid-sampled rendering with random offsets,
 # region-indexed targets, the masked L1 + cosine loss fused into the forward, and the
@@ -57,7 +62,7 @@ for _s in (1, 2, 4):
         make=lambda: S.config_semantic(n_poses=100), bf16=True, l1=False, grid=_s,
         desc=f"room 1M Gaussians, SH3, 64 bf16 feats, 1200x680, grid stride {_s} (random offsets), "
              "region targets, fused masked L1+cos loss, features-only backward")
-DEFAULT_WORKLOAD = "slam_640x480_200k"
+DEFAULT_WORKLOAD = "memory_3840x2160_3m"
 METRIC = "Mpix/s fwd+bwd (RGB+D+feat) at 1 GB300"
 L2_FLUSH_BYTES = 256 << 20
 
@@ -155,8 +160,25 @@ def stage_flops(st, D, K):
 
 
 def fp32_peak_tflops(peaks):
-    """FP32 FMA peak derived from the unit counts: 152 SMs x 128 lanes x 2 FLOP x max clock."""
+    """FP32 FMA peak derived from the unit counts: 152 SMs x 128 lanes x 2 FLOP x max clock
+    (used only when no measurement is available)."""
     return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def measure_fp32_peak(L, dev, index, iters=65536, reps=3):
+    """FP32 FMA rate of this GPU from the library's microbenchmark (independent FMA chains
+    at full occupancy, CUDA events), with the SM clock sampled while it runs.  Untimed:
+    taken before the timed region.  Returns the best of ``reps`` runs."""
+    clocks = make_clock_sampler(dev, index)
+    clocks.start()
+    runs = [L.gs_measure_fp32_peak(iters) for _ in range(reps)]
+    clk = clocks.stop()
+    tf, ms = max(runs)
+    return {"tflops": round(tf, 2), "ms": round(ms, 3), "runs_tflops": [round(r[0], 2) for r in runs],
+            "sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+            "reasons": clk.get("reasons"),
+            "how": "gs_measure_fp32_peak: 8 independent fmaf chains per thread, every SM at its "
+                   "occupancy limit, CUDA events; best of %d, SM clock sampled meanwhile" % reps}
 
 
 KERNEL_SOURCES = {
@@ -312,16 +334,25 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- GPU arm
 
-def build_roofline(stage, sb_tot, sf_tot, pairs, steps, workload):
+def build_roofline(stage, sb_tot, sf_tot, pairs, steps, workload, fp32=None, sm_mhz=None):
     """Roofline of the dominant stage: algorithmic bytes and FLOPs per launch (summed over
     the timed poses in sb_tot / sf_tot) against the measured stage time; the binding
-    bound is whichever of the HBM and FP32 times is larger."""
+    bound is whichever of the HBM and FP32 times is larger.  ``fp32`` is the measured FP32
+    peak (measure_fp32_peak; the unit-count derivation only without it) and ``sm_mhz`` the
+    median SM clock of the timed region, which gives the FP32 fraction at the clock the
+    kernel ran at as well."""
     stage_ms = {name: stage[name][0] / max(stage[name][1], 1) for name in stage}
     dom = max(stage_ms, key=stage_ms.get)
     peaks, src = load_peaks()
     alg_b = sb_tot[dom] / steps
     alg_f = sf_tot[dom] / steps
-    p_alu = fp32_peak_tflops(peaks)
+    if fp32 and fp32.get("tflops"):
+        p_alu = float(fp32["tflops"])
+        alu_src = ("measured: FMA microbenchmark (gs_measure_fp32_peak) on this GPU in this run, "
+                   f"at {fp32.get('sm_mhz')} MHz median SM clock")
+    else:
+        p_alu = fp32_peak_tflops(peaks)
+        alu_src = "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"
     t_hbm = alg_b / (peaks["hbm_gbs"] * 1e9)
     t_alu = alg_f / (p_alu * 1e12)
     t_meas = stage_ms[dom] * 1e-3
@@ -329,8 +360,7 @@ def build_roofline(stage, sb_tot, sf_tot, pairs, steps, workload):
     if t_alu > t_hbm:
         achieved = alg_f / t_meas / 1e12
         roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(p_alu, 1),
-                    "unit": "TFLOP/s", "frac": round(achieved / p_alu, 4),
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"}
+                    "unit": "TFLOP/s", "frac": round(achieved / p_alu, 4), "peak_source": alu_src}
     else:
         achieved = alg_b / t_meas / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
@@ -340,10 +370,18 @@ def build_roofline(stage, sb_tot, sf_tot, pairs, steps, workload):
         "traffic": traffic, "alg_bytes": int(alg_b), "alg_flops": int(alg_f),
         "hbm_frac": round(alg_b / t_meas / 1e9 / peaks["hbm_gbs"], 4),
         "alu_frac": round(alg_f / t_meas / 1e12 / p_alu, 4),
+        "alu_peak_tflops": round(p_alu, 2),
         "pairs_eval_per_step": int(pairs[0] / steps), "pairs_blend_per_step": int(pairs[1] / steps),
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_alg_mb": {k: round(v / steps / 1e6, 3) for k, v in sb_tot.items()},
         "stage_alg_gflop": {k: round(v / steps / 1e9, 3) for k, v in sf_tot.items()}})
+    if sm_mhz:
+        # the dominant stage in cycles (ms x MHz = thousands of cycles), comparable across
+        # clocks, and its FP32 fraction against the peak scaled to the clock it ran at
+        roofline["stage_kcycles"] = round(stage_ms[dom] * sm_mhz, 1)
+        if fp32 and fp32.get("tflops") and fp32.get("sm_mhz"):
+            p_clk = p_alu * sm_mhz / fp32["sm_mhz"]
+            roofline["alu_frac_at_kernel_clock"] = round(alg_f / t_meas / 1e12 / p_clk, 4)
     return roofline
 
 
@@ -413,10 +451,9 @@ def run_gpu(args):
     if L.gs_workspace_status(ws) != L.GS_OK:
         raise RuntimeError("instance capacity overflow during warm-up")
 
+    fp32 = measure_fp32_peak(L, dev, local)          # untimed, before the timed region
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    L.gs_timing_enable(ws, True)
-    L.gs_timing_collect(ws)
     clocks = make_clock_sampler(dev, local)
     clocks.start()
     if dist:
@@ -435,12 +472,20 @@ def run_gpu(args):
         dist.barrier()
     launches = L.gs_launch_count() - n0
     clk = clocks.stop()
-    stage = L.gs_timing_collect(ws)
-    L.gs_timing_enable(ws, False)
     status = L.gs_workspace_status(ws)
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ms = max_over_ranks(ms, dist, dev)
     value = job_throughput(world, args.steps, P, ms)
+
+    # per-stage times: a separate, untimed pass over the same poses with the library's
+    # stage events enabled (they add event records, so they stay out of the timed steps)
+    L.gs_timing_enable(ws, True)
+    L.gs_timing_collect(ws)
+    for k in range(args.steps):
+        step(gcams[poses[args.warmup + k]], gf)
+        flush.fill_(float(k))
+    stage = L.gs_timing_collect(ws)
+    L.gs_timing_enable(ws, False)
 
     # algorithmic bytes per stage, averaged over the timed poses (untimed recount)
     sb_tot, sf_tot, pairs = {}, {}, [0, 0]
@@ -456,7 +501,8 @@ def run_gpu(args):
             sb_tot[name] = sb_tot.get(name, 0.0) + b
         for name, f in stage_flops(st, D, K).items():
             sf_tot[name] = sf_tot.get(name, 0.0) + f
-    roofline = build_roofline(stage, sb_tot, sf_tot, pairs, args.steps, args.workload)
+    roofline = build_roofline(stage, sb_tot, sf_tot, pairs, args.steps, args.workload, fp32,
+                              clk.get("sm_mhz"))
     # device memory of the step: the scene, images and gradients (torch; the L2 flush buffer
     # excluded) and the library workspace's high-water mark
     torch_peak = int(torch.cuda.max_memory_allocated(dev)) - flush.numel() * flush.element_size()
@@ -478,10 +524,11 @@ def run_gpu(args):
                    "pixels_per_step": P, "poses": len(gcams), "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
-        "memory": memory, "device_status": L.status_string(status),
+        "fp32_peak": fp32, "memory": memory, "device_status": L.status_string(status),
     }
     if rank == 0 and not args.no_cpu and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args, scene_np, cams, target_budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(args, scene_np, cams, target_budget_s=args.cpu_budget,
+                                            mode=wl.get("cpu_mode", 1))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -549,7 +596,8 @@ def run_e2e(args, L, scene, gcams, poses, dev, stream, ws, K, D, H, W):
             "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
             "ms_per_step": round(ms / args.steps, 4),
             "what": "per step: upstream gradient images host->device (double-buffered on a copy "
-                    "stream), pose gradient device->host; the Gaussians stay resident"}
+                    "stream), pose gradient device->host (a tracking loop's result); the Gaussians "
+                    "stay resident; no rendered image and no Gaussian gradient is read back"}
 
 
 def run_grid(args):
@@ -856,13 +904,21 @@ def run_vq(args):
 
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_step(O, scene_np, cam, pixels):
+def sample_grads(n_feat, n_pix, seed):
+    """Seeded N(0,1) upstream gradients at the sampled pixels only ([C, n_pix])."""
+    rng = np.random.default_rng(seed)
+    return {k: rng.standard_normal((c, n_pix)).astype(np.float32)
+            for k, c in (("rgb", 3), ("depth", 1), ("alpha", 1), ("feat", n_feat))}
+
+
+def oracle_step(O, scene_np, cam, pixels, gs, mode=1):
     """One bounded sample of the workload through the CPU oracle (FP32): forward and
-    backward of a loss restricted to ``pixels`` (flat indices)."""
-    g = S.upstream_grads(cam.H, cam.W, scene_np.n_feat)
-    gs = {k: v.reshape(v.shape[:-2] + (-1,))[..., pixels] for k, v in g.items()}
-    O.render(scene_np, cam, "f32", pixels=pixels)
-    O.backward(scene_np, cam, gs, "f32", pixels=pixels)
+    backward of a loss restricted to ``pixels`` (flat indices) with upstream gradients
+    ``gs`` at those pixels.  ``mode`` 1 builds the sorted tile lists of the whole frame, 0
+    takes each sampled tile's candidates by brute force over all Gaussians (at 4K the
+    frame's lists hold ~10^8 instances, which a sample does not need)."""
+    O.render(scene_np, cam, "f32", pixels=pixels, mode=mode)
+    O.backward(scene_np, cam, gs, "f32", pixels=pixels, mode=mode)
 
 
 def sample_pixels(cam, n_tiles, rng, stride=1):
@@ -882,27 +938,34 @@ def sample_pixels(cam, n_tiles, rng, stride=1):
     return np.concatenate(pix)
 
 
-def cpu_baseline(args, scene_np, cams, target_budget_s=15.0, stride=1):
+def cpu_tiles(args, wl):
+    return args.cpu_tiles if args.cpu_tiles else wl.get("cpu_tiles", 300)
+
+
+def cpu_baseline(args, scene_np, cams, target_budget_s=15.0, stride=1, mode=1):
     from oracle import oracle as O
     O.build()
     cores = O.set_threads(os.cpu_count() or 1)
     rng = np.random.default_rng(5)
-    n_tiles = args.cpu_tiles
+    n_tiles = cpu_tiles(args, WORKLOADS[args.workload])
     t_tot, px_tot, k = 0.0, 0, 0
     while t_tot < target_budget_s and k < len(cams):
         cam = cams[k]
         pix = sample_pixels(cam, n_tiles, rng, stride)
+        gs = sample_grads(scene_np.n_feat, pix.size, 100 + k)
         t0 = time.perf_counter()
-        oracle_step(O, scene_np, cam, pix)
+        oracle_step(O, scene_np, cam, pix, gs, mode)
         t_tot += time.perf_counter() - t0
         px_tot += pix.size
         k += 1
+    lists = ("tile lists of the full frame" if mode == 1 else
+             "brute-force candidates of each sampled tile")
     return {"value": round(px_tot / t_tot / 1e6, 5), "unit": "Mpix/s", "cores": cores,
             "kind": "oracle",
             "sample": f"{k} poses x {n_tiles} random 16x16 tiles"
                       + (f" of the stride-{stride} sample grid" if stride > 1 else "")
-                      + ", FP32 oracle forward + backward (projection and tile lists of the "
-                      f"full scene each pose), {t_tot:.1f} s"}
+                      + f", FP32 oracle forward + backward (projection of the full scene and {lists} "
+                      f"each pose), {t_tot:.1f} s"}
 
 
 def run_reference(args):
@@ -916,11 +979,13 @@ def run_reference(args):
     scene_np, cams = wl["make"]()
     rng = np.random.default_rng(5)
     times, px = [], 0
+    n_tiles = cpu_tiles(args, wl)
     for k in range(args.warmup + args.steps):
         cam = cams[k % len(cams)]
-        pix = sample_pixels(cam, args.cpu_tiles, rng, wl.get("grid", 1))
+        pix = sample_pixels(cam, n_tiles, rng, wl.get("grid", 1))
+        gs = sample_grads(scene_np.n_feat, pix.size, 100 + k)
         t0 = time.perf_counter()
-        oracle_step(O, scene_np, cam, pix)
+        oracle_step(O, scene_np, cam, pix, gs, wl.get("cpu_mode", 1))
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
@@ -935,7 +1000,7 @@ def run_reference(args):
                        "pixels_per_step": int(px / args.steps), "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": round(value, 5), "unit": "Mpix/s", "cores": cores,
                              "kind": "oracle",
-                             "sample": f"{args.cpu_tiles} random 16x16 tiles per step, FP32 oracle "
+                             "sample": f"{n_tiles} random 16x16 tiles per step, FP32 oracle "
                                        "forward + backward on the host cores"},
             "e2e": {"value": round(value, 5), "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -1167,7 +1232,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--cpu-tiles", type=int, default=300)
+    ap.add_argument("--cpu-tiles", type=int, default=0,
+                    help="16x16 tiles per oracle sample (0: the workload's default, 300 or 64 at 4K)")
     ap.add_argument("--serve", action="store_true", help="serving-loop benchmark instead")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=200)

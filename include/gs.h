@@ -323,6 +323,17 @@ gs_status gs_timing_collect(gs_workspace* ws, double* ms_out, int64_t* count_out
  * workspaces, all devices).  Host-side counter; no synchronisation. */
 int64_t gs_launch_count(void);
 
+/* FP32 arithmetic peak of the current device, measured: not a step of the paper's method
+ * but the denominator of the rasterizer's roofline (blending, Eq. 1, and its backward,
+ * App. B, are bound by FP32 arithmetic).  Launches one kernel that fills every SM to its
+ * occupancy limit with threads advancing eight independent fused multiply-add chains for
+ * `iters` x 16 steps each (after a short warm-up launch), times it with CUDA events on
+ * `stream` and synchronises on the end event.  *tflops_out receives the FP32 rate
+ * (2 FLOPs per FMA), *ms_out (may be NULL) the kernel time.  Reads and changes no GPU
+ * setting; the caller samples the SM clock if it wants the rate at a known clock.
+ * Errors: GS_ERR_ARG (iters <= 0, NULL tflops_out), GS_ERR_CUDA. */
+gs_status gs_measure_fp32_peak(int iters, double* tflops_out, double* ms_out, void* stream);
+
 /* ---- serving ----------------------------------------------------------------------
  *
  * Keeps several scenes resident on one GPU and renders requests (forward, optionally
@@ -402,14 +413,19 @@ gs_status gs_serve_info(gs_server* server, int64_t* scene_bytes, int64_t* in_fli
  * Every intermediate buffer lives in one file-scope device array of about 4 MB that
  * each device using the library holds until the process exits.  That bounds the
  * request: at most 16384 Gaussians, 131072 tile instances, 65536 pixels and 1024 tiles
- * (e.g. 256 x 256); a larger request returns GS_ERR_OVER_BUDGET and writes nothing.
- *   - The first call on a device, with that device current, looks the array up with
- *     cudaGetSymbolAddress and clears part of it (and synchronises the device once);
- *     make that first call before any stream capture.
+ * (e.g. 256 x 256); a larger request returns GS_ERR_OVER_BUDGET and writes no output (the
+ * instance limit is only known after projection, so that refusal comes after one
+ * projection kernel has run on `stream`).
+ *   - The first call on a device, with that device current, looks the array's device
+ *     address up with cudaGetSymbolAddress (once per device); make that first call
+ *     before any stream capture.
  *   - Every call on a device shares the array and it keeps the last call's contents:
- *     calls that overlap on the GPU (other streams, other threads) race and must be
- *     serialised by the caller.
- *   - The call synchronises `stream` once (after projection) to check the instance count.
+ *     every call first clears, on `stream`, what must start at zero (its counters, its
+ *     persistent-kernel queues and the tile counts of its image).  Calls that overlap on
+ *     the GPU (other streams, other threads) race on the array and must be serialised by
+ *     the caller.
+ *   - Every call synchronises `stream` once, after projection, to read the instance
+ *     count it checks against the limit.
  * scene, cam and the outputs are as for gs_project / gs_render_fwd (device pointers,
  * outputs channel-major, any output may be NULL).  Errors: GS_ERR_ARG, GS_ERR_OVER_BUDGET,
  * GS_ERR_CUDA. */

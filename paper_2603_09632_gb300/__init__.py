@@ -2,7 +2,7 @@
 
 The compute path is the CUDA library ``libgs.so`` behind the C ABI in ``include/gs.h``;
 ``_lib`` is its ctypes binding (argument marshalling only), ``render`` a convenience
-layer, ``autograd`` the ``torch.autograd.Function`` and ``serve`` the serving loop.
+layer, ``autograd`` the ``torch.autograd.Function``; the serving loop is ``_lib.Server``.
 The library is loaded on first use of any of these names and loading raises if it has
 not been built (``python -m paper_2603_09632_gb300._build``); there is no fallback.
 """

@@ -94,6 +94,7 @@ def _load():
         "gs_timing_enable": ([P, i32], st),
         "gs_timing_collect": ([P, P, P], st),
         "gs_launch_count": ([], i64),
+        "gs_measure_fp32_peak": ([i32, C.POINTER(C.c_double), C.POINTER(C.c_double), P], st),
         "gs_render_fwd_noalloc": ([P, P, P, P, P, P, P], st),
         "gs_serve_create": ([C.POINTER(C.c_void_p), i32, i64, i32], st),
         "gs_serve_destroy": ([P], None),
@@ -454,6 +455,14 @@ def gs_vq_decode(wmap, codebook, F_out=None, text=None, tau=10.0, relevance=None
 
 def gs_launch_count() -> int:
     return int(lib.gs_launch_count())
+
+
+def gs_measure_fp32_peak(iters=65536, stream=None):
+    """(TFLOP/s, ms) of the FP32 FMA microbenchmark on the current device."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib.gs_measure_fp32_peak(int(iters), C.byref(tf), C.byref(ms), _stream(stream)),
+           "gs_measure_fp32_peak")
+    return tf.value, ms.value
 
 
 def gs_timing_enable(ws, enable=True):

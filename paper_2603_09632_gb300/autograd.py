@@ -5,7 +5,15 @@ raw quaternions) so that callers keep their own parameterisation (log-scales, op
 logits, ...) in PyTorch and autograd chains through it; and a pose twist ``xi`` (6,)
 applied on the left of the base world->camera pose, T = Exp(xi) T0.  The gradient
 returned for ``xi`` is the twist gradient at the composed pose, which equals dL/dxi at
-xi = 0 -- the way pose tracking uses it (compose, step, reset xi).
+xi = 0 -- the way pose tracking uses it (compose, step, reset xi).  The pose is composed
+on the host; pass ``xi`` as a CPU tensor to keep the forward free of a device
+synchronisation (its gradient is returned on the device of ``xi``).
+
+Several renders may share one Rasterizer before a single backward (e.g. the keyframes of
+one mapping step, Eq. 3, summed into one loss).  The workspace keeps only the latest
+forward's state, so the backward of an earlier render first recomputes its own forward
+(projection, tile lists and per-pixel state; deterministic, so identical to the original)
+before differentiating.
 """
 from __future__ import annotations
 
@@ -57,16 +65,26 @@ class GSRenderFunction(torch.autograd.Function):
         c = _Cam(cam, T[:3, :3], T[:3, 3])
         scene = L.Scene(means.detach(), scales.detach(), quats.detach(), opacities.detach(),
                         sh.detach(), feats.detach() if feats is not None else None)
-        out = rast.forward(scene, c, feat=feats is not None and feats.shape[1] > 0)
+        want_feat = feats is not None and feats.shape[1] > 0
+        out = rast.forward(scene, c, feat=want_feat)
+        # saved so that autograd rejects a backward after an in-place change of the parameters
+        ctx.save_for_backward(means, scales, quats, opacities, sh, *(() if feats is None else (feats,)))
         ctx.scene, ctx.cam, ctx.rast = scene, c, rast
+        ctx.generation, ctx.want_feat = rast.generation, want_feat
         ctx.feat_dtype = None if feats is None else feats.dtype
         ctx.has_feats = feats is not None
+        ctx.xi_device = xi.device
         f = out["feat"] if out["feat"] is not None else torch.zeros((0,) + out["depth"].shape,
                                                                     device=means.device)
         return out["rgb"], out["depth"], out["alpha"], f
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_alpha, g_feat):
+        ctx.saved_tensors   # raises if a parameter was modified in place since the forward
+        if ctx.rast.generation != ctx.generation:
+            # another render has used the workspace since: rebuild this render's state
+            ctx.rast.forward(ctx.scene, ctx.cam, feat=ctx.want_feat)
+
         def c(g):
             return None if g is None else g.contiguous().float()
         gr = ctx.rast.backward(ctx.scene, ctx.cam, c(g_rgb), c(g_depth), c(g_alpha),
@@ -76,7 +94,7 @@ class GSRenderFunction(torch.autograd.Function):
             gfe = gr["feats"] if gr["feats"] is not None else torch.zeros_like(ctx.scene.feats, dtype=torch.float32)
             gfe = gfe.to(ctx.feat_dtype)
         return (gr["means"], gr["scales"], gr["quats"], gr["opacities"], gr["sh"], gfe,
-                gr["pose"].to(torch.float32), None, None)
+                gr["pose"].to(device=ctx.xi_device, dtype=torch.float32), None, None)
 
 
 def render(means, scales, quats, opacities, sh, feats, cam, xi=None, rasterizer=None):

@@ -93,6 +93,10 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   if (c->W <= 0 || c->H <= 0 || c->tile != kTile || !(c->fx > 0.f) || !(c->fy > 0.f) ||
       !(c->near_z > 0.f) || c->stride != 1 || c->off_x != 0 || c->off_y != 0)
     return GS_ERR_ARG;
+  // size limits first, so that the tile counts below cannot overflow an int
+  if (scene->n > kNaMaxGauss || c->W > kNaMaxPix || c->H > kNaMaxPix ||
+      (int64_t)c->W * c->H > kNaMaxPix)
+    return GS_ERR_OVER_BUDGET;
   CamDev cd;
   cd.W = c->W;
   cd.H = c->H;
@@ -111,8 +115,7 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   cd.GW = cd.W;
   cd.GH = cd.H;
   const int64_t ntl = (int64_t)cd.TX * cd.TY;
-  if (scene->n > kNaMaxGauss || (int64_t)c->W * c->H > kNaMaxPix || ntl > kNaMaxTiles)
-    return GS_ERR_OVER_BUDGET;
+  if (ntl > kNaMaxTiles) return GS_ERR_OVER_BUDGET;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
@@ -150,6 +153,8 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
       cudaStreamSynchronize(st) != cudaSuccess)
     return GS_ERR_CUDA;
   const int64_t I = h_cnt[kCntInst];
+  // too many tile instances: nothing is written; the tile counts the projection added are
+  // cleared by the next call, like every other value that must start at zero
   if (I > kNaMaxInst) return GS_ERR_OVER_BUDGET;
   BinArgs b;
   b.n = scene->n;

@@ -24,12 +24,18 @@ def grid_shape(cam):
 
 
 class Rasterizer:
-    """One workspace on one device.  Not thread-safe; one stream order at a time."""
+    """One workspace on one device.  Not thread-safe; one stream order at a time.
+
+    The workspace holds the state of the most recent forward (projection, tile lists,
+    per-pixel transmittance and last-contributor counts), which ``backward`` consumes.
+    ``generation`` counts the forwards, so that a caller holding an older forward can tell
+    that the workspace has moved on (the autograd function then recomputes its forward)."""
 
     def __init__(self, device=None):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self.ws = L.Workspace(self.device.index)
+        self.generation = 0
 
     def reserve(self, n_gauss, n_instances, n_pixels):
         L.gs_workspace_reserve(self.ws, n_gauss, n_instances, n_pixels)
@@ -45,6 +51,7 @@ class Rasterizer:
             out = dict(rgb=torch.empty((3, H, W), device=dev), depth=torch.empty((H, W), device=dev),
                        alpha=torch.empty((H, W), device=dev),
                        feat=torch.empty((scene.n_feat, H, W), device=dev) if feat and scene.n_feat else None)
+        self.generation += 1
         L.gs_project(scene, c, self.ws, stream)
         n_inst = L.gs_bin_tiles(self.ws, sync, stream)
         L.gs_render_fwd(scene, c, self.ws, out["rgb"], out["depth"], out["alpha"], out.get("feat"),

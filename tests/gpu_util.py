@@ -56,3 +56,71 @@ def max_abs_unflagged(gpu, ref, flags):
     d = np.abs(np.asarray(gpu, np.float64) - np.asarray(ref, np.float64))
     d = d[..., ok] if d.ndim == flags.ndim + 1 else d[ok]
     return float(d.max()) if d.size else 0.0
+
+
+# ---------------------------------------------------------------- element-wise gradient gates
+#
+# A pixel the oracle flags (one of its blend decisions -- sigma < 0, alpha against 1/255 or
+# 0.99, T(1 - alpha) against 1e-4 -- lies within rounding distance of its threshold) may take
+# the other branch on the GPU.  Its contribution to every gradient is linear in its upstream
+# gradient, so zeroing the upstream gradient at the flagged pixels, on both sides, removes it
+# exactly from every Gaussian's gradient and from the pose's.  Nothing else is excluded: every
+# entry of every gradient tensor is then compared one by one.
+
+GRAD_RTOL = 1e-3      # per entry, relative to the reference entry
+GRAD_FLOOR = 1e-5     # per entry, absolute floor as a fraction of the tensor's largest entry
+
+
+def mask_flagged(grads, flags):
+    """Upstream gradients (name -> [C, H, W] or [H, W] image) with the pixels the oracle
+    flags ([H, W]) zeroed.  Returns (masked copies, number of flagged pixels)."""
+    bad = np.asarray(flags) != 0
+    out = {}
+    for k, v in grads.items():
+        a = np.array(v, copy=True)
+        a[..., bad] = 0
+        out[k] = a
+    return out, int(bad.sum())
+
+
+def grad_violations(got, ref, rtol=GRAD_RTOL, floor=GRAD_FLOOR):
+    """Entries with |got - ref| > rtol |ref| + floor max|ref|: (count, worst ratio of the
+    error to its bound, number of entries compared)."""
+    g = np.asarray(got, np.float64).reshape(-1)
+    r = np.asarray(ref, np.float64).reshape(-1)
+    if r.size == 0:
+        return 0, 0.0, 0
+    bound = rtol * np.abs(r) + floor * max(np.abs(r).max(), 1e-30)
+    err = np.abs(g - r)
+    ratio = err / bound
+    return int((err > bound).sum()), float(ratio.max()), int(r.size)
+
+
+def assert_grads_close(got, ref, keys, rtol=GRAD_RTOL, floor=GRAD_FLOOR, norm_tol=1e-3, label=""):
+    """Every entry of every gradient within its bound, and the relative Frobenius error of
+    each tensor within ``norm_tol``.  Returns {key: (violations, worst ratio, entries)}."""
+    stats, bad = {}, []
+    for k in keys:
+        g, r = got[k], ref[k]
+        if g is None and r is None:
+            continue
+        n, worst, m = grad_violations(g, r, rtol, floor)
+        rel = rel_err(g, r)
+        stats[k] = (n, worst, m)
+        if n or rel > norm_tol:
+            bad.append((k, f"{n}/{m} entries over the bound (worst {worst:.3g}x)", f"rel {rel:.3g}"))
+    _report(label, stats)
+    assert not bad, (label, bad)
+    return stats
+
+
+def _report(label, stats):
+    """Append the per-tensor comparison to $GS_PARITY_REPORT (JSON lines) when set."""
+    import json
+    import os
+    path = os.environ.get("GS_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"case": label, "grads": {k: {"violations": v[0], "worst": v[1],
+                                                             "entries": v[2]}
+                                                         for k, v in stats.items()}}) + "\n")

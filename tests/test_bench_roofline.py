@@ -59,3 +59,21 @@ def test_hbm_bound_dominant_stage_and_missing_capture():
     assert r["frac"] == pytest.approx(r["achieved"] / peaks["hbm_gbs"], rel=1e-3)
     assert r["peak_source"] == src
     assert r["traffic"] is None   # no capture recorded for this workload
+
+
+def test_measured_fp32_peak_is_the_alu_denominator():
+    import bench
+    steps = 3
+    stage = _stage({"fwd": 0.07, "bwd_raster": 0.18, "bin": 0.05}, steps)
+    sb = {"fwd": 40e6 * steps, "bwd_raster": 50e6 * steps, "bin": 6e6 * steps}
+    sf = {"fwd": 0.8e9 * steps, "bwd_raster": 2e9 * steps, "bin": 0.0}
+    fp32 = {"tflops": 70.0, "sm_mhz": 1900.0}
+    r = bench.build_roofline(stage, sb, sf, (0, 0), steps, "no_such_workload", fp32, 2000.0)
+    achieved = 2e9 / 0.18e-3 / 1e12
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(70.0)
+    assert r["peak_source"].startswith("measured")
+    assert r["frac"] == pytest.approx(achieved / 70.0, rel=1e-3)
+    assert r["alu_frac"] == pytest.approx(achieved / 70.0, rel=1e-3)
+    # the same fraction against the peak scaled to the clock the kernel ran at
+    assert r["alu_frac_at_kernel_clock"] == pytest.approx(achieved / (70.0 * 2000 / 1900), rel=1e-3)
+    assert r["stage_kcycles"] == pytest.approx(0.18 * 2000.0, rel=1e-3)

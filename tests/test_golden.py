@@ -6,7 +6,8 @@ Gaussian across the image edge and one in front of the near plane.
 On the CPU the oracle must still reproduce the stored values (a change of the oracle's
 arithmetic shows here).  On the GPU the CUDA path must match them within the parity
 tolerances: forward max-abs 1e-4 and last-contributor counts bit-exact at the sampled
-pixels, gradients within relative 1e-3."""
+pixels, every gradient entry within 1e-3 of its stored value plus 1e-5 of the tensor's
+largest entry (no pixel of the scene is near a blend threshold, so nothing is masked)."""
 import json
 import os
 import sys
@@ -73,5 +74,5 @@ def test_cuda_path_matches_the_fixture(golden):
     T, nc = L.gs_get_pixel_state(gpu["rast"].ws, cam.H, cam.W)
     np.testing.assert_array_equal(nc.reshape(-1)[pix], golden["n_contrib"])
     assert np.abs(T.reshape(-1)[pix] - np.array(golden["forward"]["T_final"])).max() <= 1e-4
-    for k in GRAD_KEYS:
-        assert U.rel_err(gpu["grads"][k], np.array(golden["grads"][k])) <= 1e-3, k
+    U.assert_grads_close(gpu["grads"], {k: np.array(golden["grads"][k]) for k in GRAD_KEYS},
+                         GRAD_KEYS, label="golden hand scene 40x28 (FP64 fixture)")

@@ -80,9 +80,12 @@ def test_mix_equals_alone():
         assert res["instances"] == alone["instances"]
         if gin is not None:
             ga = rast.backward(tensors[s], cam, gin["rgb"], gin["depth"], gin["alpha"], gin["feat"])
-            for k in ("means", "scales", "quats", "opacities", "sh", "feats", "pose"):
-                if gout[k] is not None:
-                    assert U.rel_err(gout[k].cpu().numpy(), ga[k].cpu().numpy()) <= 1e-3, k
+            keys = [k for k in ("means", "scales", "quats", "opacities", "sh", "feats", "pose")
+                    if gout[k] is not None]
+            # same kernels, another atomic order: every entry within the gradient bound
+            U.assert_grads_close({k: gout[k].cpu().numpy() for k in keys},
+                                 {k: ga[k].cpu().numpy() for k in keys}, keys,
+                                 label="served in the mix vs alone")
     server.close()
 
 
