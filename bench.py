@@ -43,6 +43,13 @@ WORKLOADS = {
                                 desc="room 3M Gaussians, SH0, 32 fp32 feats, 3840x2160, fx=3600, "
                                      "per-tile recomputation (no stored blend lists)",
                                 cpu_mode=0, cpu_tiles=64),
+    # the memory form's kernels (32 fp32 channels, every gradient) at a size a full ncu
+    # capture can take (about 2 GB on the device); profiling size, not a headline
+    "memory_1920x1080_1m": dict(make=lambda: (S.room_scene(1_000_000, n_feat=32, sh_degree=0),
+                                              S.room_trajectory(10, 1920, 1080, 1800.0)),
+                                bf16=False, l1=False, cpu_mode=0, cpu_tiles=64,
+                                desc="room 1M Gaussians, SH0, 32 fp32 feats, 1920x1080, fx=1800 "
+                                     "(profiling size of the memory form)"),
 }
 # Semantic distillation phase (Sec. 3.2, App. D): grid-sampled rendering with random offsets,
 # region-indexed targets, the masked L1 + cosine loss fused into the forward, and the

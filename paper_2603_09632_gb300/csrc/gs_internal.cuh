@@ -198,6 +198,42 @@ inline int persistent_grid(Kernel kern, int threads, size_t smem, int n_items) {
   return n_items < g ? (n_items > 0 ? n_items : 1) : g;
 }
 
+// One render in a raster launch: its camera, inputs and outputs.  A launch takes a table of
+// up to NJ of them and drains their work items through one persistent grid (serving batches
+// several requests' tiles into one launch this way; a plain render is a table of one).  Work
+// items of job k are [job[k-1].item_end, job[k].item_end) of the launch's queue, taken in
+// the job's heavy-first tile order.
+struct RasterJob {
+  CamDev cam;
+  const GaussRec* rec;
+  const void* feats;
+  int D;
+  int item_end;
+  const uint2* ranges;
+  const uint32_t* inst_id;
+  const uint32_t* order;        // heavy-first tile order, or null (row-major)
+  float *rgb, *depth, *alpha, *feat;   // forward outputs (any may be null)
+  float* T_final;               // written by the forward, read by the backward
+  uint32_t* n_contrib;
+  const float *g_rgb, *g_depth, *g_alpha, *g_feat;   // backward inputs
+  float *g2d, *g_feats;         // backward accumulators
+};
+constexpr int kMaxJobs = 8;
+template <int NJ>
+struct RasterJobs {
+  int n;
+  RasterJob job[NJ];
+  // job of work item q (q below the last item_end) and the first item of that job
+  __device__ __forceinline__ int find(uint32_t q, uint32_t* first) const {
+    int k = 0;
+    if constexpr (NJ > 1)
+      while (k < n - 1 && q >= (uint32_t)job[k].item_end) ++k;
+    *first = k > 0 ? (uint32_t)job[k - 1].item_end : 0u;
+    return k;
+  }
+  __device__ __forceinline__ uint32_t items() const { return (uint32_t)job[NJ > 1 ? n - 1 : 0].item_end; }
+};
+
 // gs_raster_fwd.cu
 // Masked L1 + cosine feature loss (App. D) fused into the forward's epilogue; inactive
 // when target is null.  Per sample p with a = V_p G_hat[:, p], b = V_p G*[:, p]:
@@ -219,9 +255,21 @@ void launch_raster_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* r
                        float* T_final, uint32_t* n_contrib, const FeatLoss* loss,
                        cudaStream_t st);
 
+// Forward raster of a table of n <= kMaxJobs jobs that share one feature layout (padded
+// channel count and dtype) in one persistent launch; item_end counts half tiles (two per
+// tile).  No fused loss.
+void launch_raster_fwd_jobs(const RasterJob* jobs, int n, int feat_dtype, bool want_feat,
+                            const TileQueue& tq, cudaStream_t st);
+// Half-tile work items of the forward per tile.
+constexpr int kFwdItemsPerTile = 2;
+
 // gs_raster_bwd.cu
 // Accumulators per Gaussian: g2d[12*i + k], k = u, v, A, B, C, o, r, g, b, z
 constexpr int kG2D = 12;
+// Backward raster of a table of n <= kMaxJobs jobs (every gradient; item_end counts tiles;
+// the queue is zeroed by the caller).
+void launch_raster_bwd_jobs(const RasterJob* jobs, int n, int feat_dtype, bool want_feat,
+                            const TileQueue& tq, cudaStream_t st);
 void launch_raster_bwd(const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
                        const void* feats, int feat_dtype,
                        int D, const uint2* ranges, const uint32_t* inst_id, const float* T_final,

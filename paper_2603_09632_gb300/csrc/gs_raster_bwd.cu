@@ -26,6 +26,8 @@
 // frozen): only dL/df_i = sum_p w_i g_F is needed, so phase 1 keeps just the weights, the
 // features themselves are not fetched, and phase 2b and every geometry accumulator are
 // skipped.
+#include <algorithm>
+
 #include "gs_blend.cuh"
 #include "gs_internal.cuh"
 
@@ -139,15 +141,11 @@ __device__ __forceinline__ void red_add4(float* dst, float a, float b, float c, 
   atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a, b, c, d));
 }
 
-template <int DP, bool BF16, bool FO>
+// J: the renders of this launch (one for a plain backward, up to kMaxJobs for a serving
+// batch); their tiles are taken from one queue.
+template <int DP, bool BF16, bool FO, int NJ>
 __global__ void __launch_bounds__(kT, (BwdCfg<DP, FO>::CTAS))
-k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
-             const void* __restrict__ feats, int D,
-             const uint2* __restrict__ ranges, const uint32_t* __restrict__ inst_id,
-             const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
-             const float* __restrict__ g_rgb, const float* __restrict__ g_depth,
-             const float* __restrict__ g_alpha, const float* __restrict__ g_feat,
-             float* __restrict__ g2d, float* __restrict__ g_feats) {
+k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
   using Cfg = BwdCfg<DP, FO>;
   constexpr int B = Cfg::B;
   __shared__ float4 s_r0[kT], s_r1[kT], s_r2[kT];   // compacted records of the chunk
@@ -166,16 +164,37 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   float* s_outF = s_fb + (FO ? 0 : 2) * B * DP;   // [NPART][B][DP] partial sums
 
   const int t = threadIdx.x;
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_job;
   // persistent CTA: tiles from the queue, heaviest first
   for (;;) {
     if (t == 0) {
       const uint32_t q = atomicAdd(tq.head, 1u);
-      s_tile = q < (uint32_t)tq.n_tiles ? (int)(tq.order ? tq.order[q] : q) : -1;
+      s_tile = -1;
+      if (q < J.items()) {
+        uint32_t first;
+        const int k = J.find(q, &first);
+        const uint32_t local = q - first;
+        const uint32_t* order = J.job[k].order;
+        s_tile = (int)(order ? order[local] : local);
+        s_job = k;
+      }
     }
     __syncthreads();
     const int tile = s_tile;
     if (tile < 0) break;
+    const RasterJob& jb = J.job[NJ > 1 ? s_job : 0];
+    const CamDev& cam = jb.cam;
+    const GaussRec* __restrict__ rec = jb.rec;
+    const void* __restrict__ feats = jb.feats;
+    const int D = jb.D;
+    const uint2* __restrict__ ranges = jb.ranges;
+    const uint32_t* __restrict__ inst_id = jb.inst_id;
+    const float* __restrict__ T_final = jb.T_final;
+    const uint32_t* __restrict__ n_contrib = jb.n_contrib;
+    const float *__restrict__ g_rgb = jb.g_rgb, *__restrict__ g_depth = jb.g_depth;
+    const float *__restrict__ g_alpha = jb.g_alpha, *__restrict__ g_feat = jb.g_feat;
+    float* __restrict__ g2d = jb.g2d;
+    float* __restrict__ g_feats = jb.g_feats;
     const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile;
     const int px = tx0 + strip_px(t), py = ty0 + strip_py(t);
     const bool inside = px < cam.W && py < cam.H;
@@ -523,44 +542,40 @@ k_raster_bwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   }
 }
 
-template <int DP, bool BF16, bool FO>
-void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const void* feats, int D,
-              const uint2* ranges, const uint32_t* inst_id, const float* T_final,
-              const uint32_t* n_contrib, const float* g_rgb, const float* g_depth,
-              const float* g_alpha, const float* g_feat, float* g2d, float* g_feats,
-              cudaStream_t st) {
+template <int DP, bool BF16, bool FO, int NJ>
+void launch_t(const RasterJobs<NJ>& jobs, const TileQueue& tq, cudaStream_t st) {
   const size_t smem = sizeof(float) * BwdCfg<DP, FO>::smem_floats;
-  auto kern = k_raster_bwd<DP, BF16, FO>;
-  const int grid = persistent_grid(kern, kT, smem, tq.n_tiles);
-  kern<<<grid, kT, smem, st>>>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,
-                               g_depth, g_alpha, g_feat, g2d, g_feats);
+  auto kern = k_raster_bwd<DP, BF16, FO, NJ>;
+  const int items = jobs.job[NJ > 1 ? jobs.n - 1 : 0].item_end;
+  const int grid = persistent_grid(kern, kT, smem, items);
+  kern<<<grid, kT, smem, st>>>(jobs, tq);
   note_launch();
 }
 
 // Dispatch of the run-time options to the kernel variants (features-only needs features).
 template <int DP>
-void launch_dp(bool bf, bool fo, const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-               const void* feats, int D, const uint2* ranges, const uint32_t* inst_id,
-               const float* T_final, const uint32_t* n_contrib, const float* g_rgb,
-               const float* g_depth, const float* g_alpha, const float* g_feat, float* g2d,
-               float* g_feats, cudaStream_t st) {
+void launch_dp(bool bf, bool fo, const RasterJobs<1>& jobs, const TileQueue& tq, cudaStream_t st) {
   if constexpr (DP > 0) {
     if (fo) {
       if (bf)
-        launch_t<DP, true, true>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib,
-                                 g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
+        launch_t<DP, true, true, 1>(jobs, tq, st);
       else
-        launch_t<DP, false, true>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib,
-                                  g_rgb, g_depth, g_alpha, g_feat, g2d, g_feats, st);
+        launch_t<DP, false, true, 1>(jobs, tq, st);
       return;
     }
   }
   if (bf)
-    launch_t<DP, true, false>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,
-                              g_depth, g_alpha, g_feat, g2d, g_feats, st);
+    launch_t<DP, true, false, 1>(jobs, tq, st);
   else
-    launch_t<DP, false, false>(cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb,
-                               g_depth, g_alpha, g_feat, g2d, g_feats, st);
+    launch_t<DP, false, false, 1>(jobs, tq, st);
+}
+
+template <int DP>
+void launch_dp_jobs(bool bf, const RasterJobs<kMaxJobs>& jobs, const TileQueue& tq, cudaStream_t st) {
+  if (bf)
+    launch_t<DP, true, false, kMaxJobs>(jobs, tq, st);
+  else
+    launch_t<DP, false, false, kMaxJobs>(jobs, tq, st);
 }
 
 }  // namespace
@@ -575,9 +590,50 @@ void launch_raster_bwd(const CamDev& cam, const TileQueue& tq, const GaussRec* r
   const bool bf = feat_dtype == GS_BF16;
   const int DP = g_feat ? padded_feat(D) : 0;
   const bool fo = features_only && DP > 0 && g_feats;
-#define GS_BWD(dp)                                                                         \
-  launch_dp<dp>(bf, fo, cam, tq, rec, feats, D, ranges, inst_id, T_final, n_contrib, g_rgb, \
-                g_depth, g_alpha, g_feat, g2d, g_feats, st)
+  RasterJobs<1> jobs{};
+  jobs.n = 1;
+  RasterJob& j = jobs.job[0];
+  j.cam = cam;
+  j.rec = rec;
+  j.feats = feats;
+  j.D = D;
+  j.item_end = tq.n_tiles;
+  j.ranges = ranges;
+  j.inst_id = inst_id;
+  j.order = tq.order;
+  j.T_final = const_cast<float*>(T_final);
+  j.n_contrib = const_cast<uint32_t*>(n_contrib);
+  j.g_rgb = g_rgb;
+  j.g_depth = g_depth;
+  j.g_alpha = g_alpha;
+  j.g_feat = g_feat;
+  j.g2d = g2d;
+  j.g_feats = g_feats;
+#define GS_BWD(dp) launch_dp<dp>(bf, fo, jobs, tq, st)
+  switch (DP) {
+    case 0: GS_BWD(0); break;
+    case 8: GS_BWD(8); break;
+    case 16: GS_BWD(16); break;
+    case 32: GS_BWD(32); break;
+    default: GS_BWD(64); break;
+  }
+#undef GS_BWD
+}
+
+void launch_raster_bwd_jobs(const RasterJob* src, int n, int feat_dtype, bool want_feat,
+                            const TileQueue& tq, cudaStream_t st) {
+  if (n <= 0 || n > kMaxJobs) return;
+  RasterJobs<kMaxJobs> jobs{};
+  jobs.n = n;
+  int Dmax = 0;
+  for (int k = 0; k < n; ++k) {
+    jobs.job[k] = src[k];
+    Dmax = std::max(Dmax, src[k].D);
+  }
+  if (jobs.job[n - 1].item_end <= 0) return;
+  const bool bf = feat_dtype == GS_BF16;
+  const int DP = want_feat ? padded_feat(Dmax) : 0;
+#define GS_BWD(dp) launch_dp_jobs<dp>(bf, jobs, tq, st)
   switch (DP) {
     case 0: GS_BWD(0); break;
     case 8: GS_BWD(8); break;

@@ -10,6 +10,8 @@
 // only the batch entries that can reach it (ballot over a per-strip box test), stops when
 // all its pixels have terminated (checked before each group of 32 candidates), and the
 // CTA stops when all 128 pixels have.
+#include <algorithm>
+
 #include "gs_blend.cuh"
 #include "gs_internal.cuh"
 
@@ -67,34 +69,47 @@ __device__ __forceinline__ void stage_features(const void* __restrict__ feats, i
 
 // Resident CTAs per SM by channel count, the most whose register share (80, 96, 128) holds
 // the kernel without spills: 6 up to 16 channels, 5 at 32, 4 at 64.
-template <int DP, bool BF16, bool LOSS>
+static_assert(kSplit == kFwdItemsPerTile, "work items per tile");
+
+// J: the renders of this launch (one for a plain render, up to kMaxJobs for a serving
+// batch); their half tiles are taken from one queue.
+template <int DP, bool BF16, bool LOSS, int NJ>
 __global__ void __launch_bounds__(kB, DP <= 16 ? 6 : (DP <= 32 ? 5 : 4))
-k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
-             const void* __restrict__ feats, int D, const uint2* __restrict__ ranges,
-             const uint32_t* __restrict__ inst_id, float* __restrict__ rgb,
-             float* __restrict__ depth, float* __restrict__ alpha, float* __restrict__ feat,
-             float* __restrict__ T_final, uint32_t* __restrict__ n_contrib, FeatLoss fl) {
+k_raster_fwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq, FeatLoss fl) {
   __shared__ float4 s_r0[kB], s_r1[kB], s_r2[kB];
   __shared__ uint32_t s_id[kB];
   __shared__ int s_orig[kB];
   __shared__ int s_wc[kB / 32];
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_job;
   extern __shared__ __align__(16) float s_feat[];   // [kB][DP]
   double l1_sum = 0.0, cos_sum = 0.0;   // fused loss (LOSS): this thread's samples, all tiles
 
   // persistent CTA: tiles from the queue, heaviest first
   for (;;) {
     if (threadIdx.x == 0) {
-      // work item q: part (q mod kSplit) of the (q / kSplit)-th tile in heavy-first order
+      // work item q: part (local mod kSplit) of the (local / kSplit)-th tile of its job in
+      // heavy-first order, local = q - the job's first item
       const uint32_t q = atomicAdd(tq.head, 1u);
-      const uint32_t r = q / kSplit;
-      s_tile = q < (uint32_t)kSplit * (uint32_t)tq.n_tiles
-                   ? kSplit * (int)(tq.order ? tq.order[r] : r) + (int)(q - r * kSplit)
-                   : -1;
+      s_tile = -1;
+      if (q < J.items()) {
+        uint32_t first;
+        const int k = J.find(q, &first);
+        const uint32_t local = q - first, r = local / kSplit;
+        const uint32_t* order = J.job[k].order;
+        s_tile = kSplit * (int)(order ? order[r] : r) + (int)(local - r * kSplit);
+        s_job = k;
+      }
     }
     __syncthreads();
     const int item = s_tile;
     if (item < 0) break;
+    const RasterJob& jb = J.job[NJ > 1 ? s_job : 0];
+    const CamDev& cam = jb.cam;
+    const GaussRec* __restrict__ rec = jb.rec;
+    const void* __restrict__ feats = jb.feats;
+    const int D = jb.D;
+    const uint2* __restrict__ ranges = jb.ranges;
+    const uint32_t* __restrict__ inst_id = jb.inst_id;
     const int tile = item / kSplit;
 
     const int tx0 = (tile % cam.TX) * kTile, ty0 = (tile / cam.TX) * kTile + kRowsB * (item % kSplit);
@@ -200,6 +215,7 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
       if (lastj >= 0) { last = s_orig[lastj] + 1; lastj = -1; }
     }
     if (inside) {
+      float *rgb = jb.rgb, *depth = jb.depth, *alpha = jb.alpha, *feat = jb.feat;
       const int64_t HW = (int64_t)cam.W * cam.H;
       const int64_t p = (int64_t)py * cam.W + px;
       if (rgb) {
@@ -216,8 +232,8 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
             if (c < D) feat[c * HW + p] = acc[c];
         }
       }
-      T_final[p] = T;
-      n_contrib[p] = (uint32_t)last;
+      jb.T_final[p] = T;
+      jb.n_contrib[p] = (uint32_t)last;
     }
     if constexpr (LOSS) {
       // Masked L1 + cosine loss of each sample and its gradient w.r.t. G_hat.  The
@@ -289,42 +305,42 @@ k_raster_fwd(CamDev cam, TileQueue tq, const GaussRec* __restrict__ rec,
   }
 }
 
-template <int DP, bool BF16, bool LOSS>
-void launch_t(const CamDev& cam, const TileQueue& tq, const GaussRec* rec, const void* feats, int D,
-              const uint2* ranges, const uint32_t* inst_id, float* rgb, float* depth, float* alpha,
-              float* feat, float* T_final, uint32_t* n_contrib, const FeatLoss& fl,
-              cudaStream_t st) {
+template <int DP, bool BF16, bool LOSS, int NJ>
+void launch_t(const RasterJobs<NJ>& jobs, const TileQueue& tq, const FeatLoss& fl, cudaStream_t st) {
   const size_t smem = sizeof(float) * kB * DP;
-  auto kern = k_raster_fwd<DP, BF16, LOSS>;
-  const int grid = persistent_grid(kern, kB, smem, kSplit * tq.n_tiles);
-  kern<<<grid, kB, smem, st>>>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
-                               T_final, n_contrib, fl);
+  auto kern = k_raster_fwd<DP, BF16, LOSS, NJ>;
+  const int items = jobs.job[NJ > 1 ? jobs.n - 1 : 0].item_end;
+  const int grid = persistent_grid(kern, kB, smem, items);
+  kern<<<grid, kB, smem, st>>>(jobs, tq, fl);
   note_launch();
 }
 
 // Dispatch of the run-time options to the kernel variants (the loss needs features).
 template <int DP>
-void launch_dp(bool bf, bool loss, const CamDev& cam, const TileQueue& tq, const GaussRec* rec,
-               const void* feats, int D, const uint2* ranges, const uint32_t* inst_id, float* rgb,
-               float* depth, float* alpha, float* feat, float* T_final, uint32_t* n_contrib,
+void launch_dp(bool bf, bool loss, const RasterJobs<1>& jobs, const TileQueue& tq,
                const FeatLoss& fl, cudaStream_t st) {
   if constexpr (DP > 0) {
     if (loss) {
       if (bf)
-        launch_t<DP, true, true>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
-                                 T_final, n_contrib, fl, st);
+        launch_t<DP, true, true, 1>(jobs, tq, fl, st);
       else
-        launch_t<DP, false, true>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
-                                  T_final, n_contrib, fl, st);
+        launch_t<DP, false, true, 1>(jobs, tq, fl, st);
       return;
     }
   }
   if (bf)
-    launch_t<DP, true, false>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
-                              T_final, n_contrib, fl, st);
+    launch_t<DP, true, false, 1>(jobs, tq, fl, st);
   else
-    launch_t<DP, false, false>(cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat,
-                               T_final, n_contrib, fl, st);
+    launch_t<DP, false, false, 1>(jobs, tq, fl, st);
+}
+
+template <int DP>
+void launch_dp_jobs(bool bf, const RasterJobs<kMaxJobs>& jobs, const TileQueue& tq, cudaStream_t st) {
+  const FeatLoss fl{};
+  if (bf)
+    launch_t<DP, true, false, kMaxJobs>(jobs, tq, fl, st);
+  else
+    launch_t<DP, false, false, kMaxJobs>(jobs, tq, fl, st);
 }
 
 }  // namespace
@@ -349,9 +365,48 @@ void launch_raster_fwd(const CamDev& cam, const TileQueue& tq, const GaussRec* r
   // features are blended when written or when the fused loss needs them
   const int DP = (feat || fl.target) ? padded_feat(D) : 0;
   const bool loss_on = fl.target != nullptr;
-#define GS_FWD(dp)                                                                           \
-  launch_dp<dp>(bf, loss_on, cam, tq, rec, feats, D, ranges, inst_id, rgb, depth, alpha, feat, \
-                T_final, n_contrib, fl, st)
+  RasterJobs<1> jobs{};
+  jobs.n = 1;
+  RasterJob& j = jobs.job[0];
+  j.cam = cam;
+  j.rec = rec;
+  j.feats = feats;
+  j.D = D;
+  j.item_end = kSplit * tq.n_tiles;
+  j.ranges = ranges;
+  j.inst_id = inst_id;
+  j.order = tq.order;
+  j.rgb = rgb;
+  j.depth = depth;
+  j.alpha = alpha;
+  j.feat = feat;
+  j.T_final = T_final;
+  j.n_contrib = n_contrib;
+#define GS_FWD(dp) launch_dp<dp>(bf, loss_on, jobs, tq, fl, st)
+  switch (DP) {
+    case 0: GS_FWD(0); break;
+    case 8: GS_FWD(8); break;
+    case 16: GS_FWD(16); break;
+    case 32: GS_FWD(32); break;
+    default: GS_FWD(64); break;
+  }
+#undef GS_FWD
+}
+
+void launch_raster_fwd_jobs(const RasterJob* src, int n, int feat_dtype, bool want_feat,
+                            const TileQueue& tq, cudaStream_t st) {
+  if (n <= 0 || n > kMaxJobs) return;
+  RasterJobs<kMaxJobs> jobs{};
+  jobs.n = n;
+  int Dmax = 0;
+  for (int k = 0; k < n; ++k) {
+    jobs.job[k] = src[k];
+    Dmax = std::max(Dmax, src[k].D);
+  }
+  if (jobs.job[n - 1].item_end <= 0) return;
+  const bool bf = feat_dtype == GS_BF16;
+  const int DP = want_feat ? padded_feat(Dmax) : 0;
+#define GS_FWD(dp) launch_dp_jobs<dp>(bf, jobs, tq, st)
   switch (DP) {
     case 0: GS_FWD(0); break;
     case 8: GS_FWD(8); break;
