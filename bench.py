@@ -533,6 +533,10 @@ def run_gpu(args):
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roofline,
         "fp32_peak": fp32, "memory": memory, "device_status": L.status_string(status),
     }
+    if rank == 0 and not args.no_serve:
+        # p50/p99 serve latency next to the throughput: the serving mix at saturation (2x
+        # the plain arm's capacity), both arms on the same arrivals
+        line["serve"] = serve_summary(serve_measure(args, dev, local, (SERVE_SAT,)))
     if rank == 0 and not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(args, scene_np, cams, target_budget_s=args.cpu_budget,
                                             mode=wl.get("cpu_mode", 1))
@@ -1015,6 +1019,7 @@ def run_reference(args):
 
 
 SERVE_RATES = (0.25, 0.5, 1.0, 1.5, 2.0)
+SERVE_SAT = 2.0   # the rate of the serving summary in the main line (x plain capacity)
 
 
 def wait_until(t):
@@ -1031,27 +1036,24 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, np.float64), q)) if len(xs) else float("nan")
 
 
-def run_serve(args):
+def serve_measure(args, dev, local, rates):
     """Serving mix: 8 resident scenes (100k-2M Gaussians, SH = id mod 4, 16/32/64 bf16
     feature channels), Poisson arrivals of single-pose requests at resolutions drawn from
     {256x256, 640x480, 1200x680, 1920x1080}, 30 % with backward.  Two arms on the same
     request sequence and arrival times:
       plain: one request at a time through gs_project -> gs_bin_tiles -> gs_render_fwd
              (-> gs_render_bwd) on one stream, synchronised per request;
-      serve: the serving loop (gs_serve_submit / gs_serve_poll) with --serve-slots slots.
-    The rate is swept from 0.25x to 2x the plain arm's closed-loop capacity.  Latency runs
+      serve: the serving loop (gs_serve_submit / gs_serve_poll) with --serve-slots slots:
+             batches of requests projected together, admitted by their real tile-instance
+             counts and rendered by shared persistent raster launches.
+    The rate is given as multiples of the plain arm's closed-loop capacity.  Latency runs
     from the scheduled arrival to poll-visible completion (so time a request waits for a
     client buffer counts); throughput is served pixels over first arrival -> last
-    completion."""
+    completion.  Returns the measurement as a dict."""
     import torch
     from paper_2603_09632_gb300 import _lib as L
     from paper_2603_09632_gb300.render import as_camera
 
-    rank, world, local = env_rank()
-    if rank != 0:
-        return
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     scenes_np = S.serving_scenes(scale=args.serve_scale)
     scenes = []
     for sc in scenes_np:
@@ -1202,7 +1204,7 @@ def run_serve(args):
 
     serve_open(cap_rps, min(len(reqs), 4 * args.serve_slots))     # warm the slots
     rows = []
-    for x in SERVE_RATES:
+    for x in rates:
         rate = x * cap_rps
         lp, tp = plain_open(rate)
         ls, tsv = serve_open(rate)
@@ -1213,20 +1215,45 @@ def run_serve(args):
                      "serve": {"mpix_s": round(px / tsv / 1e6, 2), "p50_ms": round(1e3 * _pct(ls, 50), 3),
                                "p99_ms": round(1e3 * _pct(ls, 99), 3)}})
     info = L.gs_serve_info(server)
+    stats = L.gs_serve_stats(server)
     server.close()
-    top = rows[-1]
-    line = {"metric": "serving Mpix/s with p50/p99 latency, mixed scenes/resolutions, 30% fwd+bwd",
-            "value": top["serve"]["mpix_s"], "unit": "Mpix/s", "n_gpus": 1,
-            "higher_is_better": True, "dtype": "f32 (bf16 features)", "data": "synthetic",
-            "plain_capacity": {"rps": round(cap_rps, 2), "mpix_s": round(cap_mpix, 2), "requests": m},
-            "sweep": rows,
+    return {"plain_capacity": {"rps": round(cap_rps, 2), "mpix_s": round(cap_mpix, 2), "requests": m},
+            "sweep": rows, "server": dict(info, **stats),
             "config": {"workload": "serve_mix_8_scenes", "scenes": [
                 {"n": sc.n, "sh": sc.sh_degree, "feat": sc.n_feat} for sc in scenes_np],
                 "requests": len(reqs), "slots": args.serve_slots,
                 "budget_gb": args.serve_budget_gb, "client_buffer_sets": n_sets,
                 "resolutions": sorted({(c.W, c.H) for _, _, c, _ in reqs}),
-                "bwd_fraction": round(sum(r[3] for r in reqs) / len(reqs), 3)},
-            "server": info}
+                "bwd_fraction": round(sum(r[3] for r in reqs) / len(reqs), 3)}}
+
+
+def serve_summary(res):
+    """Serving figures at the highest swept rate: both arms' Mpix/s and p50/p99 latency."""
+    top = res["sweep"][-1]
+    return {"rate_x_plain_capacity": top["x_capacity"], "rate_rps": top["rate_rps"],
+            "serve_mpix_s": top["serve"]["mpix_s"], "serve_p50_ms": top["serve"]["p50_ms"],
+            "serve_p99_ms": top["serve"]["p99_ms"], "plain_mpix_s": top["plain"]["mpix_s"],
+            "plain_p50_ms": top["plain"]["p50_ms"], "plain_p99_ms": top["plain"]["p99_ms"],
+            "throughput_x_plain": round(top["serve"]["mpix_s"] / max(top["plain"]["mpix_s"], 1e-9), 3),
+            "batches": res["server"]["batches"], "peak_batch": res["server"]["peak_batch"],
+            "workload": res["config"]["workload"], "requests": res["config"]["requests"]}
+
+
+def run_serve(args):
+    """The serving sweep (serve_measure) from 0.25x to 2x the plain capacity, one JSON line."""
+    import torch
+    rank, world, local = env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    res = serve_measure(args, dev, local, SERVE_RATES)
+    top = res["sweep"][-1]
+    line = {"metric": "serving Mpix/s with p50/p99 latency, mixed scenes/resolutions, 30% fwd+bwd",
+            "value": top["serve"]["mpix_s"], "unit": "Mpix/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32 (bf16 features)", "data": "synthetic",
+            "plain_capacity": res["plain_capacity"], "sweep": res["sweep"],
+            "config": res["config"], "server": res["server"], "summary": serve_summary(res)}
     print(json.dumps(line), flush=True)
 
 
@@ -1242,10 +1269,12 @@ def main():
     ap.add_argument("--cpu-tiles", type=int, default=0,
                     help="16x16 tiles per oracle sample (0: the workload's default, 300 or 64 at 4K)")
     ap.add_argument("--serve", action="store_true", help="serving-loop benchmark instead")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="leave the serving summary (p50/p99 at saturation) out of the main line")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-capacity-requests", type=int, default=100)
-    ap.add_argument("--serve-budget-gb", type=float, default=48.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=16.0)
     ap.add_argument("--serve-scale", type=float, default=1.0, help="scale of the scene sizes")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -337,15 +337,28 @@ gs_status gs_measure_fp32_peak(int iters, double* tflops_out, double* ms_out, vo
 /* ---- serving ----------------------------------------------------------------------
  *
  * Keeps several scenes resident on one GPU and renders requests (forward, optionally
- * backward) with continuous admission: each of max_slots slots is a host worker with
- * its own CUDA stream and workspace; a free slot takes the oldest pending request whose
- * device-memory estimate fits what is left of the HBM budget, so requests that arrive
- * while others run are admitted as slots and memory free up and their kernels overlap
- * on the device.  The Perceiver renders many views of the same map (tracking, mapping
- * over a keyframe window, semantic phases; Sec. 3.2, Eq. 2-3); serving is the systems
- * form of that load.  A request's results equal those of the same request rendered
- * alone (forward bit for bit; backward up to the order of atomic additions).
- * Host-side waits are bounded by the caller's timeout; no kernel waits on another. */
+ * backward) with continuous batching.  The Perceiver renders many views of the same map
+ * (tracking, mapping over a keyframe window, semantic phases; Sec. 3.2, Eq. 2-3); serving
+ * is the systems form of that load.
+ *   - Memory.  At the first submit the server divides its budget once: resident scenes,
+ *     then request workspaces (two lanes of ceil(max_slots / 2) workspaces, reserved for
+ *     the largest scene and a per-request pixel limit; together at most half of what the
+ *     scenes leave), then one arena of tile-instance buffers with the rest.  Nothing is
+ *     allocated or freed while requests run, and scenes can no longer be added.
+ *   - Admission in two phases.  A batch takes the oldest pending requests for a free
+ *     lane and projects them; each request's tile-instance count (read back once per
+ *     batch) is what it needs from the arena.  Ranges are granted in arrival order; a
+ *     request that does not fit waits at the head of the queue, and once it has waited
+ *     50 ms no request behind it is admitted before it.
+ *   - Execution.  The admitted requests are binned into their ranges and rendered by ONE
+ *     persistent forward raster launch whose queue holds every (request, tile) item of the
+ *     batch (one launch per feature layout), then one backward raster launch for those
+ *     that want gradients and their projection backward.  While one lane's batch is on
+ *     the device the other lane admits the next, so requests that arrive meanwhile start
+ *     as memory frees up and their work overlaps on the device.
+ * A request's results equal those of the same request rendered alone (forward bit for
+ * bit; backward up to the order of atomic additions).  Host-side waits are bounded by the
+ * caller's timeout; no kernel waits on another. */
 typedef struct gs_server gs_server;
 
 typedef struct {
@@ -361,28 +374,34 @@ typedef struct {
 
 typedef struct {
   gs_status status;       /* outcome of the request */
-  int32_t slot;           /* slot that ran it (-1 if it never started) */
+  int32_t slot;           /* workspace that ran it: lane x slots per lane + slot (-1: never) */
   int64_t instances;      /* tile instances of its binning */
   double queue_us;        /* submit -> start */
   double run_us;          /* start -> results ready on the device */
   double latency_us;      /* submit -> results ready */
 } gs_result;
 
-/* Create a server on `device` with a device-memory budget (bytes) shared by resident
- * scenes and in-flight requests, and max_slots (1..64) concurrent slots.
- * Errors: GS_ERR_ARG, GS_ERR_CUDA. */
+/* Create a server on `device` with a device-memory budget (bytes) for everything it holds
+ * (resident scenes, request workspaces, the instance arena) and max_slots (1..64): up to
+ * ceil(max_slots / 2) (at most 8) requests per batch on each of two lanes.  Nothing is
+ * allocated on the device until scenes are added.  Errors: GS_ERR_ARG, GS_ERR_CUDA. */
 gs_status gs_serve_create(gs_server** server, int device, int64_t hbm_budget_bytes, int max_slots);
 
 /* Cancel pending requests, wait for running ones, free everything.  NULL is a no-op. */
 void gs_serve_destroy(gs_server* server);
 
 /* Copy a scene (device pointers, as for gs_project) into server-owned device memory.
- * *scene_id receives its id.  GS_ERR_OVER_BUDGET if it does not fit the budget. */
+ * *scene_id receives its id.  GS_ERR_OVER_BUDGET if it does not fit the budget;
+ * GS_ERR_STATE once a request has been submitted (the budget is divided then);
+ * GS_ERR_ARG, GS_ERR_OOM. */
 gs_status gs_serve_add_scene(gs_server* server, const gs_scene* scene, int* scene_id);
 
 /* Queue a request; *ticket identifies it.  The request struct is copied; its buffers
- * must stay valid until the request is polled.  GS_ERR_OVER_BUDGET if its memory
- * estimate can never fit the budget; GS_ERR_ARG for an unknown scene or bad camera. */
+ * must stay valid until the request is polled.  The first submit divides the budget
+ * (see above) and may allocate.  GS_ERR_OVER_BUDGET if the image exceeds the per-request
+ * pixel limit or the budget cannot hold the workspaces; GS_ERR_ARG for an unknown scene
+ * or a bad camera (grid sampling is not served).  A request whose tile instances exceed
+ * the whole arena finishes with status GS_ERR_OVER_BUDGET. */
 gs_status gs_serve_submit(gs_server* server, const gs_request* req, uint64_t* ticket);
 
 /* Wait up to timeout_us (0: do not wait; negative: wait without limit) for a request.
@@ -391,15 +410,30 @@ gs_status gs_serve_submit(gs_server* server, const gs_request* req, uint64_t* ti
  * already released ticket. */
 gs_status gs_serve_poll(gs_server* server, uint64_t ticket, int64_t timeout_us, gs_result* result);
 
-/* Cancel a request that has not started (its result status becomes GS_ERR_CANCELLED);
- * GS_ERR_BUSY if it is running or finished. */
+/* Cancel a request that is waiting in the queue (its result status becomes
+ * GS_ERR_CANCELLED); GS_ERR_BUSY once a batch has taken it; GS_ERR_ARG for an unknown
+ * ticket or a server that has no request yet. */
 gs_status gs_serve_cancel(gs_server* server, uint64_t ticket);
 
-/* Memory held by resident scenes, admission estimate of the requests running now and
+/* Memory held by resident scenes, arena bytes granted to the requests running now and
  * its peak, and the peak number of requests running at once (any may be NULL).
  * Errors: GS_ERR_ARG (NULL server). */
 gs_status gs_serve_info(gs_server* server, int64_t* scene_bytes, int64_t* in_flight_bytes,
                         int64_t* peak_in_flight_bytes, int32_t* peak_running);
+
+typedef struct {
+  int64_t scene_bytes;       /* resident scenes */
+  int64_t workspace_bytes;   /* request workspaces and queues, reserved at the first submit */
+  int64_t arena_bytes;       /* tile-instance arena */
+  int64_t arena_peak_bytes;  /* most of it granted at once */
+  int64_t max_pixels;        /* per-request pixel limit */
+  int64_t batches;           /* batches launched */
+  int32_t lanes, slots_per_lane, peak_batch, peak_running;
+} gs_serve_stats_t;
+
+/* How the server divided its budget and how it batched: fills *out (zeros before the
+ * first submit).  Errors: GS_ERR_ARG (NULL server or out). */
+gs_status gs_serve_stats(gs_server* server, gs_serve_stats_t* out);
 
 /* ---- rendering without allocation ------------------------------------------------
  *

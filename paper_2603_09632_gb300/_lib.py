@@ -57,6 +57,13 @@ class gs_result(C.Structure):
                 ("queue_us", C.c_double), ("run_us", C.c_double), ("latency_us", C.c_double)]
 
 
+class gs_serve_stats_t(C.Structure):
+    _fields_ = [("scene_bytes", C.c_int64), ("workspace_bytes", C.c_int64), ("arena_bytes", C.c_int64),
+                ("arena_peak_bytes", C.c_int64), ("max_pixels", C.c_int64), ("batches", C.c_int64),
+                ("lanes", C.c_int32), ("slots_per_lane", C.c_int32), ("peak_batch", C.c_int32),
+                ("peak_running", C.c_int32)]
+
+
 class gs_feat_loss(C.Structure):
     _fields_ = [("target", C.c_void_p), ("mask", C.c_void_p), ("lambda_sem", C.c_float),
                 ("g_feat", C.c_void_p), ("loss", C.c_void_p)]
@@ -103,6 +110,7 @@ def _load():
         "gs_serve_poll": ([P, C.c_uint64, i64, P], st),
         "gs_serve_cancel": ([P, C.c_uint64], st),
         "gs_serve_info": ([P, P, P, P, P], st),
+        "gs_serve_stats": ([P, P], st),
         "gs_grid_target_region": ([P, i32, i32, P, i32, i32, i32, i32, i32, P, P, P], st),
         "gs_vq_weights": ([P, i64, i32, i32, P, P], st),
         "gs_vq_weights_bwd": ([P, P, i64, i32, P, P], st),
@@ -400,6 +408,13 @@ def gs_serve_info(server):
     _check(lib.gs_serve_info(server.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "gs_serve_info")
     return dict(scene_bytes=a.value, in_flight_bytes=b.value, peak_in_flight_bytes=c.value,
                 peak_running=d.value)
+
+
+def gs_serve_stats(server):
+    """How the server divided its budget (scenes, workspaces, arena) and how it batched."""
+    r = gs_serve_stats_t()
+    _check(lib.gs_serve_stats(server.h, C.byref(r)), "gs_serve_stats")
+    return {k: getattr(r, k) for k, _ in gs_serve_stats_t._fields_}
 
 
 def gs_render_fwd_noalloc(scene, cam, rgb=None, depth=None, alpha=None, feat=None, stream=None):

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "gs_internal.cuh"
+#include "gs_serve_ws.hpp"
 
 using namespace gs;
 
@@ -48,18 +49,26 @@ namespace {
 template <class T>
 struct DevBuf {
   T* p = nullptr;
-  size_t cap = 0;   // elements
+  size_t cap = 0;      // elements
+  bool owned = true;   // false: memory lent by the caller (a serving arena range)
   cudaError_t ensure(size_t n) {
     if (n <= cap) return cudaSuccess;
     // a buffer that has to grow grows by at least a quarter, so that sizes drifting upwards
     // (instance counts over a trajectory) do not reallocate (and synchronise) every call
     const size_t m = std::max<size_t>(std::max<size_t>(n, 16), cap + cap / 4);
-    if (p) cudaFree(p);
+    if (p && owned) cudaFree(p);
     p = nullptr;
     cap = 0;
+    owned = true;
     cudaError_t e = cudaMalloc(&p, m * sizeof(T));
     if (e == cudaSuccess) cap = m;
     return e;
+  }
+  void lend(T* q, size_t n) {
+    release();
+    p = q;
+    cap = n;
+    owned = false;
   }
   // as ensure(), and a (re)allocated buffer is filled with zeros
   cudaError_t ensure_zeroed(size_t n) {
@@ -68,9 +77,10 @@ struct DevBuf {
     return e == cudaSuccess ? cudaMemset(p, 0, cap * sizeof(T)) : e;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p && owned) cudaFree(p);
     p = nullptr;
     cap = 0;
+    owned = true;
   }
 };
 
@@ -703,3 +713,74 @@ gs_status gs_timing_collect(gs_workspace* ws, double* ms_out, int64_t* count_out
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- serving helpers
+// Internal (C++) interface of the serving executor (gs_serve.cu): a request's workspace is
+// reserved once, its instance buffers are ranges of the server's arena, and its raster
+// work joins a multi-request launch.
+namespace gs {
+
+gs_status ws_reserve_fixed(gs_workspace* ws, int64_t n_gauss, int64_t n_pixels, int64_t n_tiles) {
+  if (!ws || n_gauss < 0 || n_pixels < 0 || n_tiles < 0) return GS_ERR_ARG;
+  DeviceGuard g(ws->device);
+  GS_TRY(ensure_gauss(ws, n_gauss));
+  GS_TRY(ensure_pix(ws, n_pixels, n_tiles));
+  return GS_OK;
+}
+
+void ws_lend_instances(gs_workspace* ws, uint32_t* key0, uint32_t* id0, uint32_t* key1,
+                       uint32_t* id1, uint32_t* tile, int64_t cap) {
+  const size_t m = (size_t)std::max<int64_t>(cap, 0);
+  ws->inst_key.lend(key0, m);
+  ws->inst_id.lend(id0, m);
+  ws->inst_key2.lend(key1, m);
+  ws->inst_id2.lend(id1, m);
+  ws->inst_tile.lend(tile, m);
+}
+
+bool ws_fits(const gs_workspace* ws, int64_t n_gauss, int64_t n_pixels, int64_t n_tiles) {
+  return (int64_t)ws->rec.cap >= n_gauss && (int64_t)ws->T_final.cap >= n_pixels &&
+         (int64_t)ws->ranges.cap >= n_tiles;
+}
+
+gs_status ws_instances_async(gs_workspace* ws, uint32_t* host, cudaStream_t st) {
+  if (ws->stage < 1) return GS_ERR_STATE;
+  GS_TRY(cudaMemcpyAsync(host, ws->counters.p + kCntInst, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  return GS_OK;
+}
+
+gs_status ws_job(gs_workspace* ws, const gs_scene& sc, RasterJob* j) {
+  if (ws->stage < 2 || sc.n != ws->n) return GS_ERR_STATE;
+  *j = RasterJob{};
+  j->cam = ws->cam;
+  j->rec = ws->rec.p;
+  j->feats = sc.feats;
+  j->D = sc.n_feat;
+  j->ranges = ws->ranges.p;
+  j->inst_id = ws->id_sorted;
+  j->order = ws->ordered ? ws->tile_order.p : nullptr;
+  j->T_final = ws->T_final.p;
+  j->n_contrib = ws->n_contrib.p;
+  j->g2d = ws->g2d.p;
+  return GS_OK;
+}
+
+int ws_tiles(const gs_workspace* ws) { return ws->TX * ws->TY; }
+
+gs_status ws_bwd_clear(gs_workspace* ws, int D, float* g_feats, cudaStream_t st) {
+  const int64_t n = ws->n;
+  if (n > 0) GS_TRY(cudaMemsetAsync(ws->g2d.p, 0, sizeof(float) * kG2D * (size_t)n, st));
+  if (g_feats && n > 0 && D > 0) GS_TRY(cudaMemsetAsync(g_feats, 0, sizeof(float) * (size_t)n * D, st));
+  return GS_OK;
+}
+
+gs_status ws_project_bwd(gs_workspace* ws, const gs_scene& sc, float* g_means, float* g_scales,
+                         float* g_quats, float* g_opac, float* g_sh, float* g_pose6, cudaStream_t st) {
+  launch_project_bwd(sc, ws->cam, ws->rec.p, ws->ntiles.p, ws->g2d.p, g_means, g_scales, g_quats,
+                     g_opac, g_sh, ws->pose_partials.p, g_pose6, st);
+  GS_TRY(cudaGetLastError());
+  return GS_OK;
+}
+
+}  // namespace gs
+

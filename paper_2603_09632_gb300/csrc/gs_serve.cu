@@ -1,24 +1,47 @@
-// Serving: resident scenes, continuous admission by an HBM budget, overlapping execution.
+// Serving: resident scenes, continuous batching, two-phase admission by an HBM budget.
 //
-// A server owns copies of the scenes it serves (device memory counted against its
-// budget) and a pool of slots.  Each slot is a worker thread with its own CUDA stream and
-// workspace; a worker takes the oldest pending request whose memory estimate fits what is
-// left of the budget and runs project -> bin -> render (-> backward) on its stream, so
-// requests that arrive while others are on the GPU are admitted as soon as a slot and the
-// memory free up and their kernels overlap with the running ones.  Results are
-// bit-identical to the same request rendered alone (forward) and equal within atomic
-// reordering (backward).
+// A server owns copies of the scenes it serves and, once the first request arrives, every
+// buffer it will use: two lanes, each a CUDA stream with its own request workspaces
+// (reserved for the largest resident scene and a per-request pixel limit), and one arena of
+// tile-instance buffers that takes the rest of the budget.  Nothing is allocated or freed
+// while requests run.
+//
+// The scheduler (serve_core.hpp) forms a batch from the oldest pending requests for a free
+// lane.  Phase A projects each of them on the lane's stream and reads back their tile
+// instance counts (one synchronisation per batch): that count, not an estimate, is what a
+// request needs from the arena.  Admission grants arena ranges in arrival order.  Phase B
+// bins each admitted request into its range, then renders all of them in ONE persistent
+// forward raster launch whose queue holds every (request, tile) item of the batch (one
+// launch per feature layout), and likewise one backward raster launch for the requests
+// that want gradients, followed by their projection backward.  While one lane's batch is
+// on the device the other lane projects and admits the next batch, so requests that arrive
+// meanwhile start as soon as memory frees up and their work overlaps on the device.
+// Results are bit-identical to the same request rendered alone (forward) and equal within
+// atomic reordering (backward).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "gs_internal.cuh"
+#include "gs_serve_ws.hpp"
 #include "serve_core.hpp"
 
 namespace {
+
+using gs::RasterJob;
+
+constexpr int kLanes = 2;
+constexpr double kAgingS = 0.05;          // a request that waited 50 ms is not overtaken
+constexpr int64_t kInstBytes = 20;        // per instance: key, id, their ping-pong, tile
+constexpr int64_t kGaussBytes = 112;      // per Gaussian in a request workspace (planning)
+constexpr int64_t kPixBytes = 8;          // per pixel: final transmittance, last contributor
+constexpr int64_t kMaxPixPerRequest = 3840LL * 2160LL;
+constexpr int64_t kMinPixPerRequest = 256LL * 256LL;
 
 struct SceneStore {
   gs_scene view;                   // points at the buffers below
@@ -26,70 +49,239 @@ struct SceneStore {
   size_t bytes = 0;
 };
 
-struct Slot {
-  gs_workspace* ws = nullptr;
+struct Lane {
   cudaStream_t stream = nullptr;
-  int64_t res_n = 0, res_pix = 0;   // what the workspace was last reserved for (worker-owned)
+  cudaEvent_t done = nullptr;
+  uint32_t* h_inst = nullptr;          // pinned, one count per workspace
+  uint32_t* queue = nullptr;           // device: forward queue [0, 1], backward [2, 3]
+  std::vector<gs_workspace*> ws;
 };
 
 size_t feat_elem_bytes(const gs_scene& s) { return s.feat_dtype == GS_BF16 ? 2 : 4; }
+
+int64_t tiles_of(int64_t W, int64_t H) { return ((W + 15) / 16) * ((H + 15) / 16); }
 
 }  // namespace
 
 struct gs_server {
   int device = 0;
   int64_t budget = 0;
-  std::mutex mu;                   // scenes
+  int slots_per_lane = 1;
+  std::mutex mu;                   // scenes and start-up
   std::vector<SceneStore> scenes;
   int64_t scene_bytes = 0;
   int64_t max_n = 0;               // largest resident scene
-  std::vector<Slot> slots;
+  bool started = false;
+  int64_t pix_cap = 0, tile_cap = 0;   // per-request limits of the reserved workspaces
+  int64_t fixed_bytes = 0;             // workspaces, queues
+  Lane lanes[kLanes];
+  void* arena = nullptr;
+  int64_t arena_inst = 0;              // instance slots in the arena
+  uint32_t* arr[5] = {};               // key0, id0, key1, id1, tile: [arena_inst] each
   std::unique_ptr<gs_serve::Scheduler<gs_request>> sched;
 };
 
 namespace {
 
-// Admission estimate of the device memory a request's intermediates need: per Gaussian
-// ~112 bytes (record, keys, sort buffers, gradient accumulators), per pixel 12 bytes,
-// per tile instance 16 bytes with an assumed 8 instances per Gaussian.
-int64_t request_cost(const gs_scene& s, const gs_camera& c) {
-  return s.n * 112 + (int64_t)c.W * c.H * 12 + s.n * 8 * 16 + (1 << 20);
+struct Grouping {
+  int dp;
+  int dtype;
+  bool operator<(const Grouping& o) const { return dp != o.dp ? dp < o.dp : dtype < o.dtype; }
+};
+
+gs_scene scene_of(gs_server* sv, int id) {
+  std::lock_guard<std::mutex> lk(sv->mu);
+  return sv->scenes[(size_t)id].view;
 }
 
-int run_request(gs_server* sv, int slot, const gs_request& r, int64_t* instances) {
+// Phase A: project every request of the batch and read back its tile-instance count.
+void measure(gs_server* sv, int lane, std::vector<gs_serve::Item<gs_request>>& items) {
   cudaSetDevice(sv->device);
-  Slot& sl = sv->slots[slot];
-  gs_scene sc;
-  int64_t max_n;
-  {
-    std::lock_guard<std::mutex> lk(sv->mu);
-    if (r.scene_id < 0 || r.scene_id >= (int)sv->scenes.size()) return GS_ERR_ARG;
-    sc = sv->scenes[r.scene_id].view;
-    max_n = sv->max_n;
+  Lane& ln = sv->lanes[lane];
+  for (auto& it : items) {
+    gs_workspace* ws = ln.ws[(size_t)it.slot];
+    const gs_scene sc = scene_of(sv, it.req.scene_id);
+    gs_status s = gs_project(&sc, &it.req.cam, ws, ln.stream);
+    if (s == GS_OK) s = gs::ws_instances_async(ws, ln.h_inst + it.slot, ln.stream);
+    it.status = s;
   }
-  // Grow this slot's workspace to the largest resident scene at once (and to the pixel
-  // count with headroom), so that the device-wide synchronisation of a reallocation
-  // happens rarely rather than whenever a slot meets a larger scene or frame.
-  const int64_t pix = (int64_t)r.cam.W * r.cam.H;
-  if (max_n > sl.res_n || pix > sl.res_pix) {
-    const int64_t want_pix = std::max<int64_t>(sl.res_pix, pix + pix / 4);
-    gs_status s = gs_workspace_reserve(sl.ws, max_n, 0, want_pix);
-    if (s != GS_OK) return s;
-    sl.res_n = max_n;
-    sl.res_pix = want_pix;
+  if (cudaStreamSynchronize(ln.stream) != cudaSuccess)
+    for (auto& it : items) it.status = it.status ? it.status : GS_ERR_CUDA;
+  for (auto& it : items)
+    if (it.status == GS_OK) it.cost = (int64_t)ln.h_inst[it.slot];
+}
+
+// Phase B: bin each admitted request into its arena range, then one forward raster launch
+// (and one backward raster launch) per feature layout for the whole batch.
+void launch(gs_server* sv, int lane, std::vector<gs_serve::Item<gs_request>>& items) {
+  cudaSetDevice(sv->device);
+  Lane& ln = sv->lanes[lane];
+  std::map<Grouping, std::vector<std::pair<size_t, RasterJob>>> fwd, bwd;
+  for (size_t k = 0; k < items.size(); ++k) {
+    auto& it = items[k];
+    gs_workspace* ws = ln.ws[(size_t)it.slot];
+    const gs_scene sc = scene_of(sv, it.req.scene_id);
+    const int64_t o = it.offset;
+    gs::ws_lend_instances(ws, sv->arr[0] + o, sv->arr[1] + o, sv->arr[2] + o, sv->arr[3] + o,
+                          sv->arr[4] + o, it.cost);
+    gs_status s = gs_bin_tiles(ws, nullptr, ln.stream);
+    RasterJob j;
+    if (s == GS_OK) s = gs::ws_job(ws, sc, &j);
+    if (s != GS_OK) {
+      it.status = s;
+      continue;
+    }
+    const gs_request& r = it.req;
+    const int D = sc.n_feat;
+    j.rgb = r.rgb;
+    j.depth = r.depth;
+    j.alpha = r.alpha;
+    j.feat = D > 0 ? r.feat : nullptr;
+    fwd[Grouping{j.feat ? gs::padded_feat(D) : 0, sc.feat_dtype}].push_back({k, j});
+    if (r.want_bwd) {
+      if ((s = gs::ws_bwd_clear(ws, D, D > 0 ? r.g_feats : nullptr, ln.stream)) != GS_OK) {
+        it.status = s;
+        continue;
+      }
+      j.g_rgb = r.g_rgb;
+      j.g_depth = r.g_depth;
+      j.g_alpha = r.g_alpha;
+      j.g_feat = D > 0 ? r.g_feat : nullptr;
+      j.g_feats = D > 0 ? r.g_feats : nullptr;
+      bwd[Grouping{j.g_feat ? gs::padded_feat(D) : 0, sc.feat_dtype}].push_back({k, j});
+    }
   }
-  gs_status s = gs_project(&sc, &r.cam, sl.ws, sl.stream);
-  if (s != GS_OK) return s;
-  if ((s = gs_bin_tiles(sl.ws, instances, sl.stream)) != GS_OK) return s;
-  if ((s = gs_render_fwd(&sc, &r.cam, sl.ws, r.rgb, r.depth, r.alpha, r.feat, sl.stream)) != GS_OK)
-    return s;
-  if (r.want_bwd &&
-      (s = gs_render_bwd(&sc, &r.cam, sl.ws, r.g_rgb, r.g_depth, r.g_alpha, r.g_feat, r.g_means,
-                         r.g_scales, r.g_quats, r.g_opac, r.g_sh, r.g_feats, r.g_pose6,
-                         sl.stream)) != GS_OK)
-    return s;
-  if (cudaStreamSynchronize(sl.stream) != cudaSuccess) return GS_ERR_CUDA;
-  return gs_workspace_status(sl.ws, sl.stream);
+  const gs::TileQueue fq{ln.queue, ln.queue + 1, nullptr, 0};
+  for (auto& g : fwd) {
+    std::vector<RasterJob> jobs;
+    int end = 0;
+    for (auto& e : g.second) {
+      if (items[e.first].status != GS_OK) continue;
+      end += gs::kFwdItemsPerTile * e.second.cam.TX * e.second.cam.TY;
+      e.second.item_end = end;
+      jobs.push_back(e.second);
+    }
+    gs::launch_raster_fwd_jobs(jobs.data(), (int)jobs.size(), g.first.dtype, g.first.dp > 0, fq,
+                               ln.stream);
+  }
+  const gs::TileQueue bq{ln.queue + 2, ln.queue + 3, nullptr, 0};
+  for (auto& g : bwd) {
+    std::vector<RasterJob> jobs;
+    int end = 0;
+    for (auto& e : g.second) {
+      if (items[e.first].status != GS_OK) continue;
+      end += e.second.cam.TX * e.second.cam.TY;
+      e.second.item_end = end;
+      jobs.push_back(e.second);
+    }
+    if (jobs.empty()) continue;
+    // the backward kernels leave their queue to the host: zeroed before each launch
+    cudaMemsetAsync(ln.queue + 2, 0, 8, ln.stream);
+    gs::launch_raster_bwd_jobs(jobs.data(), (int)jobs.size(), g.first.dtype, g.first.dp > 0, bq,
+                               ln.stream);
+  }
+  for (auto& it : items) {
+    const gs_request& r = it.req;
+    if (!r.want_bwd || it.status != GS_OK) continue;
+    const gs_scene sc = scene_of(sv, r.scene_id);
+    it.status = gs::ws_project_bwd(ln.ws[(size_t)it.slot], sc, r.g_means, r.g_scales, r.g_quats,
+                                   r.g_opac, r.g_sh, r.g_pose6, ln.stream);
+  }
+  if (cudaGetLastError() != cudaSuccess)
+    for (auto& it : items) it.status = it.status ? it.status : GS_ERR_CUDA;
+  cudaEventRecord(ln.done, ln.stream);
+}
+
+void finish(gs_server* sv, int lane, std::vector<gs_serve::Item<gs_request>>& items) {
+  cudaSetDevice(sv->device);
+  Lane& ln = sv->lanes[lane];
+  const bool ok = cudaEventSynchronize(ln.done) == cudaSuccess;
+  for (auto& it : items) {
+    it.instances = it.cost;
+    if (it.status != GS_OK) continue;
+    if (!ok) {
+      it.status = GS_ERR_CUDA;
+      continue;
+    }
+    it.status = gs_workspace_status(ln.ws[(size_t)it.slot], ln.stream);
+  }
+}
+
+void free_lanes(gs_server* sv) {
+  for (Lane& ln : sv->lanes) {
+    for (gs_workspace* w : ln.ws) gs_workspace_destroy(w);
+    ln.ws.clear();
+    if (ln.queue) cudaFree(ln.queue);
+    if (ln.h_inst) cudaFreeHost(ln.h_inst);
+    if (ln.done) cudaEventDestroy(ln.done);
+    if (ln.stream) cudaStreamDestroy(ln.stream);
+    ln = Lane{};
+  }
+}
+
+// Start-up at the first request (under sv->mu): reserve the request workspaces (half of
+// the budget left after the scenes at most) and give the rest to the instance arena.
+gs_status start_locked(gs_server* sv) {
+  if (sv->started) return GS_OK;
+  if (sv->scenes.empty()) return GS_ERR_STATE;
+  cudaSetDevice(sv->device);
+  const int nws = kLanes * sv->slots_per_lane;
+  const int64_t left = sv->budget - sv->scene_bytes;
+  const int64_t per_ws = left / 2 / nws - sv->max_n * kGaussBytes;
+  int64_t pix = std::min<int64_t>(kMaxPixPerRequest, per_ws / (kPixBytes + 1));
+  if (pix < kMinPixPerRequest) return GS_ERR_OVER_BUDGET;
+  const int64_t tiles = pix / 256 + 4096;
+  int64_t fixed = 0;
+  for (Lane& ln : sv->lanes) {
+    if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&ln.h_inst, sizeof(uint32_t) * gs::kMaxJobs) != cudaSuccess ||
+        cudaMalloc(&ln.queue, 4 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(ln.queue, 0, 4 * sizeof(uint32_t)) != cudaSuccess) {
+      free_lanes(sv);
+      return GS_ERR_OOM;
+    }
+    fixed += 16;
+    for (int k = 0; k < sv->slots_per_lane; ++k) {
+      gs_workspace* w = nullptr;
+      gs_status s = gs_workspace_create(&w, sv->device);
+      if (s == GS_OK) {
+        ln.ws.push_back(w);
+        s = gs::ws_reserve_fixed(w, sv->max_n, pix, tiles);
+      }
+      int64_t b = 0;
+      if (s == GS_OK) s = gs_workspace_bytes(w, &b);
+      if (s != GS_OK) {
+        free_lanes(sv);
+        return s == GS_ERR_OOM ? GS_ERR_OVER_BUDGET : s;
+      }
+      fixed += b;
+    }
+  }
+  const int64_t arena_bytes = left - fixed;
+  int64_t inst = std::min<int64_t>(arena_bytes / kInstBytes, (int64_t(1) << 31) - 1);
+  inst = inst / 64 * 64;
+  if (inst < 1024) {
+    free_lanes(sv);
+    return GS_ERR_OVER_BUDGET;
+  }
+  if (cudaMalloc(&sv->arena, (size_t)inst * kInstBytes) != cudaSuccess) {
+    free_lanes(sv);
+    return GS_ERR_OOM;
+  }
+  for (int k = 0; k < 5; ++k) sv->arr[k] = static_cast<uint32_t*>(sv->arena) + (size_t)k * inst;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GS_ERR_CUDA;
+  sv->pix_cap = pix;
+  sv->tile_cap = tiles;
+  sv->fixed_bytes = fixed;
+  sv->arena_inst = inst;
+  gs_serve::Executor<gs_request> ex;
+  ex.measure = [sv](int l, std::vector<gs_serve::Item<gs_request>>& b) { measure(sv, l, b); };
+  ex.launch = [sv](int l, std::vector<gs_serve::Item<gs_request>>& b) { launch(sv, l, b); };
+  ex.finish = [sv](int l, std::vector<gs_serve::Item<gs_request>>& b) { finish(sv, l, b); };
+  sv->sched.reset(new gs_serve::Scheduler<gs_request>(kLanes, sv->slots_per_lane, inst, kAgingS, ex));
+  sv->started = true;
+  return GS_OK;
 }
 
 }  // namespace
@@ -105,36 +297,17 @@ gs_status gs_serve_create(gs_server** out, int device, int64_t hbm_budget_bytes,
   if (!sv) return GS_ERR_OOM;
   sv->device = device;
   sv->budget = hbm_budget_bytes;
-  cudaSetDevice(device);
-  for (int i = 0; i < max_slots; ++i) {
-    Slot sl;
-    if (gs_workspace_create(&sl.ws, device) != GS_OK ||
-        cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
-      if (sl.ws) gs_workspace_destroy(sl.ws);
-      for (Slot& o : sv->slots) {
-        gs_workspace_destroy(o.ws);
-        cudaStreamDestroy(o.stream);
-      }
-      delete sv;
-      return GS_ERR_CUDA;
-    }
-    sv->slots.push_back(sl);
-  }
-  sv->sched.reset(new gs_serve::Scheduler<gs_request>(
-      max_slots, hbm_budget_bytes,
-      [sv](int slot, const gs_request& r, int64_t* inst) { return run_request(sv, slot, r, inst); }));
+  sv->slots_per_lane = std::max(1, std::min(gs::kMaxJobs, (max_slots + kLanes - 1) / kLanes));
   *out = sv;
   return GS_OK;
 }
 
 void gs_serve_destroy(gs_server* sv) {
   if (!sv) return;
-  sv->sched.reset();   // joins the workers; pending requests are cancelled
+  sv->sched.reset();   // joins the dispatcher and lanes; pending requests are cancelled
   cudaSetDevice(sv->device);
-  for (Slot& o : sv->slots) {
-    gs_workspace_destroy(o.ws);
-    cudaStreamDestroy(o.stream);
-  }
+  free_lanes(sv);
+  if (sv->arena) cudaFree(sv->arena);
   for (SceneStore& s : sv->scenes)
     for (void* p : s.buffers) cudaFree(p);
   delete sv;
@@ -154,6 +327,7 @@ gs_status gs_serve_add_scene(gs_server* sv, const gs_scene* scene, int* scene_id
   size_t total = 0;
   for (size_t b : sizes) total += b;
   std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->started) return GS_ERR_STATE;   // the budget was divided at the first request
   if (sv->scene_bytes + (int64_t)total > sv->budget) return GS_ERR_OVER_BUDGET;
   cudaSetDevice(sv->device);
   SceneStore st;
@@ -180,30 +354,33 @@ gs_status gs_serve_add_scene(gs_server* sv, const gs_scene* scene, int* scene_id
   sv->max_n = std::max<int64_t>(sv->max_n, n);
   sv->scenes.push_back(st);
   *scene_id = (int)sv->scenes.size() - 1;
-  sv->sched->set_budget(sv->budget - sv->scene_bytes);
   return GS_OK;
 }
 
 gs_status gs_serve_submit(gs_server* sv, const gs_request* req, uint64_t* ticket) {
   if (!sv || !req || !ticket) return GS_ERR_ARG;
-  gs_scene sc;
+  gs_serve::Scheduler<gs_request>* sched = nullptr;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (req->scene_id < 0 || req->scene_id >= (int)sv->scenes.size()) return GS_ERR_ARG;
-    sc = sv->scenes[req->scene_id].view;
+    const gs_camera& c = req->cam;
+    if (c.W <= 0 || c.H <= 0 || c.tile != gs::kTile || !(c.fx > 0.f) || !(c.fy > 0.f) ||
+        !(c.near_z > 0.f) || c.stride != 1 || c.off_x != 0 || c.off_y != 0)
+      return GS_ERR_ARG;
+    if (req->want_bwd && (!req->g_rgb && !req->g_depth && !req->g_alpha && !req->g_feat))
+      return GS_ERR_ARG;
+    gs_status s = start_locked(sv);
+    if (s != GS_OK) return s;
+    if ((int64_t)c.W * c.H > sv->pix_cap || tiles_of(c.W, c.H) > sv->tile_cap)
+      return GS_ERR_OVER_BUDGET;
+    sched = sv->sched.get();
   }
-  const gs_camera& c = req->cam;
-  if (c.W <= 0 || c.H <= 0 || c.tile != gs::kTile || !(c.fx > 0.f) || !(c.fy > 0.f)) return GS_ERR_ARG;
-  if (req->want_bwd && (!req->g_rgb && !req->g_depth && !req->g_alpha && !req->g_feat)) return GS_ERR_ARG;
-  const int64_t room = sv->budget - sv->scene_bytes;
-  const int64_t cost = request_cost(sc, c);
-  if (cost > room) return GS_ERR_OVER_BUDGET;
-  const int s = sv->sched->submit(*req, cost, ticket);
-  return (gs_status)s;
+  return (gs_status)sched->submit(*req, 0, ticket);
 }
 
 gs_status gs_serve_poll(gs_server* sv, uint64_t ticket, int64_t timeout_us, gs_result* out) {
   if (!sv) return GS_ERR_ARG;
+  if (!sv->sched) return GS_ERR_ARG;   // no request was ever submitted
   gs_serve::Result r;
   const int s = sv->sched->poll(ticket, timeout_us, &r);
   if (s != 0) return (gs_status)s;
@@ -219,7 +396,7 @@ gs_status gs_serve_poll(gs_server* sv, uint64_t ticket, int64_t timeout_us, gs_r
 }
 
 gs_status gs_serve_cancel(gs_server* sv, uint64_t ticket) {
-  if (!sv) return GS_ERR_ARG;
+  if (!sv || !sv->sched) return GS_ERR_ARG;
   return (gs_status)sv->sched->cancel(ticket);
 }
 
@@ -230,9 +407,29 @@ gs_status gs_serve_info(gs_server* sv, int64_t* scene_bytes, int64_t* in_flight_
     std::lock_guard<std::mutex> lk(sv->mu);
     if (scene_bytes) *scene_bytes = sv->scene_bytes;
   }
-  if (in_flight_bytes) *in_flight_bytes = sv->sched->in_flight_bytes();
-  if (peak_in_flight_bytes) *peak_in_flight_bytes = sv->sched->peak_in_flight_bytes();
-  if (peak_running) *peak_running = sv->sched->peak_running();
+  gs_serve::Scheduler<gs_request>* s = sv->sched.get();
+  if (in_flight_bytes) *in_flight_bytes = s ? s->arena_used() * kInstBytes : 0;
+  if (peak_in_flight_bytes) *peak_in_flight_bytes = s ? s->arena_peak() * kInstBytes : 0;
+  if (peak_running) *peak_running = s ? s->peak_running() : 0;
+  return GS_OK;
+}
+
+gs_status gs_serve_stats(gs_server* sv, gs_serve_stats_t* out) {
+  if (!sv || !out) return GS_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  std::lock_guard<std::mutex> lk(sv->mu);
+  out->scene_bytes = sv->scene_bytes;
+  out->workspace_bytes = sv->fixed_bytes;
+  out->arena_bytes = sv->arena_inst * kInstBytes;
+  out->max_pixels = sv->pix_cap;
+  out->lanes = sv->started ? kLanes : 0;
+  out->slots_per_lane = sv->slots_per_lane;
+  if (gs_serve::Scheduler<gs_request>* s = sv->sched.get()) {
+    out->arena_peak_bytes = s->arena_peak() * kInstBytes;
+    out->batches = s->batches();
+    out->peak_batch = s->peak_batch();
+    out->peak_running = s->peak_running();
+  }
   return GS_OK;
 }
 

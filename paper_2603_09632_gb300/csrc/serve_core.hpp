@@ -1,10 +1,17 @@
 // Host-side scheduler of the serving loop (pure C++; no CUDA here, so its admission,
-// queueing, timeout and cancellation logic can be exercised without a GPU).
+// batching, queueing, timeout and cancellation logic can be exercised without a GPU).
 //
-// Requests are admitted continuously: a worker per slot takes the oldest pending request
-// whose memory estimate fits the remaining budget, runs it through the executor and
-// publishes the result; requests that arrive while others are running start as soon as
-// a slot and enough budget are free, so their device work overlaps with the running ones.
+// Continuous batching in two phases.  A dispatcher thread forms a batch from the oldest
+// pending requests (up to one per workspace of a free lane) and runs phase A, the work
+// that fixes a request's true memory need (on the GPU: its projection, which counts its
+// tile instances).  Admission then grants each request a range of a fixed arena (the
+// instance buffers, sized once from the budget) in arrival order; a request that does not
+// fit goes back to the head of the queue, and once it has waited longer than the aging
+// limit nothing behind it is admitted before it, so a large request is never overtaken
+// forever.  Phase B launches the admitted requests together (on the GPU: one persistent
+// raster launch for all of them) and a completion thread per lane publishes their results
+// and frees their arena ranges.  Two lanes let one batch's phase A run while the other
+// batch is on the device, and requests that arrive meanwhile join the next batch.
 #pragma once
 
 #include <chrono>
@@ -12,22 +19,96 @@
 #include <cstdint>
 #include <deque>
 #include <functional>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 namespace gs_serve {
 
-enum class State { Pending, Running, Done };
+// First-fit allocator of ranges [offset, offset + n) of an arena of `capacity` units.
+class Arena {
+ public:
+  explicit Arena(int64_t capacity = 0) { reset(capacity); }
+  void reset(int64_t capacity) {
+    cap_ = capacity > 0 ? capacity : 0;
+    used_ = 0;
+    free_.clear();
+    if (cap_ > 0) free_[0] = cap_;
+  }
+  int64_t capacity() const { return cap_; }
+  int64_t used() const { return used_; }
+  // Offset of a free range of n units (0 for n <= 0, which takes nothing), or -1.
+  int64_t alloc(int64_t n) {
+    if (n <= 0) return 0;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < n) continue;
+      const int64_t off = it->first, len = it->second;
+      free_.erase(it);
+      if (len > n) free_[off + n] = len - n;
+      used_ += n;
+      return off;
+    }
+    return -1;
+  }
+  void release(int64_t off, int64_t n) {
+    if (n <= 0 || off < 0) return;
+    used_ -= n;
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t free_ranges() const { return free_.size(); }
+
+ private:
+  int64_t cap_ = 0, used_ = 0;
+  std::map<int64_t, int64_t> free_;   // offset -> length, disjoint, not adjacent
+};
+
+// One request inside a batch.
+template <class Request>
+struct Item {
+  uint64_t ticket = 0;
+  Request req;
+  int slot = -1;          // workspace of its lane
+  int64_t cost = 0;       // arena units, set by phase A
+  int64_t offset = -1;    // arena range granted by admission
+  int status = 0;         // executor status (0 = ok)
+  int64_t instances = 0;  // reported back to the caller
+};
+
+// The device side.  measure: phase A for the items of a batch on `lane` (their slots are
+// assigned); returns once every item's cost (or an error status) is known.  launch: phase
+// B for the admitted items, asynchronously.  finish: waits for the lane's launched work and
+// sets each item's status and instance count.
+template <class Request>
+struct Executor {
+  std::function<void(int lane, std::vector<Item<Request>>&)> measure;
+  std::function<void(int lane, std::vector<Item<Request>>&)> launch;
+  std::function<void(int lane, std::vector<Item<Request>>&)> finish;
+};
+
+enum class State { Pending, Measuring, Running, Done };
 
 template <class Request>
 struct Job {
   uint64_t ticket = 0;
   Request req;
-  int64_t cost = 0;            // admission estimate (bytes)
   State state = State::Pending;
-  int status = 0;              // executor status (0 = ok)
+  int status = 0;
   int slot = -1;
   int64_t instances = 0;
   double t_submit = 0, t_start = 0, t_done = 0;   // seconds, steady clock
@@ -40,19 +121,19 @@ struct Result {
   double queue_us, run_us, latency_us;
 };
 
-// Executor: runs one request on slot `slot`; returns a status (0 = ok) and the instance
-// count through `instances`.
-template <class Request>
-using Executor = std::function<int(int slot, const Request&, int64_t* instances)>;
-
 template <class Request>
 class Scheduler {
  public:
   static constexpr int kOk = 0, kBusy = 6, kOverBudget = 7, kArg = 1, kCancelled = 9;
 
-  Scheduler(int n_slots, int64_t budget, Executor<Request> exec)
-      : budget_(budget), exec_(std::move(exec)) {
-    for (int s = 0; s < n_slots; ++s) workers_.emplace_back([this, s] { work(s); });
+  // lanes x slots_per_lane requests may be in flight; the arena has `arena_units` units;
+  // a request that could not be admitted waits at most `aging_s` before it blocks the
+  // requests behind it.
+  Scheduler(int lanes, int slots_per_lane, int64_t arena_units, double aging_s, Executor<Request> ex)
+      : spl_(slots_per_lane), aging_(aging_s), arena_(arena_units), ex_(std::move(ex)),
+        lanes_((size_t)lanes) {
+    dispatcher_ = std::thread([this] { dispatch(); });
+    for (int l = 0; l < lanes; ++l) finishers_.emplace_back([this, l] { complete(l); });
   }
 
   ~Scheduler() { shutdown(); }
@@ -63,10 +144,10 @@ class Scheduler {
       if (stop_) return;
       stop_ = true;
     }
-    cv_work_.notify_all();
-    for (auto& t : workers_)
+    cv_.notify_all();
+    if (dispatcher_.joinable()) dispatcher_.join();
+    for (auto& t : finishers_)
       if (t.joinable()) t.join();
-    // requests still pending are cancelled
     std::lock_guard<std::mutex> lk(mu_);
     for (auto& kv : jobs_)
       if (kv.second.state == State::Pending) finish_locked(kv.second, kCancelled);
@@ -74,22 +155,21 @@ class Scheduler {
     cv_done_.notify_all();
   }
 
-  // Queue a request whose device memory estimate is `cost` bytes.  A request that could
-  // never fit the budget is refused at once.
-  int submit(const Request& r, int64_t cost, uint64_t* ticket) {
-    if (!ticket || cost < 0) return kArg;
+  // Queue a request; `min_cost` is a lower bound of its arena need known without the GPU
+  // (a request that can never fit is refused at once).
+  int submit(const Request& r, int64_t min_cost, uint64_t* ticket) {
+    if (!ticket || min_cost < 0) return kArg;
     std::lock_guard<std::mutex> lk(mu_);
-    if (cost > budget_) return kOverBudget;
+    if (min_cost > arena_.capacity()) return kOverBudget;
     if (stop_) return kArg;
     Job<Request> j;
     j.ticket = ++next_ticket_;
     j.req = r;
-    j.cost = cost;
     j.t_submit = now();
     jobs_[j.ticket] = j;
     pending_.push_back(j.ticket);
     *ticket = j.ticket;
-    cv_work_.notify_one();
+    cv_.notify_all();
     return kOk;
   }
 
@@ -125,7 +205,7 @@ class Scheduler {
     return kOk;
   }
 
-  // Cancel a request that has not started; kBusy if it is already running or done.
+  // Cancel a request that is waiting in the queue; kBusy once its batch has taken it.
   int cancel(uint64_t ticket) {
     std::lock_guard<std::mutex> lk(mu_);
     auto it = jobs_.find(ticket);
@@ -141,29 +221,38 @@ class Scheduler {
     return kOk;
   }
 
-  // Change the budget available to requests (e.g. after resident data took a share).
-  void set_budget(int64_t b) {
-    {
-      std::lock_guard<std::mutex> lk(mu_);
-      budget_ = b;
-    }
-    cv_work_.notify_all();
-  }
-
-  int64_t in_flight_bytes() {
+  int64_t arena_used() {
     std::lock_guard<std::mutex> lk(mu_);
-    return in_flight_;
+    return arena_.used();
   }
-  int64_t peak_in_flight_bytes() {
+  int64_t arena_peak() {
     std::lock_guard<std::mutex> lk(mu_);
-    return peak_in_flight_;
+    return arena_peak_;
+  }
+  int64_t arena_capacity() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return arena_.capacity();
   }
   int peak_running() {
     std::lock_guard<std::mutex> lk(mu_);
     return peak_running_;
   }
+  int64_t batches() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return batches_;
+  }
+  int peak_batch() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return peak_batch_;
+  }
 
  private:
+  struct Lane {
+    bool busy = false;       // a batch is being formed or is on the device
+    bool launched = false;   // its items await completion
+    std::vector<Item<Request>> items;
+  };
+
   static double now() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
   }
@@ -174,59 +263,141 @@ class Scheduler {
     j.t_done = now();
   }
 
-  // Oldest pending request that fits the remaining budget (FIFO among those that fit).
-  bool take_locked(uint64_t* ticket) {
-    for (auto p = pending_.begin(); p != pending_.end(); ++p) {
-      Job<Request>& j = jobs_[*p];
-      if (in_flight_ + j.cost <= budget_) {
-        *ticket = *p;
-        pending_.erase(p);
-        return true;
-      }
-    }
+  int free_lane_locked() const {
+    for (size_t l = 0; l < lanes_.size(); ++l)
+      if (!lanes_[l].busy) return (int)l;
+    return -1;
+  }
+  bool any_busy_locked() const {
+    for (const Lane& ln : lanes_)
+      if (ln.busy) return true;
     return false;
   }
 
-  void work(int slot) {
+  void dispatch() {
     std::unique_lock<std::mutex> lk(mu_);
     while (true) {
-      uint64_t t = 0;
-      cv_work_.wait(lk, [&] { return stop_ || take_locked(&t); });
-      if (stop_ && t == 0) return;
-      Job<Request>& j = jobs_[t];
-      j.state = State::Running;
-      j.slot = slot;
-      j.t_start = now();
-      in_flight_ += j.cost;
-      if (in_flight_ > peak_in_flight_) peak_in_flight_ = in_flight_;
-      ++running_;
-      if (running_ > peak_running_) peak_running_ = running_;
-      const Request req = j.req;
+      cv_.wait(lk, [&] {
+        return stop_ || (!pending_.empty() && free_lane_locked() >= 0 && !blocked_);
+      });
+      if (stop_) return;
+      const int lane = free_lane_locked();
+      lanes_[(size_t)lane].busy = true;
+      std::vector<Item<Request>> batch;
+      while (!pending_.empty() && (int)batch.size() < spl_) {
+        Job<Request>& j = jobs_[pending_.front()];
+        pending_.pop_front();
+        j.state = State::Measuring;
+        Item<Request> it;
+        it.ticket = j.ticket;
+        it.req = j.req;
+        it.slot = (int)batch.size();
+        batch.push_back(it);
+      }
       lk.unlock();
-      int64_t inst = 0;
-      const int st = exec_(slot, req, &inst);
+      ex_.measure(lane, batch);   // phase A: true costs
       lk.lock();
-      Job<Request>& jd = jobs_[t];
-      jd.instances = inst;
-      finish_locked(jd, st);
-      in_flight_ -= jd.cost;
-      --running_;
-      cv_done_.notify_all();
-      cv_work_.notify_all();   // budget freed: another waiting request may fit now
+      std::vector<Item<Request>> admitted, back;
+      bool hold = false;   // an aged request does not fit: admit nothing behind it
+      for (Item<Request>& it : batch) {
+        Job<Request>& j = jobs_[it.ticket];
+        if (stop_) {
+          finish_locked(j, kCancelled);
+          continue;
+        }
+        if (hold) {
+          back.push_back(it);
+          continue;
+        }
+        if (it.status != kOk) {
+          finish_locked(j, it.status);
+          continue;
+        }
+        if (it.cost > arena_.capacity()) {
+          finish_locked(j, kOverBudget);
+          continue;
+        }
+        const int64_t off = arena_.alloc(it.cost);
+        if (off >= 0) {
+          it.offset = off;
+          j.state = State::Running;
+          j.t_start = now();
+          admitted.push_back(it);
+        } else {
+          back.push_back(it);
+          if (now() - j.t_submit > aging_) hold = true;
+        }
+      }
+      for (auto r = back.rbegin(); r != back.rend(); ++r) {   // back to the head, in order
+        jobs_[r->ticket].state = State::Pending;
+        pending_.push_front(r->ticket);
+      }
+      if (arena_.used() > arena_peak_) arena_peak_ = arena_.used();
+      Lane& ln = lanes_[(size_t)lane];
+      if (admitted.empty()) {
+        ln.busy = false;
+        // nothing fits until running requests free memory (none running: the arena is
+        // empty and every cost <= capacity was admitted, so this cannot stall)
+        blocked_ = any_busy_locked();
+        cv_done_.notify_all();
+        cv_.notify_all();
+        continue;
+      }
+      running_ += (int)admitted.size();
+      if (running_ > peak_running_) peak_running_ = running_;
+      ++batches_;
+      if ((int)admitted.size() > peak_batch_) peak_batch_ = (int)admitted.size();
+      lk.unlock();
+      ex_.launch(lane, admitted);   // phase B, asynchronous
+      lk.lock();
+      ln.items = std::move(admitted);
+      ln.launched = true;
+      cv_.notify_all();
     }
   }
 
-  int64_t budget_;
-  Executor<Request> exec_;
+  void complete(int lane) {
+    std::unique_lock<std::mutex> lk(mu_);
+    Lane& ln = lanes_[(size_t)lane];
+    while (true) {
+      cv_.wait(lk, [&] { return ln.launched || (stop_ && !ln.busy); });
+      if (!ln.launched) return;   // stopping, nothing in flight on this lane
+      std::vector<Item<Request>> items = std::move(ln.items);
+      ln.items.clear();
+      lk.unlock();
+      ex_.finish(lane, items);
+      lk.lock();
+      for (Item<Request>& it : items) {
+        arena_.release(it.offset, it.cost);
+        Job<Request>& j = jobs_[it.ticket];
+        j.instances = it.instances;
+        j.slot = lane * spl_ + it.slot;
+        finish_locked(j, it.status);
+      }
+      running_ -= (int)items.size();
+      ln.launched = false;
+      ln.busy = false;
+      blocked_ = false;   // memory was freed
+      cv_done_.notify_all();
+      cv_.notify_all();
+    }
+  }
+
+  const int spl_;
+  const double aging_;
+  Arena arena_;
+  Executor<Request> ex_;
+  std::vector<Lane> lanes_;
   std::mutex mu_;
-  std::condition_variable cv_work_, cv_done_;
+  std::condition_variable cv_, cv_done_;
   std::deque<uint64_t> pending_;
   std::unordered_map<uint64_t, Job<Request>> jobs_;
-  std::vector<std::thread> workers_;
+  std::thread dispatcher_;
+  std::vector<std::thread> finishers_;
   uint64_t next_ticket_ = 0;
-  int64_t in_flight_ = 0, peak_in_flight_ = 0;
-  int running_ = 0, peak_running_ = 0;
-  bool stop_ = false;
+  int64_t arena_peak_ = 0, batches_ = 0;
+  int running_ = 0, peak_running_ = 0, peak_batch_ = 0;
+  bool stop_ = false, blocked_ = false;
 };
 
 }  // namespace gs_serve

@@ -68,8 +68,14 @@ def test_mix_equals_alone():
         results.append(res)
     torch.cuda.synchronize()
     info = L.gs_serve_info(server)
+    stats = L.gs_serve_stats(server)
     assert info["peak_running"] >= 2            # requests did run concurrently
     assert len({r["slot"] for r in results}) >= 2
+    assert stats["peak_batch"] >= 2             # and shared raster launches
+    assert stats["batches"] < len(reqs)
+    assert info["peak_in_flight_bytes"] <= stats["arena_bytes"]
+    # admission used the real instance counts: every request's granted range is its count
+    assert all(r["instances"] > 0 for r in results)
 
     rast = Rasterizer(dev)
     for (s, cam, out, gin, gout, _), res in zip(reqs, results):
@@ -103,13 +109,35 @@ def test_budget_refusals_and_cancel():
     tiny.close()
     server = L.Server(64 << 20, 1, dev.index)               # fits the scene, not a 4K request
     sid = L.gs_serve_add_scene(server, t)
+    # large Gaussians seen from close by: far more tile instances than the arena holds
+    crowd = S.cube_scene(20_000, n_feat=4, seed=4, log_scale_mu=-1.5, log_scale_sd=0.1)
+    cid = L.gs_serve_add_scene(server, U.upload(crowd))
     big = S.pinhole(3840, 2160, 3600.0, 3600.0, np.eye(3), np.array([0.0, 0.0, 3.0]))
     out = _outputs(torch, dev, S.pinhole(64, 64, 60.0), 4)
     st, _ = L.gs_serve_submit(server, L.make_request(sid, as_camera(big), out))
     assert st == L.GS_ERR_OVER_BUDGET
     st, _ = L.gs_serve_submit(server, L.make_request(sid + 5, as_camera(big), out))
     assert st == L.GS_ERR_ARG
-    # cancel a queued request behind a running one on the single slot
+    # the budget is divided at the first submit: no more scenes
+    with pytest.raises(L.GSError) as e:
+        L.gs_serve_add_scene(server, t)
+    assert e.value.status == L.GS_ERR_STATE
+    stats = L.gs_serve_stats(server)
+    assert stats["scene_bytes"] + stats["workspace_bytes"] + stats["arena_bytes"] <= 64 << 20
+    assert stats["max_pixels"] < 3840 * 2160
+    # admission by the real instance count: a request that needs more than the whole arena
+    # is refused after its projection, and nothing is written
+    close = S.pinhole(1280, 1024, 1000.0, 1000.0, np.eye(3), np.array([0.0, 0.0, 2.0]))
+    o2 = _outputs(torch, dev, close, 4)
+    o2["alpha"].fill_(-7.0)
+    st, tb = L.gs_serve_submit(server, L.make_request(cid, as_camera(close), o2))
+    assert st == L.GS_OK
+    st, res = L.gs_serve_poll(server, tb, 10_000_000)
+    assert st == L.GS_OK and res["status"] == L.GS_ERR_OVER_BUDGET and res["slot"] == -1
+    assert res["instances"] == 0
+    torch.cuda.synchronize()
+    assert (o2["alpha"] == -7.0).all()
+    # cancel queued requests behind running ones (one request per lane)
     cams = S.room_trajectory(4, 64, 64, 60.0)
     tk = []
     for c in cams:
