@@ -1271,7 +1271,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving-loop benchmark instead")
     ap.add_argument("--no-serve", action="store_true",
                     help="leave the serving summary (p50/p99 at saturation) out of the main line")
-    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-capacity-requests", type=int, default=100)
     ap.add_argument("--serve-budget-gb", type=float, default=16.0)

@@ -341,21 +341,23 @@ gs_status gs_measure_fp32_peak(int iters, double* tflops_out, double* ms_out, vo
  * (tracking, mapping over a keyframe window, semantic phases; Sec. 3.2, Eq. 2-3); serving
  * is the systems form of that load.
  *   - Memory.  At the first submit the server divides its budget once: resident scenes,
- *     then request workspaces (two lanes of ceil(max_slots / 2) workspaces, reserved for
- *     the largest scene and a per-request pixel limit; together at most half of what the
- *     scenes leave), then one arena of tile-instance buffers with the rest.  Nothing is
+ *     then request workspaces (min(4, max_slots) lanes of ceil(max_slots / lanes)
+ *     workspaces, reserved for the largest scene and a per-request pixel limit; together at
+ *     most half of what the scenes leave), then one arena of tile-instance buffers with the
+ *     rest.  Nothing is
  *     allocated or freed while requests run, and scenes can no longer be added.
- *   - Admission in two phases.  A batch takes the oldest pending requests for a free
- *     lane and projects them; each request's tile-instance count (read back once per
+ *   - Admission in two phases.  Each lane is a worker that takes a batch of the oldest
+ *     pending requests (one per workspace) and projects them; each request's tile-instance count (read back once per
  *     batch) is what it needs from the arena.  Ranges are granted in arrival order; a
  *     request that does not fit waits at the head of the queue, and once it has waited
  *     50 ms no request behind it is admitted before it.
  *   - Execution.  The admitted requests are binned into their ranges and rendered by ONE
  *     persistent forward raster launch whose queue holds every (request, tile) item of the
  *     batch (one launch per feature layout), then one backward raster launch for those
- *     that want gradients and their projection backward.  While one lane's batch is on
- *     the device the other lane admits the next, so requests that arrive meanwhile start
- *     as memory frees up and their work overlaps on the device.
+ *     that want gradients and their projection backward.  Lanes run independently, so
+ *     while one lane's batch is on the device the others admit and launch theirs:
+ *     requests that arrive meanwhile start as a lane and memory free up, and their work
+ *     overlaps on the device.
  * A request's results equal those of the same request rendered alone (forward bit for
  * bit; backward up to the order of atomic additions).  Host-side waits are bounded by the
  * caller's timeout; no kernel waits on another. */
@@ -383,7 +385,8 @@ typedef struct {
 
 /* Create a server on `device` with a device-memory budget (bytes) for everything it holds
  * (resident scenes, request workspaces, the instance arena) and max_slots (1..64): up to
- * ceil(max_slots / 2) (at most 8) requests per batch on each of two lanes.  Nothing is
+ * ceil(max_slots / lanes) (at most 8) requests per batch on each of min(4, max_slots)
+ * lanes.  Nothing is
  * allocated on the device until scenes are added.  Errors: GS_ERR_ARG, GS_ERR_CUDA. */
 gs_status gs_serve_create(gs_server** server, int device, int64_t hbm_budget_bytes, int max_slots);
 

@@ -1,7 +1,7 @@
 // Serving: resident scenes, continuous batching, two-phase admission by an HBM budget.
 //
 // A server owns copies of the scenes it serves and, once the first request arrives, every
-// buffer it will use: two lanes, each a CUDA stream with its own request workspaces
+// buffer it will use: up to four lanes, each a CUDA stream with its own request workspaces
 // (reserved for the largest resident scene and a per-request pixel limit), and one arena of
 // tile-instance buffers that takes the rest of the budget.  Nothing is allocated or freed
 // while requests run.
@@ -13,9 +13,10 @@
 // bins each admitted request into its range, then renders all of them in ONE persistent
 // forward raster launch whose queue holds every (request, tile) item of the batch (one
 // launch per feature layout), and likewise one backward raster launch for the requests
-// that want gradients, followed by their projection backward.  While one lane's batch is
-// on the device the other lane projects and admits the next batch, so requests that arrive
-// meanwhile start as soon as memory frees up and their work overlaps on the device.
+// that want gradients, followed by their projection backward.  Lanes are independent
+// workers, so while one lane's batch is on the device the others project, admit and launch
+// theirs: requests that arrive meanwhile start as soon as a lane and memory free up, and
+// their work overlaps on the device.
 // Results are bit-identical to the same request rendered alone (forward) and equal within
 // atomic reordering (backward).
 #include <algorithm>
@@ -35,7 +36,7 @@ namespace {
 
 using gs::RasterJob;
 
-constexpr int kLanes = 2;
+constexpr int kMaxLanes = 4;
 constexpr double kAgingS = 0.05;          // a request that waited 50 ms is not overtaken
 constexpr int64_t kInstBytes = 20;        // per instance: key, id, their ping-pong, tile
 constexpr int64_t kGaussBytes = 112;      // per Gaussian in a request workspace (planning)
@@ -66,7 +67,7 @@ int64_t tiles_of(int64_t W, int64_t H) { return ((W + 15) / 16) * ((H + 15) / 16
 struct gs_server {
   int device = 0;
   int64_t budget = 0;
-  int slots_per_lane = 1;
+  int n_lanes = 1, slots_per_lane = 1;
   std::mutex mu;                   // scenes and start-up
   std::vector<SceneStore> scenes;
   int64_t scene_bytes = 0;
@@ -74,7 +75,7 @@ struct gs_server {
   bool started = false;
   int64_t pix_cap = 0, tile_cap = 0;   // per-request limits of the reserved workspaces
   int64_t fixed_bytes = 0;             // workspaces, queues
-  Lane lanes[kLanes];
+  Lane lanes[kMaxLanes];
   void* arena = nullptr;
   int64_t arena_inst = 0;              // instance slots in the arena
   uint32_t* arr[5] = {};               // key0, id0, key1, id1, tile: [arena_inst] each
@@ -225,14 +226,15 @@ gs_status start_locked(gs_server* sv) {
   if (sv->started) return GS_OK;
   if (sv->scenes.empty()) return GS_ERR_STATE;
   cudaSetDevice(sv->device);
-  const int nws = kLanes * sv->slots_per_lane;
+  const int nws = sv->n_lanes * sv->slots_per_lane;
   const int64_t left = sv->budget - sv->scene_bytes;
   const int64_t per_ws = left / 2 / nws - sv->max_n * kGaussBytes;
   int64_t pix = std::min<int64_t>(kMaxPixPerRequest, per_ws / (kPixBytes + 1));
   if (pix < kMinPixPerRequest) return GS_ERR_OVER_BUDGET;
   const int64_t tiles = pix / 256 + 4096;
   int64_t fixed = 0;
-  for (Lane& ln : sv->lanes) {
+  for (int l = 0; l < sv->n_lanes; ++l) {
+    Lane& ln = sv->lanes[l];
     if (cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&ln.h_inst, sizeof(uint32_t) * gs::kMaxJobs) != cudaSuccess ||
@@ -279,7 +281,7 @@ gs_status start_locked(gs_server* sv) {
   ex.measure = [sv](int l, std::vector<gs_serve::Item<gs_request>>& b) { measure(sv, l, b); };
   ex.launch = [sv](int l, std::vector<gs_serve::Item<gs_request>>& b) { launch(sv, l, b); };
   ex.finish = [sv](int l, std::vector<gs_serve::Item<gs_request>>& b) { finish(sv, l, b); };
-  sv->sched.reset(new gs_serve::Scheduler<gs_request>(kLanes, sv->slots_per_lane, inst, kAgingS, ex));
+  sv->sched.reset(new gs_serve::Scheduler<gs_request>(sv->n_lanes, sv->slots_per_lane, inst, kAgingS, ex));
   sv->started = true;
   return GS_OK;
 }
@@ -297,7 +299,9 @@ gs_status gs_serve_create(gs_server** out, int device, int64_t hbm_budget_bytes,
   if (!sv) return GS_ERR_OOM;
   sv->device = device;
   sv->budget = hbm_budget_bytes;
-  sv->slots_per_lane = std::max(1, std::min(gs::kMaxJobs, (max_slots + kLanes - 1) / kLanes));
+  // up to four lanes (independent pipelines on the device), the rest as batch width
+  sv->n_lanes = std::min(kMaxLanes, max_slots);
+  sv->slots_per_lane = std::max(1, std::min(gs::kMaxJobs, (max_slots + sv->n_lanes - 1) / sv->n_lanes));
   *out = sv;
   return GS_OK;
 }
@@ -422,7 +426,7 @@ gs_status gs_serve_stats(gs_server* sv, gs_serve_stats_t* out) {
   out->workspace_bytes = sv->fixed_bytes;
   out->arena_bytes = sv->arena_inst * kInstBytes;
   out->max_pixels = sv->pix_cap;
-  out->lanes = sv->started ? kLanes : 0;
+  out->lanes = sv->started ? sv->n_lanes : 0;
   out->slots_per_lane = sv->slots_per_lane;
   if (gs_serve::Scheduler<gs_request>* s = sv->sched.get()) {
     out->arena_peak_bytes = s->arena_peak() * kInstBytes;

@@ -1,17 +1,18 @@
 // Host-side scheduler of the serving loop (pure C++; no CUDA here, so its admission,
 // batching, queueing, timeout and cancellation logic can be exercised without a GPU).
 //
-// Continuous batching in two phases.  A dispatcher thread forms a batch from the oldest
-// pending requests (up to one per workspace of a free lane) and runs phase A, the work
-// that fixes a request's true memory need (on the GPU: its projection, which counts its
-// tile instances).  Admission then grants each request a range of a fixed arena (the
-// instance buffers, sized once from the budget) in arrival order; a request that does not
-// fit goes back to the head of the queue, and once it has waited longer than the aging
-// limit nothing behind it is admitted before it, so a large request is never overtaken
-// forever.  Phase B launches the admitted requests together (on the GPU: one persistent
-// raster launch for all of them) and a completion thread per lane publishes their results
-// and frees their arena ranges.  Two lanes let one batch's phase A run while the other
-// batch is on the device, and requests that arrive meanwhile join the next batch.
+// Continuous batching in two phases.  Each lane (on the GPU: a CUDA stream with its own
+// request workspaces) is a worker that takes a batch of the oldest pending requests (up to
+// one per workspace) and runs phase A, the work that fixes a request's true memory need
+// (on the GPU: its projection, which counts its tile instances).  Admission then grants
+// each request a range of a fixed arena (the instance buffers, sized once from the budget)
+// in arrival order; a request that does not fit goes back to the head of the queue, and
+// once it has waited longer than the aging limit nothing behind it is admitted before it,
+// so a large request is never overtaken forever.  Phase B launches the admitted requests
+// together (on the GPU: one persistent raster launch for all of them); the worker waits for
+// them, publishes their results, frees their arena ranges and takes the next batch.  Lanes
+// run independently, so several batches are on the device at once, and requests that
+// arrive meanwhile join the next batch of the first lane that frees up.
 #pragma once
 
 #include <chrono>
@@ -90,10 +91,10 @@ struct Item {
   int64_t instances = 0;  // reported back to the caller
 };
 
-// The device side.  measure: phase A for the items of a batch on `lane` (their slots are
-// assigned); returns once every item's cost (or an error status) is known.  launch: phase
-// B for the admitted items, asynchronously.  finish: waits for the lane's launched work and
-// sets each item's status and instance count.
+// The device side, called from the lane's own worker thread.  measure: phase A for the
+// items of a batch on `lane` (their slots are assigned); returns once every item's cost (or
+// an error status) is known.  launch: phase B for the admitted items.  finish: waits for the
+// lane's launched work and sets each item's status and instance count.
 template <class Request>
 struct Executor {
   std::function<void(int lane, std::vector<Item<Request>>&)> measure;
@@ -130,10 +131,8 @@ class Scheduler {
   // a request that could not be admitted waits at most `aging_s` before it blocks the
   // requests behind it.
   Scheduler(int lanes, int slots_per_lane, int64_t arena_units, double aging_s, Executor<Request> ex)
-      : spl_(slots_per_lane), aging_(aging_s), arena_(arena_units), ex_(std::move(ex)),
-        lanes_((size_t)lanes) {
-    dispatcher_ = std::thread([this] { dispatch(); });
-    for (int l = 0; l < lanes; ++l) finishers_.emplace_back([this, l] { complete(l); });
+      : spl_(slots_per_lane), aging_(aging_s), arena_(arena_units), ex_(std::move(ex)) {
+    for (int l = 0; l < lanes; ++l) workers_.emplace_back([this, l] { work(l); });
   }
 
   ~Scheduler() { shutdown(); }
@@ -145,8 +144,7 @@ class Scheduler {
       stop_ = true;
     }
     cv_.notify_all();
-    if (dispatcher_.joinable()) dispatcher_.join();
-    for (auto& t : finishers_)
+    for (auto& t : workers_)
       if (t.joinable()) t.join();
     std::lock_guard<std::mutex> lk(mu_);
     for (auto& kv : jobs_)
@@ -247,12 +245,6 @@ class Scheduler {
   }
 
  private:
-  struct Lane {
-    bool busy = false;       // a batch is being formed or is on the device
-    bool launched = false;   // its items await completion
-    std::vector<Item<Request>> items;
-  };
-
   static double now() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
   }
@@ -263,26 +255,16 @@ class Scheduler {
     j.t_done = now();
   }
 
-  int free_lane_locked() const {
-    for (size_t l = 0; l < lanes_.size(); ++l)
-      if (!lanes_[l].busy) return (int)l;
-    return -1;
-  }
-  bool any_busy_locked() const {
-    for (const Lane& ln : lanes_)
-      if (ln.busy) return true;
-    return false;
-  }
-
-  void dispatch() {
+  void work(int lane) {
     std::unique_lock<std::mutex> lk(mu_);
+    uint64_t seen_release = 0;   // releases seen when this lane last admitted nothing
+    bool waiting_memory = false;
     while (true) {
       cv_.wait(lk, [&] {
-        return stop_ || (!pending_.empty() && free_lane_locked() >= 0 && !blocked_);
+        return stop_ || (!pending_.empty() && (!waiting_memory || releases_ != seen_release));
       });
       if (stop_) return;
-      const int lane = free_lane_locked();
-      lanes_[(size_t)lane].busy = true;
+      waiting_memory = false;
       std::vector<Item<Request>> batch;
       while (!pending_.empty() && (int)batch.size() < spl_) {
         Job<Request>& j = jobs_[pending_.front()];
@@ -333,13 +315,12 @@ class Scheduler {
         pending_.push_front(r->ticket);
       }
       if (arena_.used() > arena_peak_) arena_peak_ = arena_.used();
-      Lane& ln = lanes_[(size_t)lane];
+      cv_done_.notify_all();
       if (admitted.empty()) {
-        ln.busy = false;
-        // nothing fits until running requests free memory (none running: the arena is
-        // empty and every cost <= capacity was admitted, so this cannot stall)
-        blocked_ = any_busy_locked();
-        cv_done_.notify_all();
+        // nothing fits until running requests free memory; if none is running the arena is
+        // empty and every cost <= capacity was admitted, so this cannot stall
+        waiting_memory = running_ > 0;
+        seen_release = releases_;
         cv_.notify_all();
         continue;
       }
@@ -347,37 +328,20 @@ class Scheduler {
       if (running_ > peak_running_) peak_running_ = running_;
       ++batches_;
       if ((int)admitted.size() > peak_batch_) peak_batch_ = (int)admitted.size();
+      if (!back.empty()) cv_.notify_all();   // another lane may take what was put back
       lk.unlock();
-      ex_.launch(lane, admitted);   // phase B, asynchronous
+      ex_.launch(lane, admitted);   // phase B
+      ex_.finish(lane, admitted);   // wait for this lane's batch
       lk.lock();
-      ln.items = std::move(admitted);
-      ln.launched = true;
-      cv_.notify_all();
-    }
-  }
-
-  void complete(int lane) {
-    std::unique_lock<std::mutex> lk(mu_);
-    Lane& ln = lanes_[(size_t)lane];
-    while (true) {
-      cv_.wait(lk, [&] { return ln.launched || (stop_ && !ln.busy); });
-      if (!ln.launched) return;   // stopping, nothing in flight on this lane
-      std::vector<Item<Request>> items = std::move(ln.items);
-      ln.items.clear();
-      lk.unlock();
-      ex_.finish(lane, items);
-      lk.lock();
-      for (Item<Request>& it : items) {
+      for (Item<Request>& it : admitted) {
         arena_.release(it.offset, it.cost);
         Job<Request>& j = jobs_[it.ticket];
         j.instances = it.instances;
         j.slot = lane * spl_ + it.slot;
         finish_locked(j, it.status);
       }
-      running_ -= (int)items.size();
-      ln.launched = false;
-      ln.busy = false;
-      blocked_ = false;   // memory was freed
+      running_ -= (int)admitted.size();
+      ++releases_;
       cv_done_.notify_all();
       cv_.notify_all();
     }
@@ -387,17 +351,15 @@ class Scheduler {
   const double aging_;
   Arena arena_;
   Executor<Request> ex_;
-  std::vector<Lane> lanes_;
   std::mutex mu_;
   std::condition_variable cv_, cv_done_;
   std::deque<uint64_t> pending_;
   std::unordered_map<uint64_t, Job<Request>> jobs_;
-  std::thread dispatcher_;
-  std::vector<std::thread> finishers_;
-  uint64_t next_ticket_ = 0;
+  std::vector<std::thread> workers_;
+  uint64_t next_ticket_ = 0, releases_ = 0;
   int64_t arena_peak_ = 0, batches_ = 0;
   int running_ = 0, peak_running_ = 0, peak_batch_ = 0;
-  bool stop_ = false, blocked_ = false;
+  bool stop_ = false;
 };
 
 }  // namespace gs_serve

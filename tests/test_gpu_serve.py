@@ -37,7 +37,7 @@ def test_mix_equals_alone():
         sc = S.room_scene(n, n_feat=D, sh_degree=deg, seed=50 + k)
         scenes.append(sc)
         tensors.append(U.upload(sc, bf16=bf))
-    server = L.Server(8 << 30, 3, dev.index)
+    server = L.Server(8 << 30, 16, dev.index)   # four lanes of up to four requests
     ids = [L.gs_serve_add_scene(server, t) for t in tensors]
     rng = np.random.default_rng(8)
     reqs = []
