@@ -99,7 +99,7 @@ struct gs_workspace {
   DevBuf<float> g2d;
   DevBuf<float> pose_partials;
   // per instance: sorted depth keys and ids, their ping-pong space, the slot's tile
-  DevBuf<uint32_t> inst_key, inst_id, inst_key2, inst_id2, inst_tile;
+  DevBuf<uint32_t> inst_key, inst_id, inst_key2, inst_id2;
   // per tile / pixel
   DevBuf<uint2> ranges;
   DevBuf<uint32_t> tile_order, queue;   // heavy-first tile order; persistent-kernel queues
@@ -118,7 +118,6 @@ struct gs_workspace {
   int W = 0, H = 0, TX = 0, TY = 0;
   int stage = 0;             // 1 projected, 2 binned, 3 rendered
   int64_t inst_bound = 0;    // host bound on I used for grids
-  const uint32_t* tile_sorted = nullptr;  // tile of every instance slot
   const uint32_t* id_sorted = nullptr;    // Gaussian id of every instance slot
   // timing
   bool timing = false;
@@ -238,7 +237,7 @@ cudaError_t ensure_inst(gs_workspace* ws, int64_t cap) {
   const size_t m = (size_t)std::max<int64_t>(cap, 1);
   cudaError_t e;
   if ((e = ws->inst_key.ensure(m)) || (e = ws->inst_id.ensure(m)) ||
-      (e = ws->inst_key2.ensure(m)) || (e = ws->inst_id2.ensure(m)) || (e = ws->inst_tile.ensure(m)))
+      (e = ws->inst_key2.ensure(m)) || (e = ws->inst_id2.ensure(m)))
     return e;
   return cudaSuccess;
 }
@@ -303,7 +302,6 @@ void gs_workspace_destroy(gs_workspace* ws) {
     ws->rec.release(); ws->depth_key.release(); ws->ntiles.release();
     ws->rect.release(); ws->item_max.release(); ws->g2d.release(); ws->pose_partials.release();
     ws->inst_key.release(); ws->inst_id.release(); ws->inst_key2.release(); ws->inst_id2.release();
-    ws->inst_tile.release();
     ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
     ws->tile_order.release(); ws->queue.release(); ws->tile_count.release(); ws->tile_cursor.release();
     ws->counters.release(); ws->stats64.release();
@@ -351,7 +349,7 @@ gs_status gs_workspace_bytes(gs_workspace* ws, int64_t* bytes) {
   auto add = [&b](const auto& buf) { b += buf.cap * sizeof(*buf.p); };
   add(ws->rec); add(ws->depth_key); add(ws->ntiles); add(ws->rect); add(ws->item_max);
   add(ws->g2d); add(ws->pose_partials);
-  add(ws->inst_key); add(ws->inst_id); add(ws->inst_key2); add(ws->inst_id2); add(ws->inst_tile);
+  add(ws->inst_key); add(ws->inst_id); add(ws->inst_key2); add(ws->inst_id2);
   add(ws->ranges); add(ws->tile_order); add(ws->queue); add(ws->tile_count); add(ws->tile_cursor);
   add(ws->T_final); add(ws->n_contrib); add(ws->counters); add(ws->stats64);
   *bytes = (int64_t)b;
@@ -440,11 +438,9 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   b.id0 = ws->inst_id.p;
   b.key1 = ws->inst_key2.p;
   b.id1 = ws->inst_id2.p;
-  b.tile_out = ws->inst_tile.p;
   b.counters = cnt;
   ws->ordered = launch_bin(b, st);
   ws->tile_counts_dirty = false;   // the scan cleared them
-  ws->tile_sorted = ws->inst_tile.p;
   ws->id_sorted = ws->inst_id.p;
   GS_TRY(cudaGetLastError());
   ws->inst_bound = std::min(bound, cap);
@@ -623,14 +619,20 @@ gs_status gs_get_instances(gs_workspace* ws, uint32_t* tiles_out, uint32_t* ids_
   const int64_t I = std::min<int64_t>(ws->h_counters[kCntInst], ws->inst_bound);
   if (n_out) *n_out = ws->h_counters[kCntInst];
   const int64_t m = std::min(I, cap);
-  if (m > 0 && tiles_out)
-    GS_TRY(cudaMemcpyAsync(tiles_out, ws->tile_sorted, m * 4, cudaMemcpyDeviceToHost, st));
+  const int ntl = ws->TX * ws->TY;
+  std::vector<uint2> rg((size_t)ntl);
   if (m > 0 && ids_out)
     GS_TRY(cudaMemcpyAsync(ids_out, ws->id_sorted, m * 4, cudaMemcpyDeviceToHost, st));
-  if (ranges_out)
-    GS_TRY(cudaMemcpyAsync(ranges_out, ws->ranges.p, sizeof(uint2) * (size_t)ws->TX * ws->TY,
+  if (ntl > 0)
+    GS_TRY(cudaMemcpyAsync(rg.data(), ws->ranges.p, sizeof(uint2) * (size_t)ntl,
                            cudaMemcpyDeviceToHost, st));
   GS_TRY(cudaStreamSynchronize(st));
+  if (ranges_out && ntl > 0) std::memcpy(ranges_out, rg.data(), sizeof(uint2) * (size_t)ntl);
+  if (tiles_out) {   // the tile of every slot, from the tile ranges
+    for (int t = 0; t < ntl; ++t)
+      for (int64_t j = rg[(size_t)t].x; j < (int64_t)rg[(size_t)t].y && j < m; ++j)
+        tiles_out[j] = (uint32_t)t;
+  }
   return GS_OK;
 }
 
@@ -729,13 +731,12 @@ gs_status ws_reserve_fixed(gs_workspace* ws, int64_t n_gauss, int64_t n_pixels, 
 }
 
 void ws_lend_instances(gs_workspace* ws, uint32_t* key0, uint32_t* id0, uint32_t* key1,
-                       uint32_t* id1, uint32_t* tile, int64_t cap) {
+                       uint32_t* id1, int64_t cap) {
   const size_t m = (size_t)std::max<int64_t>(cap, 0);
   ws->inst_key.lend(key0, m);
   ws->inst_id.lend(id0, m);
   ws->inst_key2.lend(key1, m);
   ws->inst_id2.lend(id1, m);
-  ws->inst_tile.lend(tile, m);
 }
 
 bool ws_fits(const gs_workspace* ws, int64_t n_gauss, int64_t n_pixels, int64_t n_tiles) {

@@ -34,8 +34,7 @@ constexpr size_t oK0 = al(oRect + kNaMaxGauss * 8);        // instance depth key
 constexpr size_t oI0 = al(oK0 + kNaMaxInst * 4);
 constexpr size_t oK1 = al(oI0 + kNaMaxInst * 4);          // their ping-pong space
 constexpr size_t oI1 = al(oK1 + kNaMaxInst * 4);
-constexpr size_t oTile = al(oI1 + kNaMaxInst * 4);        // tile of every slot
-constexpr size_t oTf = al(oTile + kNaMaxInst * 4);
+constexpr size_t oTf = al(oI1 + kNaMaxInst * 4);
 constexpr size_t oNc = al(oTf + kNaMaxPix * 4);
 constexpr size_t oRanges = al(oNc + kNaMaxPix * 4);
 constexpr size_t oOrder = al(oRanges + kNaMaxTiles * 8);
@@ -129,7 +128,6 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   uint2* rect = reinterpret_cast<uint2*>(base + oRect);
   uint32_t *k0 = reinterpret_cast<uint32_t*>(base + oK0), *i0 = reinterpret_cast<uint32_t*>(base + oI0);
   uint32_t *k1 = reinterpret_cast<uint32_t*>(base + oK1), *i1 = reinterpret_cast<uint32_t*>(base + oI1);
-  uint32_t* tile_of = reinterpret_cast<uint32_t*>(base + oTile);
   float* Tf = reinterpret_cast<float*>(base + oTf);
   uint32_t* nc = reinterpret_cast<uint32_t*>(base + oNc);
   uint2* ranges = reinterpret_cast<uint2*>(base + oRanges);
@@ -143,7 +141,7 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   // the tile counts the projection adds to, and the queues, which reset themselves but are
   // cleared here as well since nothing else initialises this array)
   if (cudaMemsetAsync(cnt, 0, kCntNum * 4, st) != cudaSuccess ||
-      cudaMemsetAsync(queue, 0, 4 * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(queue, 0, 8 * 4, st) != cudaSuccess ||
       cudaMemsetAsync(tcount, 0, ntl * 4, st) != cudaSuccess)
     return GS_ERR_CUDA;
   launch_project(*scene, cd, rec, key, nt, rect, cnt, tcount, st);
@@ -173,7 +171,6 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   b.id0 = i0;
   b.key1 = k1;
   b.id1 = i1;
-  b.tile_out = tile_of;
   b.counters = cnt;
   const bool ordered = launch_bin(b, st);
   const TileQueue tq{queue, queue + 1, ordered ? order : nullptr, (int)ntl};

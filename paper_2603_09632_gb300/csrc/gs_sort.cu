@@ -14,8 +14,9 @@
 //   4. sort: one block per tile sorts its range by depth with a stable LSD radix sort in
 //      shared memory (8-bit digits; a pass whose digit is the same for the whole range is
 //      skipped), then orders runs of equal depth by id, which makes the order the total
-//      (depth, id) order whatever order the scatter left.  Ranges longer than shared
-//      memory holds are sorted in chunks through global ping-pong buffers.
+//      (depth, id) order whatever order the scatter left, and writes the sorted ids back.
+//      Ranges longer than shared memory holds are sorted in chunks through global
+//      ping-pong buffers.
 // Steps 1 and 3 (warp_tile_instances) flatten the instances of a warp's 32 Gaussians and
 // aggregate the atomic additions of equal tiles within a warp, so a Gaussian covering many
 // tiles is spread over the warp instead of serialising one thread.
@@ -303,12 +304,11 @@ __device__ __forceinline__ uint32_t block_diff_bits(uint32_t v_or, uint32_t v_an
 }
 
 // One block per tile (persistent, heavy-first): sort the tile's range by (depth, id).
-// Final keys and ids are left in (key0, id0); (key1, id1) is the ping-pong space of ranges
-// longer than kSeg.  tile_out[slot] receives the tile of every sorted slot.
+// The sorted ids are left in id0 (the sorted keys are not written back: nothing reads
+// them); (key1, id1) is the ping-pong space of ranges longer than kSeg.
 __global__ void __launch_bounds__(kThreads)
 k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict__ key0,
-           uint32_t* __restrict__ id0, uint32_t* __restrict__ key1, uint32_t* __restrict__ id1,
-           uint32_t* __restrict__ tile_out) {
+           uint32_t* __restrict__ id0, uint32_t* __restrict__ key1, uint32_t* __restrict__ id1) {
   __shared__ uint32_t s_k[2][kSeg], s_v[2][kSeg];
   __shared__ uint32_t s_w[kWarps * kRadix];
   __shared__ uint32_t s_dstart[kRadix], s_run[kRadix], s_cnt[kRadix];
@@ -326,7 +326,6 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
     const uint2 rg = ranges[tile];
     const int s = (int)rg.x, n = (int)(rg.y - rg.x);
     if (n <= 1) {
-      if (n == 1 && threadIdx.x == 0) tile_out[s] = (uint32_t)tile;
       __syncthreads();
       continue;
     }
@@ -363,11 +362,7 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
       }
       order_ties(s_k[cur], s_v[cur], n);
       __syncthreads();
-      for (int i = threadIdx.x; i < n; i += kThreads) {
-        key0[s + i] = s_k[cur][i];
-        id0[s + i] = s_v[cur][i];
-        tile_out[s + i] = (uint32_t)tile;
-      }
+      for (int i = threadIdx.x; i < n; i += kThreads) id0[s + i] = s_v[cur][i];
     } else {
       // long range: LSD passes through global memory, chunks of kSeg taken in order
       uint32_t *ka = key0 + s, *ia = id0 + s, *kb = key1 + s, *ib = id1 + s;
@@ -426,14 +421,8 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
       }
       order_ties(ka, ia, n);
       __syncthreads();
-      const bool moved = ka != key0 + s;
-      for (int i = threadIdx.x; i < n; i += kThreads) {
-        if (moved) {
-          key0[s + i] = ka[i];
-          id0[s + i] = ia[i];
-        }
-        tile_out[s + i] = (uint32_t)tile;
-      }
+      if (ia != id0 + s)
+        for (int i = threadIdx.x; i < n; i += kThreads) id0[s + i] = ia[i];
     }
     __syncthreads();   // shared memory and s_tile are reused by the next tile
   }
@@ -517,7 +506,7 @@ bool launch_bin(const BinArgs& b, cudaStream_t st) {
   // per-tile sort: persistent blocks over the tiles, heaviest first
   const TileQueue tq{b.queue, b.queue + 1, order, T};
   const int grid = persistent_grid(k_bin_sort, kThreads, 0, T);
-  k_bin_sort<<<grid, kThreads, 0, st>>>(tq, b.ranges, b.key0, b.id0, b.key1, b.id1, b.tile_out);
+  k_bin_sort<<<grid, kThreads, 0, st>>>(tq, b.ranges, b.key0, b.id0, b.key1, b.id1);
   note_launch();
   return order != nullptr;
 }
