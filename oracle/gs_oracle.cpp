@@ -23,6 +23,11 @@
 // precision (and, for the key-affecting projection, its exact operation
 // order), double is the FP64 reference.  Build with -ffp-contract=off so
 // that float results are the IEEE results of the written expressions.
+// A third mode evaluates everything in double but takes each Gaussian's
+// discrete projection decisions -- visibility, 3-sigma tile rectangle and
+// the depth that orders the tile lists -- from the float projection: the
+// readings define those with separately rounded float operations, so this
+// is the same function in exact arithmetic (the "mixed" entry points).
 //
 // Parity pins: see tests/test_oracle_*.py (closed forms, invariants, brute
 // force, finite differences, SH orthonormality, Monte-Carlo/FD projection).
@@ -127,6 +132,7 @@ struct Proj {
   S det;
   S conic[3];             // A, B, C of Sigma'^{-1}
   S u, v, depth;
+  S key;                  // depth that orders the tile lists (the float depth in mixed mode)
   int radius;
   int rect[4];            // x0, y0, x1, y1 in tiles, [x0,x1) x [y0,y1)
   S dir[3], dlen;         // unit view direction and the length it came from
@@ -137,16 +143,19 @@ struct Proj {
 // Sigma = R S S^T R^T, Sigma' = J W Sigma W^T J^T (App. A) with the readings:
 // guard band 1.3 x half-FOV on J, +0.3 px^2 low-pass on the diagonal, 3-sigma radius.
 // The operation order below is the key-affecting convention (see design notes).
+// d32 (mixed mode): the float projection of the same Gaussian, whose visibility, tile
+// rectangle and depth key are taken as they are.
 template <class S>
 Proj<S> project_one(const Cam<S>& k, const S* mu, const S* s, const S* q, const S* sh,
-                    int deg) {
+                    int deg, const Proj<float>* d32 = nullptr) {
   Proj<S> P;
+  if (d32 && !d32->valid) return P;
   const S* R = k.R;
   P.p[0] = ((R[0] * mu[0] + R[1] * mu[1]) + R[2] * mu[2]) + k.t[0];
   P.p[1] = ((R[3] * mu[0] + R[4] * mu[1]) + R[5] * mu[2]) + k.t[1];
   P.p[2] = ((R[6] * mu[0] + R[7] * mu[1]) + R[8] * mu[2]) + k.t[2];
   const S x = P.p[0], y = P.p[1], z = P.p[2];
-  if (!(z > k.near_z)) return P;
+  if (!d32 && !(z > k.near_z)) return P;
 
   S qq = ((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3];
   P.qlen = std::sqrt(qq);
@@ -208,7 +217,7 @@ Proj<S> project_one(const Cam<S>& k, const S* mu, const S* s, const S* q, const 
   const S c = (T11 * j11 + T12 * j12) + (S)0.3;
   P.cov[0] = a; P.cov[1] = b; P.cov[2] = c;
   P.det = a * c - b * b;
-  if (!(P.det > 0)) return P;
+  if (!d32 && !(P.det > 0)) return P;
   const S mid = (S)0.5 * (a + c);
   const S lam = mid + std::sqrt(std::max((S)0.1, mid * mid - P.det));
   const S r = std::ceil((S)3 * std::sqrt(lam));
@@ -223,8 +232,14 @@ Proj<S> project_one(const Cam<S>& k, const S* mu, const S* s, const S* q, const 
   P.rect[1] = clampi(std::floor((P.v - r) / (S)TILE), k.TY);
   P.rect[3] = clampi(std::floor((P.v + r) / (S)TILE) + (S)1, k.TY);
   P.radius = (int)std::min(r, (S)2147483647.0);
-  if (k.thresholds && (P.rect[2] <= P.rect[0] || P.rect[3] <= P.rect[1])) return P;
+  if (d32) {
+    for (int i = 0; i < 4; ++i) P.rect[i] = d32->rect[i];
+    P.radius = d32->radius;
+  } else if (k.thresholds && (P.rect[2] <= P.rect[0] || P.rect[3] <= P.rect[1])) {
+    return P;
+  }
   P.depth = z;
+  P.key = d32 ? (S)d32->depth : z;
   P.conic[0] = c / P.det;
   P.conic[1] = -b / P.det;
   P.conic[2] = a / P.det;
@@ -257,13 +272,14 @@ struct Inputs {
 };
 
 template <class S>
-std::vector<Proj<S>> project_all(const Cam<S>& k, const Inputs<S>& in) {
+std::vector<Proj<S>> project_all(const Cam<S>& k, const Inputs<S>& in,
+                                 const std::vector<Proj<float>>* d32 = nullptr) {
   const int K = (in.deg + 1) * (in.deg + 1);
   std::vector<Proj<S>> P((size_t)in.n);
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < in.n; ++i)
     P[i] = project_one<S>(k, in.means + 3 * i, in.scales + 3 * i, in.quats + 4 * i,
-                          in.sh + (size_t)K * 3 * i, in.deg);
+                          in.sh + (size_t)K * 3 * i, in.deg, d32 ? &(*d32)[(size_t)i] : nullptr);
   return P;
 }
 
@@ -277,7 +293,7 @@ bool covers(const Proj<S>& P, const Cam<S>& k, int tx, int ty) {
 
 template <class S>
 bool depth_less(const std::vector<Proj<S>>& P, int64_t a, int64_t b) {
-  if (P[a].depth != P[b].depth) return P[a].depth < P[b].depth;
+  if (P[a].key != P[b].key) return P[a].key < P[b].key;
   return a < b;
 }
 
@@ -307,7 +323,7 @@ void tile_lists(const std::vector<Proj<S>>& P, const Cam<S>& k, std::vector<uint
   ids.clear();
   for (int64_t i = 0; i < (int64_t)P.size(); ++i) {
     if (!P[i].valid) continue;
-    const uint32_t db = float_bits((float)P[i].depth);
+    const uint32_t db = float_bits((float)P[i].key);
     for (int ty = P[i].rect[1]; ty < P[i].rect[3]; ++ty)
       for (int tx = P[i].rect[0]; tx < P[i].rect[2]; ++tx) {
         keys.push_back(((uint64_t)(ty * k.TX + tx) << 32) | db);
@@ -462,8 +478,9 @@ std::vector<std::vector<int64_t>> tile_candidates(const CandidateSource<S>& src,
 
 template <class S>
 int render(const Inputs<S>& in, const Cam<S>& k, int mode, const int64_t* pix, int64_t npix,
-           S* rgb, S* depth, S* alpha, S* feat, S* T_final, int32_t* n_contrib, int32_t* flags) {
-  auto P = project_all<S>(k, in);
+           S* rgb, S* depth, S* alpha, S* feat, S* T_final, int32_t* n_contrib, int32_t* flags,
+           const std::vector<Proj<float>>* d32 = nullptr) {
+  auto P = project_all<S>(k, in, d32);
   CandidateSource<S> src(P, k, mode);
   auto pixels = pixel_set<S>(k, pix, npix);
   auto per_tile = tile_candidates<S>(src, k, pixels);
@@ -688,8 +705,9 @@ void project_backward(const Cam<S>& k, const Inputs<S>& in, const std::vector<Pr
 template <class S>
 int backward(const Inputs<S>& in, const Cam<S>& k, int mode, const int64_t* pix, int64_t npix,
              const S* g_rgb, const S* g_depth, const S* g_alpha, const S* g_feat, S* g_means,
-             S* g_scales, S* g_quats, S* g_opac, S* g_sh, S* g_featp, S* g_pose, S* g2d_out) {
-  auto P = project_all<S>(k, in);
+             S* g_scales, S* g_quats, S* g_opac, S* g_sh, S* g_featp, S* g_pose, S* g2d_out,
+             const std::vector<Proj<float>>* d32 = nullptr) {
+  auto P = project_all<S>(k, in, d32);
   CandidateSource<S> src(P, k, mode);
   auto pixels = pixel_set<S>(k, pix, npix);
   auto per_tile = tile_candidates<S>(src, k, pixels);
@@ -827,6 +845,53 @@ OR_RENDER(double, f64)
   }
 OR_BACKWARD(float, f32)
 OR_BACKWARD(double, f64)
+
+// Mixed mode: double arithmetic with the float projection's visibility, tile rectangles and
+// list order (the same function as the float path in exact arithmetic; see the header).
+struct FloatCopy {
+  std::vector<float> means, scales, quats, opac, sh;
+};
+static std::vector<Proj<float>> float_decisions(int64_t n, const double* means,
+                                                const double* scales, const double* quats,
+                                                const double* opac, const double* sh, int deg,
+                                                const double* cam) {
+  const int K = (deg + 1) * (deg + 1);
+  FloatCopy f;
+  f.means.assign(means, means + 3 * n);
+  f.scales.assign(scales, scales + 3 * n);
+  f.quats.assign(quats, quats + 4 * n);
+  f.opac.assign(opac, opac + n);
+  f.sh.assign(sh, sh + (size_t)K * 3 * n);
+  const Cam<float> k = make_cam<float>(cam, 1);
+  auto in = make_inputs<float>(n, f.means.data(), f.scales.data(), f.quats.data(), f.opac.data(),
+                               f.sh.data(), deg, nullptr, 0);
+  return project_all<float>(k, in);
+}
+
+int or_render_mixed(int64_t n, const double* means, const double* scales, const double* quats,
+                    const double* opac, const double* sh, int deg, const double* feat, int D,
+                    const double* cam, int mode, const int64_t* pix, int64_t npix, double* rgb,
+                    double* depth, double* alpha, double* featout, double* T_final,
+                    int32_t* n_contrib, int32_t* flags) {
+  const auto d32 = float_decisions(n, means, scales, quats, opac, sh, deg, cam);
+  const Cam<double> k = make_cam<double>(cam, 1);
+  auto in = make_inputs<double>(n, means, scales, quats, opac, sh, deg, feat, D);
+  return render<double>(in, k, mode, pix, npix, rgb, depth, alpha, featout, T_final, n_contrib,
+                        flags, &d32);
+}
+
+int or_backward_mixed(int64_t n, const double* means, const double* scales, const double* quats,
+                      const double* opac, const double* sh, int deg, const double* feat, int D,
+                      const double* cam, int mode, const int64_t* pix, int64_t npix,
+                      const double* g_rgb, const double* g_depth, const double* g_alpha,
+                      const double* g_feat, double* g_means, double* g_scales, double* g_quats,
+                      double* g_opac, double* g_sh, double* g_featp, double* g_pose, double* g2d) {
+  const auto d32 = float_decisions(n, means, scales, quats, opac, sh, deg, cam);
+  const Cam<double> k = make_cam<double>(cam, 1);
+  auto in = make_inputs<double>(n, means, scales, quats, opac, sh, deg, feat, D);
+  return backward<double>(in, k, mode, pix, npix, g_rgb, g_depth, g_alpha, g_feat, g_means,
+                          g_scales, g_quats, g_opac, g_sh, g_featp, g_pose, g2d, &d32);
+}
 
 // Real SH basis values [npts, 16] for testing orthonormality.
 void or_sh_basis_f64(int deg, int64_t npts, const double* dirs, double* Y) {

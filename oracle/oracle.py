@@ -5,7 +5,10 @@ CPU-baseline leg of ``bench.py``.  The product library never loads it.
 
 Every function takes numpy arrays from :mod:`synth.scenes` (a ``Scene`` and a
 ``Camera``) and returns numpy arrays.  ``prec`` is ``"f32"`` (mirrors the GPU's
-precision and key-affecting operation order) or ``"f64"``.
+precision and key-affecting operation order), ``"f64"``, or, for ``render`` and
+``backward``, ``"mixed"``: double arithmetic with each Gaussian's visibility, tile
+rectangle and list order taken from the float projection (which the readings define in
+float), i.e. the same function as the float path evaluated exactly.
 """
 from __future__ import annotations
 
@@ -53,6 +56,10 @@ def lib():
                 getattr(L, f"or_backward_{suf}").argtypes = [i64, P, P, P, P, P, i32, P, i32, P,
                                                              i32, i32, P, i64, P, P, P, P, P, P,
                                                              P, P, P, P, P, P]
+            L.or_render_mixed.argtypes = [i64, P, P, P, P, P, i32, P, i32, P, i32, P, i64, P,
+                                          P, P, P, P, P, P]
+            L.or_backward_mixed.argtypes = [i64, P, P, P, P, P, i32, P, i32, P, i32, P, i64, P,
+                                            P, P, P, P, P, P, P, P, P, P, P]
             L.or_tile_lists_f32.argtypes = [i64, P, P, P, P, P, i32, P, i64, P, P, P]
             L.or_tile_lists_f32.restype = i64
             L.or_num_threads.argtypes = [i32]
@@ -72,7 +79,7 @@ def cam_array(cam) -> np.ndarray:
 
 
 def _dt(prec):
-    return np.float32 if prec == "f32" else np.float64
+    return np.float32 if prec == "f32" else np.float64   # "f64" and "mixed" are double
 
 
 def _scene_arrays(scene, prec, feats=None):
@@ -139,11 +146,19 @@ def render(scene, cam, prec="f32", thresholds=True, mode=1, pixels=None, feats=N
                feat=np.zeros((D, npix), dt), T_final=np.zeros(npix, dt),
                n_contrib=np.zeros(npix, np.int32), flags=np.zeros(npix, np.int32))
     camv = cam_array(cam)
-    getattr(lib(), f"or_render_{prec}")(
-        scene.n, _p(means), _p(scales), _p(quats), _p(opac), _p(sh), scene.sh_degree, _p(feat), D,
-        _p(camv), int(thresholds), int(mode), _p(pix), npix, _p(out["rgb"]), _p(out["depth"]),
-        _p(out["alpha"]), _p(out["feat"]), _p(out["T_final"]), _p(out["n_contrib"]),
-        _p(out["flags"]))
+    if prec == "mixed":
+        assert thresholds, "the mixed mode takes the float decisions of the thresholded path"
+        lib().or_render_mixed(
+            scene.n, _p(means), _p(scales), _p(quats), _p(opac), _p(sh), scene.sh_degree, _p(feat),
+            D, _p(camv), int(mode), _p(pix), npix, _p(out["rgb"]), _p(out["depth"]),
+            _p(out["alpha"]), _p(out["feat"]), _p(out["T_final"]), _p(out["n_contrib"]),
+            _p(out["flags"]))
+    else:
+        getattr(lib(), f"or_render_{prec}")(
+            scene.n, _p(means), _p(scales), _p(quats), _p(opac), _p(sh), scene.sh_degree, _p(feat),
+            D, _p(camv), int(thresholds), int(mode), _p(pix), npix, _p(out["rgb"]), _p(out["depth"]),
+            _p(out["alpha"]), _p(out["feat"]), _p(out["T_final"]), _p(out["n_contrib"]),
+            _p(out["flags"]))
     out["rgb"] = out["rgb"].reshape((3,) + shp)
     out["feat"] = out["feat"].reshape((D,) + shp)
     for k in ("depth", "alpha", "T_final", "n_contrib", "flags"):
@@ -174,11 +189,18 @@ def backward(scene, cam, grads, prec="f32", thresholds=True, mode=1, pixels=None
                opacities=np.zeros(n, dt), sh=np.zeros((n, K, 3), dt), feats=np.zeros((n, D), dt),
                pose=np.zeros(6, dt), g2d=np.zeros((n, 10), dt))
     camv = cam_array(cam)
-    getattr(lib(), f"or_backward_{prec}")(
-        n, _p(means), _p(scales), _p(quats), _p(opac), _p(sh), scene.sh_degree, _p(feat), D,
-        _p(camv), int(thresholds), int(mode), _p(pix), npix, _p(gr), _p(gd), _p(ga), _p(gf),
-        _p(out["means"]), _p(out["scales"]), _p(out["quats"]), _p(out["opacities"]), _p(out["sh"]),
-        _p(out["feats"]), _p(out["pose"]), _p(out["g2d"]))
+    outs = (_p(out["means"]), _p(out["scales"]), _p(out["quats"]), _p(out["opacities"]),
+            _p(out["sh"]), _p(out["feats"]), _p(out["pose"]), _p(out["g2d"]))
+    if prec == "mixed":
+        assert thresholds, "the mixed mode takes the float decisions of the thresholded path"
+        lib().or_backward_mixed(
+            n, _p(means), _p(scales), _p(quats), _p(opac), _p(sh), scene.sh_degree, _p(feat), D,
+            _p(camv), int(mode), _p(pix), npix, _p(gr), _p(gd), _p(ga), _p(gf), *outs)
+    else:
+        getattr(lib(), f"or_backward_{prec}")(
+            n, _p(means), _p(scales), _p(quats), _p(opac), _p(sh), scene.sh_degree, _p(feat), D,
+            _p(camv), int(thresholds), int(mode), _p(pix), npix, _p(gr), _p(gd), _p(ga), _p(gf),
+            *outs)
     return out
 
 

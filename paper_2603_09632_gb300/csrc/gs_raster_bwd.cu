@@ -13,8 +13,9 @@
 // taken in chunks of 256 entries; each chunk is gathered once, entries that no pixel of
 // the tile can blend are dropped (conservative test, outputs unchanged) and the rest are
 // compacted into shared memory.  The compacted chunk is processed in batches of B
-// Gaussians.  Phase 1 (one thread per pixel) writes w, dL/dsigma and dL/do of each
-// (pixel, Gaussian) pair to shared memory.  Phase 2 reduces over the 256 pixels of the
+// Gaussians.  Phase 1 (one thread per pixel) writes w and dL/do of each (pixel, Gaussian)
+// pair to shared memory (dL/dsigma = -o dL/do where the alpha cap does not hold, so it is
+// not stored).  Phase 2 reduces over the 256 pixels of the
 // tile: the feature gradient is the contraction W^T g_F with 4x4 register blocks (pixel
 // parts summed through per-warp partials in shared memory, in a fixed order), and
 // colour/depth/opacity sums and the pixel moments sum_p dL/dsigma * (1, x, y, xx, xy, yy)
@@ -40,8 +41,8 @@ constexpr int kWS = kT + 4;    // row stride of the j-major pair arrays (floats)
 template <int DP, bool FO = false>
 struct BwdCfg {
   // Gaussians per batch: 8 where a 16-Gaussian batch would leave room for only one
-  // resident CTA (64 channels features-only, 32 channels with every gradient)
-  static constexpr int B = (DP >= 64 && FO) || (DP == 32 && !FO) ? 8 : 16;
+  // resident CTA (64 channels features-only)
+  static constexpr int B = (DP >= 64 && FO) ? 8 : 16;
   static constexpr int ES = DP + 4;                     // row stride of s_E (floats)
   static constexpr int JB = B / 4;                      // 4x4 blocks of the contraction
   static constexpr int CB = DP / 4;
@@ -55,7 +56,7 @@ struct BwdCfg {
   static_assert(TASKS == 0 || TASKS % 32 == 0 || 32 % TASKS == 0, "tasks tile the warps");
   static constexpr size_t base_floats =
       (size_t)kT * ES           // s_E: upstream feature gradient per pixel
-      + (size_t)(FO ? 1 : 3) * B * kWS   // s_W (and s_GS, s_GO unless FO), j-major
+      + (size_t)(FO ? 1 : 2) * B * kWS   // s_W (and s_GO unless FO), j-major
       + (size_t)(FO ? 0 : 2) * B * DP;  // s_f: batch features, double buffered (not when FO)
   // Feature-gradient sums of a batch: one partial [B][DP] per warp (parts of a warp merged
   // by shuffles) or per part (a part spanning several warps), added in order by the flush:
@@ -158,9 +159,8 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
   extern __shared__ __align__(16) float smem[];
   float* s_E = smem;                          // [kT][ES]
   float* s_W = s_E + kT * Cfg::ES;            // [B][kWS]
-  float* s_GS = s_W + B * kWS;                // (not allocated when FO)
-  float* s_GO = s_GS + B * kWS;
-  float* s_fb = s_W + (FO ? 1 : 3) * B * kWS; // [2][B][DP]
+  float* s_GO = s_W + B * kWS;                // (not allocated when FO)
+  float* s_fb = s_W + (FO ? 1 : 2) * B * kWS; // [2][B][DP]
   float* s_outF = s_fb + (FO ? 0 : 2) * B * DP;   // [NPART][B][DP] partial sums
 
   const int t = threadIdx.x;
@@ -298,7 +298,7 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
 
         // phase 1: per pixel, reverse over the batch
         for (int j = B - 1; j >= 0; --j) {
-          float w = 0.f, gs = 0.f, go = 0.f;
+          float w = 0.f, go = 0.f;
           if ((live >> j & 1u) && s_orig[jb0 + j] < nc) {
             const float4 r0 = s_r0[jb0 + j];
             const float4 r1 = s_r1[jb0 + j];
@@ -328,20 +328,16 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
                 const float dot = (d0 + d1) + (d2 + d3);
                 const float galpha = T * (dot - s_run) + gAT * inv;
                 s_run = a * dot + (1.f - a) * s_run;
-                if (oG <= kAlphaMax) {
-                  go = galpha * G;
-                  gs = -galpha * a;
-                }
+                // dL/do = galpha G; dL/dsigma = -galpha a = -o dL/do (phase 2b scales the
+                // moments of dL/do by -o); both zero where the 0.99 cap holds alpha
+                if (oG <= kAlphaMax) go = galpha * G;
                 }
               }
             }
           }
           if (live >> j & 1u) {   // entries not live for this strip are never read
             s_W[j * kWS + t] = w;
-            if constexpr (!FO) {
-              s_GS[j * kWS + t] = gs;
-              s_GO[j * kWS + t] = go;
-            }
+            if constexpr (!FO) s_GO[j * kWS + t] = go;
           }
         }
         __syncthreads();
@@ -443,7 +439,8 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
         if constexpr (!FO) {
           constexpr int G = Cfg::G;
           const int j = t / G, pg = t % G;
-          float m1 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+          // moments of dL/do (so = its sum); those of dL/dsigma are -o times these
+          float mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
           float so = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sz = 0.f;
           // strip by strip: the G lanes of Gaussian j skip whole strips it cannot reach
           constexpr int PPS = 32 / G;   // pixels per strip per lane
@@ -452,15 +449,14 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
   #pragma unroll
             for (int u = 0; u < PPS; ++u) {
             const int q = ws * 32 + pg + u * G;
-            const float w = s_W[j * kWS + q], gs = s_GS[j * kWS + q], go = s_GO[j * kWS + q];
+            const float w = s_W[j * kWS + q], go = s_GO[j * kWS + q];
             const float4 e = s_E4[q];
             const float x = (float)strip_px(q) - 7.5f, y = (float)strip_py(q) - 7.5f;
-            m1 += gs;
-            mx = fmaf(gs, x, mx);
-            my = fmaf(gs, y, my);
-            mxx = fmaf(gs * x, x, mxx);
-            mxy = fmaf(gs * x, y, mxy);
-            myy = fmaf(gs * y, y, myy);
+            mx = fmaf(go, x, mx);
+            my = fmaf(go, y, my);
+            mxx = fmaf(go * x, x, mxx);
+            mxy = fmaf(go * x, y, mxy);
+            myy = fmaf(go * y, y, myy);
             so += go;
             sr = fmaf(w, e.x, sr);
             sg = fmaf(w, e.y, sg);
@@ -470,7 +466,6 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
           }
   #pragma unroll
           for (int o = G / 2; o > 0; o >>= 1) {
-            m1 += __shfl_xor_sync(0xffffffffu, m1, o);
             mx += __shfl_xor_sync(0xffffffffu, mx, o);
             my += __shfl_xor_sync(0xffffffffu, my, o);
             mxx += __shfl_xor_sync(0xffffffffu, mxx, o);
@@ -488,6 +483,13 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
             // moments are about the tile centre: pixel offset dx = x - uc with uc = u - centre
             const float uc = r0.x - ((float)tx0 + 8.f), vc = r0.y - ((float)ty0 + 8.f);
             const float A = r0.z, Bq = r0.w, C = r1.x;
+            const float no = -r1.y;                                        // -o
+            const float m1 = no * so;
+            mx *= no;
+            my *= no;
+            mxx *= no;
+            mxy *= no;
+            myy *= no;
             const float sdx = mx - uc * m1, sdy = my - vc * m1;            // sum gs dx, sum gs dy
             const float sdxx = mxx - 2.f * uc * mx + uc * uc * m1;         // sum gs dx^2
             const float sdyy = myy - 2.f * vc * my + vc * vc * m1;

@@ -83,30 +83,40 @@ def mask_flagged(grads, flags):
     return out, int(bad.sum())
 
 
-def grad_violations(got, ref, rtol=GRAD_RTOL, floor=GRAD_FLOOR):
-    """Entries with |got - ref| > rtol |ref| + floor max|ref|: (count, worst ratio of the
-    error to its bound, number of entries compared)."""
+def grad_violations(got, ref, rtol=GRAD_RTOL, floor=GRAD_FLOOR, ref_alt=None):
+    """Entries with |got - ref| > rtol |ref| + floor max|ref| (+ |ref - ref_alt|): (count,
+    worst ratio of the error to its bound, number of entries compared)."""
     g = np.asarray(got, np.float64).reshape(-1)
     r = np.asarray(ref, np.float64).reshape(-1)
     if r.size == 0:
         return 0, 0.0, 0
     bound = rtol * np.abs(r) + floor * max(np.abs(r).max(), 1e-30)
+    if ref_alt is not None:
+        bound = bound + np.abs(r - np.asarray(ref_alt, np.float64).reshape(-1))
     err = np.abs(g - r)
     ratio = err / bound
     return int((err > bound).sum()), float(ratio.max()), int(r.size)
 
 
-def assert_grads_close(got, ref, keys, rtol=GRAD_RTOL, floor=GRAD_FLOOR, norm_tol=1e-3, label=""):
+def assert_grads_close(got, ref, keys, rtol=GRAD_RTOL, floor=GRAD_FLOOR, norm_tol=1e-3, label="",
+                       ref_alt=None):
     """Every entry of every gradient within its bound, and the relative Frobenius error of
-    each tensor within ``norm_tol``.  Returns {key: (violations, worst ratio, entries)}."""
+    each tensor within ``norm_tol``.  ``ref_alt``: a second evaluation of the same gradients
+    (the oracle's mixed mode next to its float mode); each entry's bound then grows by the
+    two evaluations' disagreement, which is ~0 where the gradient is well conditioned and
+    the float oracle's own error where it is not.  Returns {key: (violations, worst ratio,
+    entries)}."""
     stats, bad = {}, []
     for k in keys:
         g, r = got[k], ref[k]
         if g is None and r is None:
             continue
-        n, worst, m = grad_violations(g, r, rtol, floor)
+        alt = None if ref_alt is None else ref_alt[k]
+        n, worst, m = grad_violations(g, r, rtol, floor, alt)
         rel = rel_err(g, r)
         stats[k] = (n, worst, m)
+        if alt is not None:   # how much the conditioning term contributed, for the report
+            stats[k] = (n, worst, m, grad_violations(g, r, rtol, floor)[1])
         if n or rel > norm_tol:
             bad.append((k, f"{n}/{m} entries over the bound (worst {worst:.3g}x)", f"rel {rel:.3g}"))
     _report(label, stats)
@@ -121,6 +131,7 @@ def _report(label, stats):
     path = os.environ.get("GS_PARITY_REPORT")
     if path:
         with open(path, "a") as f:
-            f.write(json.dumps({"case": label, "grads": {k: {"violations": v[0], "worst": v[1],
-                                                             "entries": v[2]}
-                                                         for k, v in stats.items()}}) + "\n")
+            f.write(json.dumps({"case": label, "grads": {
+                k: dict({"violations": v[0], "worst": v[1], "entries": v[2]},
+                        **({"worst_without_conditioning": v[3]} if len(v) > 3 else {}))
+                for k, v in stats.items()}}) + "\n")

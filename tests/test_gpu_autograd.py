@@ -42,8 +42,8 @@ def _autograd_grads(sc, cam, g):
 def _oracle_in_leaf_coords(oracle, sc, cam, g, thresholds=True):
     sc64 = S.Scene(**{k: np.asarray(getattr(sc, k), np.float32).astype(np.float64) for k in
                       ("means", "scales", "quats", "opacities", "sh", "feats")}, sh_degree=sc.sh_degree)
-    b = oracle.backward(sc64, cam, {k: v.astype(np.float64) for k, v in g.items()}, "f64",
-                        thresholds=thresholds)
+    b = oracle.backward(sc64, cam, {k: v.astype(np.float64) for k, v in g.items()},
+                        "mixed" if thresholds else "f64", thresholds=thresholds)
     o = sc64.opacities
     return dict(means=b["means"], log_scales=b["scales"] * sc64.scales, quats=b["quats"],
                 logits=b["opacities"] * o * (1 - o), sh=b["sh"], feats=b["feats"], xi=b["pose"])

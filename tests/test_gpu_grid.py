@@ -103,6 +103,7 @@ def test_grid_backward_matches_oracle(OG, room, grid):
     got = rast.backward(scene, c, gt["rgb"], gt["depth"], gt["alpha"], gt["feat"])
     ref = OG.backward(sc, cam, s, ox, oy, g, "f32")
     U.assert_grads_close({k: v.cpu().numpy() for k, v in got.items()}, ref, GRAD_KEYS,
+                         ref_alt=OG.backward(sc, cam, s, ox, oy, g, "mixed"),
                          label=f"grid s={s} off=({ox},{oy}) ({nflag} flagged samples)")
 
 
@@ -225,4 +226,5 @@ def test_fused_feature_loss(OG, room, grid, bf16):
     ref_3 = OG.backward(scb, cam, s, ox, oy, {"feat": g3}, "f32")
     U.assert_grads_close({k: v.cpu().numpy() for k, v in grads3.items()}, ref_3,
                          [k for k in GRAD_KEYS if k != "sh"],
+                         ref_alt=OG.backward(scb, cam, s, ox, oy, {"feat": g3}, "mixed"),
                          label=f"fused-loss gradient, grid s={s} ({int((flags != 0).sum())} flagged)")

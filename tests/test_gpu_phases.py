@@ -52,10 +52,12 @@ def test_features_only_backward(oracle, D, bf16, stride):
     feats = U.bf16_round(sc.feats) if bf16 else None
     if stride == 1:
         ref = oracle.backward(sc, cam, {"feat": g["feat"]}, "f32", feats=feats)
+        alt = oracle.backward(sc, cam, {"feat": g["feat"]}, "mixed", feats=feats)
     else:
         from oracle import grid as OG
         ref = OG.backward(sc, cam, c.stride, c.off_x, c.off_y, {"feat": g["feat"]}, "f32", feats=feats)
-    U.assert_grads_close({"feats": gf.cpu().numpy()}, ref, ["feats"],
+        alt = OG.backward(sc, cam, c.stride, c.off_x, c.off_y, {"feat": g["feat"]}, "mixed", feats=feats)
+    U.assert_grads_close({"feats": gf.cpu().numpy()}, ref, ["feats"], ref_alt=alt,
                          label=f"features-only vs oracle D={D} s={stride}")
 
 
@@ -70,5 +72,6 @@ def test_pose_only_backward(oracle):
     torch.cuda.synchronize()
     U.assert_grads_close({"pose": pose.cpu().numpy()}, {"pose": full["pose"].cpu().numpy()},
                          ["pose"], rtol=1e-4, floor=1e-6, norm_tol=1e-5, label="pose-only vs full")
-    ref = oracle.backward(sc, cam, {k: g[k] for k in ("rgb", "depth", "alpha")}, "f32")
-    U.assert_grads_close({"pose": pose.cpu().numpy()}, ref, ["pose"], label="pose-only vs oracle")
+    gi = {k: g[k] for k in ("rgb", "depth", "alpha")}
+    U.assert_grads_close({"pose": pose.cpu().numpy()}, oracle.backward(sc, cam, gi, "f32"), ["pose"],
+                         ref_alt=oracle.backward(sc, cam, gi, "mixed"), label="pose-only vs oracle")
