@@ -184,8 +184,9 @@ def measure_fp32_peak(L, dev, index, iters=65536, reps=3):
     return {"tflops": round(tf, 2), "ms": round(ms, 3), "runs_tflops": [round(r[0], 2) for r in runs],
             "sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
             "reasons": clk.get("reasons"),
-            "how": "gs_measure_fp32_peak: 8 independent fmaf chains per thread, every SM at its "
-                   "occupancy limit, CUDA events; best of %d, SM clock sampled meanwhile" % reps}
+            "how": "gs_measure_fp32_peak: 8 independent FMA chains per thread (scalar fmaf and "
+                   "packed f32x2 pairs, the larger rate), every SM at its occupancy limit, CUDA "
+                   "events; best of %d, SM clock sampled meanwhile" % reps}
 
 
 KERNEL_SOURCES = {

@@ -325,11 +325,12 @@ int64_t gs_launch_count(void);
 
 /* FP32 arithmetic peak of the current device, measured: not a step of the paper's method
  * but the denominator of the rasterizer's roofline (blending, Eq. 1, and its backward,
- * App. B, are bound by FP32 arithmetic).  Launches one kernel that fills every SM to its
+ * App. B, are bound by FP32 arithmetic).  Launches two kernels that fill every SM to its
  * occupancy limit with threads advancing eight independent fused multiply-add chains for
- * `iters` x 16 steps each (after a short warm-up launch), times it with CUDA events on
- * `stream` and synchronises on the end event.  *tflops_out receives the FP32 rate
- * (2 FLOPs per FMA), *ms_out (may be NULL) the kernel time.  Reads and changes no GPU
+ * `iters` x 16 steps each, one with scalar FMAs and one with packed pairs (two FMAs per
+ * instruction), each after a short warm-up launch; times them with CUDA events on
+ * `stream` and synchronises on the end events.  *tflops_out receives the larger FP32 rate
+ * (2 FLOPs per FMA), *ms_out (may be NULL) that kernel's time.  Reads and changes no GPU
  * setting; the caller samples the SM clock if it wants the rate at a known clock.
  * Errors: GS_ERR_ARG (iters <= 0, NULL tflops_out), GS_ERR_CUDA. */
 gs_status gs_measure_fp32_peak(int iters, double* tflops_out, double* ms_out, void* stream);

@@ -11,6 +11,16 @@ constexpr float kAlphaMin = 1.f / 255.f;   // skip a Gaussian with alpha below t
 constexpr float kAlphaMax = 0.99f;         // alpha cap
 constexpr float kTMin = 1e-4f;             // stop before T would drop below this
 
+// Two FP32 fused multiply-adds (or products) in one packed instruction of the sm_100
+// family.  Each component is rounded exactly as fmaf (or __fmul_rn), so a sum accumulated
+// in packed pairs equals the scalar one bit for bit; the raster kernels are bound by
+// instruction issue, and the packed form halves the issue slots of their accumulations.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 splat2(float x) { return make_float2(x, x); }
+// component c of a vector held as packed pairs
+__device__ __forceinline__ float pair_at(const float2* v, int c) { return (c & 1) ? v[c >> 1].y : v[c >> 1].x; }
+
 // sigma = 1/2 (A dx^2 + C dy^2) + B dx dy for the offset (dx, dy) = pixel - mean
 // (the exponent of G(x), App. A, with the 2D conic [[A, B], [B, C]]).
 __device__ __forceinline__ float blend_sigma(float dx, float dy, float A, float B, float C) {

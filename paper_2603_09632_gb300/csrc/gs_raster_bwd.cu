@@ -212,9 +212,9 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
     // upstream gradients of this pixel
     float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, Tf = 1.f;
     int nc = 0;
-    float gF[DP > 0 ? DP : 1];
+    float2 gF[DP > 0 ? DP / 2 : 1];   // upstream feature gradient in packed pairs
   #pragma unroll
-    for (int c = 0; c < (DP > 0 ? DP : 1); ++c) gF[c] = 0.f;
+    for (int c = 0; c < (DP > 0 ? DP / 2 : 1); ++c) gF[c] = make_float2(0.f, 0.f);
     if (inside) {
       if (!FO && g_rgb) {
         gC0 = g_rgb[p];
@@ -227,13 +227,15 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
       nc = (int)n_contrib[p];
       if constexpr (DP > 0) {
   #pragma unroll
-        for (int c = 0; c < DP; ++c) gF[c] = c < D ? g_feat[c * HW + p] : 0.f;
+        for (int c = 0; c < DP; c += 2)
+          gF[c / 2] = make_float2(c < D ? g_feat[c * HW + p] : 0.f, c + 1 < D ? g_feat[(c + 1) * HW + p] : 0.f);
       }
     }
     if constexpr (DP > 0) {
   #pragma unroll
       for (int c = 0; c < DP; c += 4)
-        *reinterpret_cast<float4*>(s_E + t * Cfg::ES + c) = make_float4(gF[c], gF[c + 1], gF[c + 2], gF[c + 3]);
+        *reinterpret_cast<float4*>(s_E + t * Cfg::ES + c) =
+            make_float4(gF[c / 2].x, gF[c / 2].y, gF[c / 2 + 1].x, gF[c / 2 + 1].y);
     }
     s_E4[t] = make_float4(gC0, gC1, gC2, gD);
     if (t == 0) s_maxn = 0;
@@ -313,19 +315,18 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
                 w = a * T;
                 if constexpr (!FO) {
                 const float4 r2 = s_r2[jb0 + j];
-                float d0 = gC0 * r2.x, d1 = gC1 * r2.y, d2 = gC2 * r2.z, d3 = gD * r1.z;
+                float2 d01 = mul2(make_float2(gC0, gC1), make_float2(r2.x, r2.y));
+                float2 d23 = mul2(make_float2(gC2, gD), make_float2(r2.z, r1.z));
                 if constexpr (DP > 0) {
                   const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
   #pragma unroll
                   for (int q = 0; q < DP / 4; ++q) {
                     const float4 f = f4[q];
-                    d0 = fmaf(gF[4 * q], f.x, d0);
-                    d1 = fmaf(gF[4 * q + 1], f.y, d1);
-                    d2 = fmaf(gF[4 * q + 2], f.z, d2);
-                    d3 = fmaf(gF[4 * q + 3], f.w, d3);
+                    d01 = fma2(gF[2 * q], make_float2(f.x, f.y), d01);
+                    d23 = fma2(gF[2 * q + 1], make_float2(f.z, f.w), d23);
                   }
                 }
-                const float dot = (d0 + d1) + (d2 + d3);
+                const float dot = (d01.x + d01.y) + (d23.x + d23.y);
                 const float galpha = T * (dot - s_run) + gAT * inv;
                 s_run = a * dot + (1.f - a) * s_run;
                 // dL/do = galpha G; dL/dsigma = -galpha a = -o dL/do (phase 2b scales the
@@ -355,11 +356,9 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
             const int jb = (t / Cfg::CB) % Cfg::JB;
             const int part = t / Cfg::TASKS;
             constexpr int PP = Cfg::PP;
-            float acc[4][4];
+            float2 acc[4][2];   // rows a, columns in packed pairs
   #pragma unroll
-            for (int a = 0; a < 4; ++a)
-  #pragma unroll
-              for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+            for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = make_float2(0.f, 0.f);
             // a part lies in one warp strip or spans whole strips; W holds values only where
             // the Gaussian is live for the strip, so liveness is applied strip by strip
             constexpr int NSP = PP >= 32 ? PP / 32 : 1;   // strips per part
@@ -383,10 +382,9 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
                   const float wa[4] = {wv[a].x, wv[a].y, wv[a].z, wv[a].w};
   #pragma unroll
                   for (int b = 0; b < 4; ++b) {
-                    acc[a][0] = fmaf(wa[b], ev[b].x, acc[a][0]);
-                    acc[a][1] = fmaf(wa[b], ev[b].y, acc[a][1]);
-                    acc[a][2] = fmaf(wa[b], ev[b].z, acc[a][2]);
-                    acc[a][3] = fmaf(wa[b], ev[b].w, acc[a][3]);
+                    const float2 w2 = splat2(wa[b]);
+                    acc[a][0] = fma2(w2, make_float2(ev[b].x, ev[b].y), acc[a][0]);
+                    acc[a][1] = fma2(w2, make_float2(ev[b].z, ev[b].w), acc[a][1]);
                   }
                 }
               }
@@ -399,7 +397,7 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
   #pragma unroll
               for (int a = 0; a < 4; ++a)
                 *reinterpret_cast<float4*>(dst + (4 * jb + a) * DP) =
-                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                    make_float4(acc[a][0].x, acc[a][0].y, acc[a][1].x, acc[a][1].y);
             } else {
               const bool hi = lane & Cfg::TASKS;
               float h[2][4];   // rows 2 hi + r
@@ -407,8 +405,8 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
               for (int r = 0; r < 2; ++r)
   #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                  const float send = hi ? acc[r][b] : acc[r + 2][b];
-                  const float keep = hi ? acc[r + 2][b] : acc[r][b];
+                  const float send = hi ? pair_at(acc[r], b) : pair_at(acc[r + 2], b);
+                  const float keep = hi ? pair_at(acc[r + 2], b) : pair_at(acc[r], b);
                   h[r][b] = keep + __shfl_xor_sync(0xffffffffu, send, Cfg::TASKS);
                 }
               if constexpr (Cfg::PW == 2) {

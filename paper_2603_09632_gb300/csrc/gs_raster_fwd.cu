@@ -125,10 +125,11 @@ k_raster_fwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq, FeatLoss fl
     const float wbx0 = (float)(tx0 + strip_px(threadIdx.x & ~31)) + 0.5f;
     const float wby0 = (float)(ty0 + strip_py(threadIdx.x & ~31)) + 0.5f;
 
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
-    float acc[DP > 0 ? DP : 1];
+    float T = 1.f;
+    float2 c01 = make_float2(0.f, 0.f), c2d = make_float2(0.f, 0.f);   // (r, g), (b, depth)
+    float2 acc[DP > 0 ? DP / 2 : 1];   // feature channels in packed pairs
 #pragma unroll
-    for (int c = 0; c < (DP > 0 ? DP : 1); ++c) acc[c] = 0.f;
+    for (int c = 0; c < (DP > 0 ? DP / 2 : 1); ++c) acc[c] = make_float2(0.f, 0.f);
     int last = 0;     // 1 + list position of the last blended entry
     int lastj = -1;   // its batch slot, resolved to a list position once per batch
     bool done = !inside;
@@ -194,19 +195,16 @@ k_raster_fwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq, FeatLoss fl
         }
         {   // accumulate unconditionally: w = 0 adds nothing, and live entries almost always blend
           const float4 r2 = s_r2[j];
-          c0 = fmaf(w, r2.x, c0);
-          c1 = fmaf(w, r2.y, c1);
-          c2 = fmaf(w, r2.z, c2);
-          dep = fmaf(w, r1.z, dep);
+          const float2 w2 = splat2(w);
+          c01 = fma2(w2, make_float2(r2.x, r2.y), c01);
+          c2d = fma2(w2, make_float2(r2.z, r1.z), c2d);
           if constexpr (DP > 0) {
             const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * DP);
 #pragma unroll
             for (int q = 0; q < DP / 4; ++q) {
               const float4 f = f4[q];
-              acc[4 * q] = fmaf(w, f.x, acc[4 * q]);
-              acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
-              acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
-              acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
+              acc[2 * q] = fma2(w2, make_float2(f.x, f.y), acc[2 * q]);
+              acc[2 * q + 1] = fma2(w2, make_float2(f.z, f.w), acc[2 * q + 1]);
             }
           }
         }
@@ -219,17 +217,17 @@ k_raster_fwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq, FeatLoss fl
       const int64_t HW = (int64_t)cam.W * cam.H;
       const int64_t p = (int64_t)py * cam.W + px;
       if (rgb) {
-        rgb[p] = c0;
-        rgb[HW + p] = c1;
-        rgb[2 * HW + p] = c2;
+        rgb[p] = c01.x;
+        rgb[HW + p] = c01.y;
+        rgb[2 * HW + p] = c2d.x;
       }
-      if (depth) depth[p] = dep;
+      if (depth) depth[p] = c2d.y;
       if (alpha) alpha[p] = 1.f - T;
       if constexpr (DP > 0) {
         if (feat) {
 #pragma unroll
           for (int c = 0; c < DP; ++c)
-            if (c < D) feat[c * HW + p] = acc[c];
+            if (c < D) feat[c * HW + p] = pair_at(acc, c);
         }
       }
       jb.T_final[p] = T;
@@ -248,7 +246,7 @@ k_raster_fwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq, FeatLoss fl
 #pragma unroll
         for (int c = 0; c < DP; ++c) {
           if (c < D) {
-            const float a = V * acc[c], b = V * __ldg(fl.target + c * HW + p);
+            const float a = V * pair_at(acc, c), b = V * __ldg(fl.target + c * HW + p);
             s_feat[c * kB + threadIdx.x] = b;
             dot = fmaf(a, b, dot);
             aa = fmaf(a, a, aa);
@@ -263,7 +261,7 @@ k_raster_fwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq, FeatLoss fl
 #pragma unroll
         for (int c = 0; c < DP; ++c) {
           if (c < D) {
-            const float a = V * acc[c], b = s_feat[c * kB + threadIdx.x];
+            const float a = V * pair_at(acc, c), b = s_feat[c * kB + threadIdx.x];
             const float sg = a > b ? 1.f : (a < b ? -1.f : 0.f);
             fl.g_feat[c * HW + p] = V * (fl.w_l1 * sg - fl.w_cos * (b * inv - cf * a));
           }

@@ -204,10 +204,11 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
     const uint2 rg = ranges[it.tile];
     const int start = (int)rg.x, end = (int)rg.y;
 
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f;
-    float acc[DP > 0 ? DP : 1];
+    float T = 1.f;
+    float2 c01 = make_float2(0.f, 0.f), c2d = make_float2(0.f, 0.f);   // (r, g), (b, depth)
+    float2 acc[DP > 0 ? DP / 2 : 1];   // feature channels in packed pairs
 #pragma unroll
-    for (int c = 0; c < (DP > 0 ? DP : 1); ++c) acc[c] = 0.f;
+    for (int c = 0; c < (DP > 0 ? DP / 2 : 1); ++c) acc[c] = make_float2(0.f, 0.f);
     int last = 0;     // 1 + list position of the last blended entry
     int lastk = -1;   // its batch slot, resolved once per batch
     bool done = !it.in_img;
@@ -240,19 +241,16 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
         }
         if (__any_sync(kFull, w != 0.f)) {
           const float4 r2 = s_r[3 * k + 2];
-          c0 = fmaf(w, r2.x, c0);
-          c1 = fmaf(w, r2.y, c1);
-          c2 = fmaf(w, r2.z, c2);
-          dep = fmaf(w, r1.z, dep);
+          const float2 w2 = splat2(w);
+          c01 = fma2(w2, make_float2(r2.x, r2.y), c01);
+          c2d = fma2(w2, make_float2(r2.z, r1.z), c2d);
           if constexpr (DP > 0) {
             const float4* f4 = reinterpret_cast<const float4*>(s_f + k * DP);
 #pragma unroll
             for (int e = 0; e < DP / 4; ++e) {
               const float4 f = f4[e];
-              acc[4 * e] = fmaf(w, f.x, acc[4 * e]);
-              acc[4 * e + 1] = fmaf(w, f.y, acc[4 * e + 1]);
-              acc[4 * e + 2] = fmaf(w, f.z, acc[4 * e + 2]);
-              acc[4 * e + 3] = fmaf(w, f.w, acc[4 * e + 3]);
+              acc[2 * e] = fma2(w2, make_float2(f.x, f.y), acc[2 * e]);
+              acc[2 * e + 1] = fma2(w2, make_float2(f.z, f.w), acc[2 * e + 1]);
             }
           }
         }
@@ -264,17 +262,17 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
     const int64_t p = (int64_t)it.m * cam.GW + it.n;
     if (it.in_img) {
       if (rgb) {
-        rgb[p] = c0;
-        rgb[HW + p] = c1;
-        rgb[2 * HW + p] = c2;
+        rgb[p] = c01.x;
+        rgb[HW + p] = c01.y;
+        rgb[2 * HW + p] = c2d.x;
       }
-      if (depth) depth[p] = dep;
+      if (depth) depth[p] = c2d.y;
       if (alpha) alpha[p] = 1.f - T;
       if constexpr (DP > 0) {
         if (feat) {
 #pragma unroll
           for (int c = 0; c < DP; ++c)
-            if (c < D) feat[c * HW + p] = acc[c];
+            if (c < D) feat[c * HW + p] = pair_at(acc, c);
         }
       }
       T_final[p] = T;
@@ -289,7 +287,7 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
 #pragma unroll
         for (int c = 0; c < DP; ++c) {
           if (c < D) {
-            const float a = V * acc[c], b = V * __ldg(fl.target + c * HW + p);
+            const float a = V * pair_at(acc, c), b = V * __ldg(fl.target + c * HW + p);
             s_f[c * 32 + lane] = b;
             dot = fmaf(a, b, dot);
             aa = fmaf(a, a, aa);
@@ -304,7 +302,7 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
 #pragma unroll
         for (int c = 0; c < DP; ++c) {
           if (c < D) {
-            const float a = V * acc[c], b = s_f[c * 32 + lane];
+            const float a = V * pair_at(acc, c), b = s_f[c * 32 + lane];
             const float sg = a > b ? 1.f : (a < b ? -1.f : 0.f);
             fl.g_feat[c * HW + p] = V * (fl.w_l1 * sg - fl.w_cos * (b * inv - cf * a));
           }
@@ -565,11 +563,9 @@ k_grid_bwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
             const int kb = task / CB, cb = task - kb * CB, k0 = 4 * kb;
             const unsigned live4 = (wlive >> k0) & 15u;
             if (!live4) continue;
-            float o[4][4];
+            float2 o[4][2];   // entries x, channels in packed pairs
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
-#pragma unroll
-              for (int y = 0; y < 4; ++y) o[x][y] = 0.f;
+            for (int x = 0; x < 4; ++x) o[x][0] = o[x][1] = make_float2(0.f, 0.f);
 #pragma unroll 8
             for (int l = 0; l < 32; ++l) {
               const float4 w4 = *reinterpret_cast<const float4*>(s_W + w_slot(l, k0));
@@ -577,10 +573,9 @@ k_grid_bwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
               const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
               for (int x = 0; x < 4; ++x) {
-                o[x][0] = fmaf(wv[x], e.x, o[x][0]);
-                o[x][1] = fmaf(wv[x], e.y, o[x][1]);
-                o[x][2] = fmaf(wv[x], e.z, o[x][2]);
-                o[x][3] = fmaf(wv[x], e.w, o[x][3]);
+                const float2 w2 = splat2(wv[x]);
+                o[x][0] = fma2(w2, make_float2(e.x, e.y), o[x][0]);
+                o[x][1] = fma2(w2, make_float2(e.z, e.w), o[x][1]);
               }
             }
 #pragma unroll
@@ -588,11 +583,11 @@ k_grid_bwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
               if (!(live4 >> x & 1u)) continue;
               float* dst = g_feats + (int64_t)s_id[k0 + x] * D + 4 * cb;
               if (D == DP) {
-                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(o[x][0], o[x][1], o[x][2], o[x][3]));
+                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(o[x][0].x, o[x][0].y, o[x][1].x, o[x][1].y));
               } else {
 #pragma unroll
                 for (int y = 0; y < 4; ++y)
-                  if (4 * cb + y < D) atomicAdd(dst + y, o[x][y]);
+                  if (4 * cb + y < D) atomicAdd(dst + y, pair_at(o[x], y));
               }
             }
           }
