@@ -261,8 +261,9 @@ gs_status gs_vq_weights(const float* logits, int64_t n, int32_t L, int32_t out_d
 gs_status gs_vq_weights_bwd(const float* logits, const float* g_w, int64_t n, int32_t L,
                             float* g_logits, void* stream);
 
-/* Decode of a rendered weight map on the tensor cores (tcgen05, TF32 inputs, FP32
- * accumulation): wmap [L][P] float32 (the channel-major feature output of a render with
+/* Decode of a rendered weight map on the tensor cores (tcgen05; FP32-accurate products by
+ * the 3xTF32 split of both operands, FP32 accumulation; above 256 columns a cluster of two
+ * CTAs on two SMs, each with half of the columns): wmap [L][P] float32 (the channel-major feature output of a render with
  * the weights as features, P pixels), codebook [L][D] float32.  Writes, when non-NULL:
  *   F_out [D][P] = E^T w(x) per pixel;
  *   relevance [P] = max_{n >= 1} 1 / (1 + exp(tau (F~.t_n - F~.t_0))), F~ = F / (|F| + 1e-8),
@@ -270,6 +271,7 @@ gs_status gs_vq_weights_bwd(const float* logits, const float* g_w, int64_t n, in
  *     negatives, unit vectors; 2 <= n_text <= 8) and tau = 10 in the paper.
  * L a multiple of 8 in [8, 64]; D a multiple of 16 in [16, 512].  err (device int32, may be
  * NULL) is set to 1 if a tensor-core completion wait timed out (outputs then invalid).
+ * Accuracy: |F - E^T w| <= 2e-5 sum_l |w_l E_l| per entry (products to 2^-22, FP32 sums).
  * Errors: GS_ERR_ARG for unsupported sizes or missing pointers. */
 gs_status gs_vq_decode(const float* wmap, int64_t P, int32_t L, const float* codebook, int32_t D,
                        float* F_out, const float* text, int32_t n_text, float tau,

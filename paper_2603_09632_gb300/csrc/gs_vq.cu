@@ -10,10 +10,16 @@
 // issued by one thread per CTA on 128-pixel tiles, operands staged in shared memory in the
 // canonical K-major core-matrix layout, completion signalled through an mbarrier, and the
 // epilogue (optional F write, |F|^2, relevance) reading the accumulator with tcgen05.ld.
-// The next tile's weights are fetched while the tensor cores and the epilogue run.  One
-// persistent CTA per SM holds the codebook in shared memory for its range of tiles.  Every
-// wait is bounded; on a timeout the kernel records an error, waits (bounded) for its own
-// MMAs, frees its tensor memory and returns.
+// Products are FP32-accurate by the 3xTF32 split: each operand x = hi + lo with hi and lo
+// rounded to tf32 (|x - hi - lo| <= 2^-22 |x|), and W E = Whi Ehi + Wlo Ehi + Whi Elo (the
+// dropped Wlo Elo is below 2^-22 of the product).  The split codebook of D = 512 columns
+// does not fit one CTA's shared memory, so above 256 columns a cluster of two CTAs (two
+// SMs) decodes the same tiles, each its half of the columns; the half-norms |F|^2 that the
+// relevance needs are sent to the first CTA through distributed shared memory.  Each CTA
+// keeps two accumulators in tensor memory, so the next tile's MMAs run during this tile's
+// epilogue, and the next weights are fetched while both run.  Every mbarrier wait is
+// bounded; on a timeout the kernel records an error, still meets every cluster barrier its
+// partner will reach, waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include <algorithm>
 #include <cstdint>
 
@@ -22,12 +28,15 @@
 namespace gs {
 namespace {
 
-constexpr int kVT = 512;             // threads per CTA (four per tile row)
-constexpr int kGroups = kVT / 128;   // threads per row = column groups of the epilogue
+constexpr int kVT = 512;             // threads per CTA (four per tile row when staging)
+constexpr int kGroups = 4;           // threads per row when staging = column groups of the epilogue
 constexpr int kRows = 128;           // tile rows (pixels) = TMEM lanes = MMA M
 constexpr int kMaxL = 64;            // K
-constexpr int kMaxDc = 512;          // N (two MMAs of N = 256)
+constexpr int kMaxDc = 512;          // D
+constexpr int kMaxDh = 256;          // columns of one CTA = N of one MMA
 constexpr int kMaxText = 8;                 // prompt + negatives (read as two float4 per codeword)
+constexpr int kDotBufs = 3;                 // prompt-dot buffers (staged two tiles ahead of use)
+constexpr int kXBufs = 3;                   // norm and exchange buffers (relevance two tiles behind)
 constexpr uint32_t kWaitLimit = 1u << 20;   // try_wait polls (each may suspend briefly)
 constexpr int kMaxResident = 2048 / kVT;   // CTAs per SM allowed by the thread count
 
@@ -88,6 +97,83 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+// x rounded to the nearest tf32 value (10 fraction bits, ties away from zero), as fp32.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// The 3xTF32 split: x = hi + lo + r with hi, lo exact in tf32 and |r| <= 2^-22 |x|
+// (x - hi is exact in fp32).
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - hi);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_ctas() {
+  uint32_t n;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+  return n;
+}
+
+// Split cluster barrier: arrive publishes this thread's earlier shared-memory writes
+// (release), wait returns once every thread of the cluster has arrived (acquire).  Every
+// thread of both CTAs takes part, the same number of times.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Address of the same shared-memory location in CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(local), "r"(rank));
+  return ra;
+}
+
+// Asynchronous 4-byte store into another CTA's shared memory that completes 4 bytes of the
+// transaction count of that CTA's mbarrier rbar (no fence on this thread's other writes).
+__device__ __forceinline__ void st_async_f32(uint32_t raddr, float v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(raddr),
+               "r"(__float_as_uint(v)), "r"(rbar)
+               : "memory");
+}
+
+// The one arrival of an mbarrier phase, expecting `bytes` of asynchronous stores.
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Arrival on an mbarrier of another CTA of the cluster (a "buffer consumed" signal: the
+// reads it follows have completed, their values are in registers or already stored).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t rmbar) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(rmbar) : "memory");
+}
+
+// Bounded wait for a phase completed by another CTA of the cluster.
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t mbar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
 // 32 consecutive fp32 columns of this warp's 32 TMEM lanes (one lane per thread).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -113,6 +199,7 @@ struct DecodeArgs {
   int L;
   const float* E;         // [L][Dc]
   int Dc;
+  int Dh0;                // columns of the cluster's first CTA (all Dc without a partner)
   float* F;               // [Dc][P] or null
   const float* text;      // [n_text][Dc] or null
   int n_text;
@@ -121,49 +208,59 @@ struct DecodeArgs {
   int32_t* err;           // set to 1 on a timed-out wait
 };
 
-// Shared-memory plan of the decode CTA (bytes).  The prompt embeddings are staged in the
-// partial-dot area, which is only used once the tiles start.
+// Shared-memory plan of the decode CTA (bytes), for L codewords and at most Dh columns.
 struct DecodeSmem {
-  uint32_t a, b, et, dot, nrm, text, bar, tmem, total;
-  __host__ __device__ DecodeSmem(int L, int Dc) {
-    a = 0;                                              // A tile [128 x L] fp32, core layout
-    b = a + (uint32_t)kRows * L * 4;                    // B = E^T [Dc x L] fp32, core layout
-    et = b + (uint32_t)Dc * L * 4;                      // E t_j  [L][kMaxText]
-    dot = et + (uint32_t)kMaxL * kMaxText * 4;          // [2 buffers][groups][kMaxText][128]
-    text = dot;                                         // prompt embeddings [kMaxText][Dc]
-    nrm = dot + 2u * kGroups * kMaxText * kRows * 4;    // [2 buffers][groups][128]
-    bar = nrm + 2u * kGroups * kRows * 4;
-    tmem = bar + 8;
+  uint32_t a_hi, a_lo, b_hi, b_lo, et, dot, nrm, peer, bar, xbar, tmem, total;
+  __host__ __device__ DecodeSmem(int L, int Dh) {
+    a_hi = 0;                                           // weights [128 x L], tf32 hi part
+    a_lo = a_hi + (uint32_t)kRows * L * 4;              // ... and lo part
+    b_hi = a_lo + (uint32_t)kRows * L * 4;              // E^T [Dh x L] of this CTA's columns
+    b_lo = b_hi + (uint32_t)Dh * L * 4;
+    et = b_lo + (uint32_t)Dh * L * 4;                   // E t_j  [L + groups][kMaxText], padded
+    dot = et + (uint32_t)(kMaxL + kGroups) * kMaxText * 4;   // prompt dots [kDotBufs][kMaxText][128]
+    nrm = dot + (uint32_t)kDotBufs * kMaxText * kRows * 4;   // |F|^2 parts [kXBufs][groups][128]
+    peer = nrm + (uint32_t)kXBufs * kGroups * kRows * 4;     // from the partner [kXBufs][1 + kMaxText][128]:
+    bar = peer + (uint32_t)kXBufs * (1 + kMaxText) * kRows * 4;   // its |F|^2, the prompt dots; MMA completion
+    xbar = bar + 8;                                     // exchange buffer full[kXBufs] (first CTA),
+    tmem = xbar + 16 * kXBufs;                          // ... consumed[kXBufs] (second CTA)
     total = tmem + 8;
   }
 };
-static_assert(2 * kGroups * kMaxText * kRows >= kMaxText * kMaxDc, "text staging must fit");
 static_assert(kMaxText == 8, "E t_j rows are read as two float4");
 
-// One 128-pixel tile per iteration.  The four threads t = r + 128 g (g = 0..3) share row r
-// (pixel p = tile * 128 + r): each loads a quarter of the row's L weights (issued before
-// the previous tile's epilogue and consumed after it), and in the epilogue warp w reads TMEM lanes 32 (w mod 4) ..
-// and every fourth 32-column chunk of F starting at chunk w / 4.  The prompt dot products
-// use F.t_j = w.(E t_j) with E t_j formed once per CTA, so the epilogue only adds |F|^2.
+// One 128-pixel tile per iteration.  Staging: warp w stages rows 8w .. 8w + 7, lanes r,
+// r + 8, r + 16, r + 24 share a row, each loading a quarter of its L weights (issued two
+// tiles ahead, consumed after the MMAs of the tile before), splitting them into tf32 hi/lo
+// parts and forming its part of the prompt dots F.t_j = w.(E t_j) (E t_j formed once per
+// CTA).  Epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (pixels) and every fourth
+// 32-column chunk of this CTA's columns starting at chunk w / 4, and writes F channel-major.
 __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int r = t & (kRows - 1), h = t >> 7;   // row, column group
-  const int L = a.L, Dc = a.Dc, LH = L / kGroups;   // weights per thread (L multiple of 8)
+  const int sr = 8 * warp + (lane & 7), sh = lane >> 3;   // staging row, its quarter
+  const int L = a.L, LH = L / kGroups;                   // weights per staging thread
+  const uint32_t rank = cluster_rank(), nrank = cluster_ctas();
+  const int n_lo = rank == 0 ? 0 : a.Dh0;                // this CTA's columns [n_lo, n_lo + Dh)
+  const int Dh = rank == 0 ? a.Dh0 : a.Dc - a.Dh0;
+  const int Db = (Dh + 31) & ~31;                        // TMEM columns per accumulator
   const bool want_rel = a.rel != nullptr;
-  const DecodeSmem sm(L, Dc);
-  float* sA = reinterpret_cast<float*>(smem + sm.a);
-  float* sB = reinterpret_cast<float*>(smem + sm.b);
+  const bool rel_here = want_rel && rank == 0;           // relevance formed by the first CTA
+  const bool exch = want_rel && nrank > 1;               // the partner sends |F|^2 and dots
+  const DecodeSmem sm(L, a.Dh0);
+  float* sAh = reinterpret_cast<float*>(smem + sm.a_hi);
+  float* sAl = reinterpret_cast<float*>(smem + sm.a_lo);
+  float* sBh = reinterpret_cast<float*>(smem + sm.b_hi);
+  float* sBl = reinterpret_cast<float*>(smem + sm.b_lo);
   float* sEt = reinterpret_cast<float*>(smem + sm.et);
   float* sDot = reinterpret_cast<float*>(smem + sm.dot);
   float* sNrm = reinterpret_cast<float*>(smem + sm.nrm);
-  float* sTx = reinterpret_cast<float*>(smem + sm.text);
+  float* sPeer = reinterpret_cast<float*>(smem + sm.peer);
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + sm.bar);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + sm.tmem);
   const uint32_t sbo = (uint32_t)(L / 4) * 128u;   // bytes between 8-row groups
 
   int ncols = 32;
-  while (ncols < Dc) ncols <<= 1;
+  while (ncols < 2 * Db) ncols <<= 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
                  "r"(ncols)
@@ -171,66 +268,127 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(s_bar)) : "memory");
+    for (int k = 0; k < 1 + 2 * kXBufs; ++k)   // MMA completion, full[kXBufs], consumed[kXBufs]
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(smem + sm.bar + 8 * k)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // codebook, transposed into the K-major B operand: element (n, k) = E[k][n]
-  for (int e = t; e < L * Dc; e += kVT) {
-    const int k = e / Dc, n = e - k * Dc;
+  // E t_j for every codeword k over all Dc columns (in the CTA that forms the prompt dots:
+  // the second of a pair, or the only one): the prompts are
+  // staged in the operand area, idle until the codebook and the first tile are staged
+  // (n_text Dc <= 8 Dc floats fit: the A and B areas hold 2 L (128 + Dh) >= 8 Dc floats for
+  // L >= 8 and Dh >= Dc / 2); one warp per codeword, lanes over the columns
+  const int ntx = want_rel ? a.n_text : 0;                 // prompts of the relevance
+  const int nt = (want_rel && rank == nrank - 1) ? ntx : 0;  // ... whose dots this CTA forms
+  if (nt > 0) {
+    float* sTx = sAh;
+    for (int e = t; e < nt * a.Dc; e += kVT) sTx[e] = __ldg(a.text + e);
+    __syncthreads();
+    for (int k = warp; k < L; k += kVT / 32) {
+      float acc[kMaxText];
+#pragma unroll
+      for (int j = 0; j < kMaxText; ++j) acc[j] = 0.f;
+#pragma unroll 4
+      for (int c = lane; c < a.Dc; c += 32) {
+        const float ev = __ldg(a.E + (int64_t)k * a.Dc + c);
+#pragma unroll
+        for (int j = 0; j < kMaxText; ++j)
+          if (j < nt) acc[j] = fmaf(ev, sTx[j * a.Dc + c], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < kMaxText; ++j) {
+        float v = acc[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sEt[(k + k / LH) * kMaxText + j] = v;
+      }
+    }
+    __syncthreads();   // the operand area is free again
+  }
+  // this CTA's codebook columns, transposed into the K-major B operand and split:
+  // element (n, k) = E[k][n_lo + n]
+  for (int e = t; e < L * Dh; e += kVT) {
+    const int k = e / Dh, n = e - k * Dh;
     const uint32_t off = (uint32_t)(n >> 3) * sbo + (uint32_t)(k >> 2) * 128u + (uint32_t)(n & 7) * 16u +
                          (uint32_t)(k & 3) * 4u;
-    *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sB) + off) = __ldg(a.E + e);
-  }
-  const int nt = want_rel ? a.n_text : 0;
-  for (int e = t; e < nt * Dc; e += kVT) sTx[e] = __ldg(a.text + e);
-  __syncthreads();
-  // E t_j for every codeword k (one warp per codeword row, lanes over the D columns)
-  for (int k = warp; k < L && nt > 0; k += kVT / 32) {
-    float acc[kMaxText];
-#pragma unroll
-    for (int j = 0; j < kMaxText; ++j) acc[j] = 0.f;
-    for (int c = lane; c < Dc; c += 32) {
-      const float ev = __ldg(a.E + (int64_t)k * Dc + c);
-#pragma unroll
-      for (int j = 0; j < kMaxText; ++j)
-        if (j < nt) acc[j] = fmaf(ev, sTx[j * Dc + c], acc[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < kMaxText; ++j) {
-      float v = acc[j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) sEt[k * kMaxText + j] = v;
-    }
+    float hi, lo;
+    split_tf32(__ldg(a.E + (int64_t)k * a.Dc + n_lo + n), hi, lo);
+    *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sBh) + off) = hi;
+    *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sBl) + off) = lo;
   }
   __syncthreads();
+  // the partner's exchange barriers are initialised before either CTA signals the other
+  if (exch) {
+    cluster_arrive();
+    cluster_wait();
+  }
 
   const uint32_t tmem = *s_tmem;
   const uint32_t bar = smem_u32(s_bar);
-  const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
+  const uint32_t full0 = smem_u32(smem + sm.xbar), cons0 = full0 + 8 * kXBufs;   // + 8 b for buffer b
+  // relevance of tile i is finished in iteration i + lag (after the last tile, in the tail):
+  // one tile behind in a single CTA, two behind in a pair, so that the partner's data for a
+  // tile, sent as it finishes the tile, is normally in before it is needed
+  const int lag = exch ? 2 : 1;
+  bool xfer_ok = true;   // this thread's exchange waits have not timed out
+  const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
+  const uint32_t idesc = idesc_tf32(kRows, Dh);
   const int64_t n_tiles = (a.P + kRows - 1) / kRows;
 
-  // this thread's quarter row of weights for one tile (load_rows), and its partial prompt
-  // dot products (row_dots, formed when the row is staged)
+  // this thread's quarter row of weights for one tile
   float wv[kMaxL / kGroups];
-  float dp[kMaxText];
   auto load_rows = [&](int64_t tile) {
-    const int64_t p = tile * kRows + r;
+    const int64_t p = tile * kRows + sr;
     const bool live = p < a.P;
 #pragma unroll
     for (int k = 0; k < kMaxL / kGroups; ++k)
-      wv[k] = (k < LH && live) ? __ldg(a.wmap + (int64_t)(h * LH + k) * a.P + p) : 0.f;
+      wv[k] = (k < LH && live) ? __ldg(a.wmap + (int64_t)(sh * LH + k) * a.P + p) : 0.f;
   };
-  auto row_dots = [&]() {
+  // split the held weights into the A operands
+  auto stage_a = [&]() {
+    unsigned char* Ah = reinterpret_cast<unsigned char*>(sAh);
+    unsigned char* Al = reinterpret_cast<unsigned char*>(sAl);
+    const uint32_t row = (uint32_t)warp * sbo + (uint32_t)(sr & 7) * 16u;
+    if (LH % 4 == 0) {   // whole 4-element core-matrix rows (L = 16, 32, 48, 64)
 #pragma unroll
-    for (int j = 0; j < kMaxText; ++j) dp[j] = 0.f;
+      for (int q = 0; q < kMaxL / kGroups / 4; ++q) {
+        if (q < LH / 4) {
+          float4 h4, l4;
+          split_tf32(wv[4 * q], h4.x, l4.x);
+          split_tf32(wv[4 * q + 1], h4.y, l4.y);
+          split_tf32(wv[4 * q + 2], h4.z, l4.z);
+          split_tf32(wv[4 * q + 3], h4.w, l4.w);
+          const uint32_t off = row + (uint32_t)(sh * LH / 4 + q) * 128u;
+          *reinterpret_cast<float4*>(Ah + off) = h4;
+          *reinterpret_cast<float4*>(Al + off) = l4;
+        }
+      }
+    } else {             // L = 8, 24, 40, 56: scalars
+#pragma unroll
+      for (int k = 0; k < kMaxL / kGroups; ++k) {
+        if (k < LH) {
+          const int kk = sh * LH + k;
+          const uint32_t off = row + (uint32_t)(kk >> 2) * 128u + (uint32_t)(kk & 3) * 4u;
+          float hi, lo;
+          split_tf32(wv[k], hi, lo);
+          *reinterpret_cast<float*>(Ah + off) = hi;
+          *reinterpret_cast<float*>(Al + off) = lo;
+        }
+      }
+    }
+  };
+  // the prompt dots of the held row (nt > 0), summed over its four quarters by
+  // shuffles and kept in dot buffer dbuf.  E t_j is stored with one padding row per quarter,
+  // so the four quarters of a warp read four different bank groups.
+  auto stage_dots = [&](int dbuf) {
     if (nt > 0) {
-      // E t_j of codeword k: two 16-byte loads for the kMaxText = 8 prompts
+      float dp[kMaxText];
+#pragma unroll
+      for (int j = 0; j < kMaxText; ++j) dp[j] = 0.f;
       const float4* et4 = reinterpret_cast<const float4*>(sEt);
 #pragma unroll
       for (int k = 0; k < kMaxL / kGroups; ++k) {
         if (k < LH) {
-          const float4 e0 = et4[(h * LH + k) * 2], e1 = et4[(h * LH + k) * 2 + 1];
+          const float4 e0 = et4[(sh * (LH + 1) + k) * 2], e1 = et4[(sh * (LH + 1) + k) * 2 + 1];
           dp[0] = fmaf(wv[k], e0.x, dp[0]);
           dp[1] = fmaf(wv[k], e0.y, dp[1]);
           dp[2] = fmaf(wv[k], e0.z, dp[2]);
@@ -241,92 +399,114 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
           dp[7] = fmaf(wv[k], e1.w, dp[7]);
         }
       }
+#pragma unroll
+      for (int j = 0; j < kMaxText; ++j) {
+        dp[j] += __shfl_xor_sync(0xffffffffu, dp[j], 8);
+        dp[j] += __shfl_xor_sync(0xffffffffu, dp[j], 16);
+      }
+      // quarter sh stores prompts 2 sh and 2 sh + 1 of its row
+#pragma unroll
+      for (int j = 0; j < kMaxText; ++j)
+        if ((j >> 1) == sh) sDot[(dbuf * kMaxText + j) * kRows + sr] = dp[j];
     }
   };
-  auto store_rows = [&](int buf) {
-    // a thread's LH = L / 4 weights fill whole 4-element core-matrix rows when LH is a
-    // multiple of 4 (L = 16, 32, 48, 64); otherwise (L = 8, 24, 40, 56) store scalars
-    if (LH % 4 == 0) {
-#pragma unroll
-      for (int q = 0; q < kMaxL / kGroups / 4; ++q) {
-        if (q < LH / 4) {
-          const uint32_t off = (uint32_t)(r >> 3) * sbo + (uint32_t)(h * LH / 4 + q) * 128u + (uint32_t)(r & 7) * 16u;
-          *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(sA) + off) =
-              make_float4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < kMaxL / kGroups; ++k) {
-        if (k < LH) {
-          const int kk = h * LH + k;
-          const uint32_t off = (uint32_t)(r >> 3) * sbo + (uint32_t)(kk >> 2) * 128u + (uint32_t)(r & 7) * 16u +
-                               (uint32_t)(kk & 3) * 4u;
-          *reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sA) + off) = wv[k];
-        }
-      }
+  // 3 L/8 MMAs of M = 128, N = Dh, K = 8 into accumulator buf (thread 0)
+  auto issue = [&](int buf) {
+    const uint32_t d = tmem + (uint32_t)(buf * Db);
+    for (int ks = 0; ks < L / 8; ++ks) {
+      const uint64_t a_hi = smem_desc(ah + 256u * ks, 128u, sbo), a_lo = smem_desc(al + 256u * ks, 128u, sbo);
+      const uint64_t b_hi = smem_desc(bh + 256u * ks, 128u, sbo), b_lo = smem_desc(bl + 256u * ks, 128u, sbo);
+      mma_tf32(d, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
+      mma_tf32(d, a_lo, b_hi, idesc, 1u);
+      mma_tf32(d, a_hi, b_lo, idesc, 1u);
     }
-#pragma unroll
-    for (int j = 0; j < kMaxText; ++j)
-      if (j < nt) sDot[((buf * kGroups + h) * kMaxText + j) * kRows + r] = dp[j];
+    mma_commit(bar);
   };
 
-  // relevance of a finished tile from its partial norms and prompt dots (buffer it & 1);
-  // run one tile later, while the next tile's MMAs and the other warps' stores proceed
+  // relevance of a finished tile (first CTA, threads t < 128 = rows) from its norm parts and
+  // the prompt dots, or with a partner, its half norm and the dots the partner formed
   auto finish_rel = [&](int64_t tl, int itl) {
-    const int64_t pr = tl * kRows + r;
+    const int64_t pr = tl * kRows + t;
     if (pr >= a.P) return;
-    const int buf = itl & 1;
+    const int nb = itl % kXBufs, db = itl % kDotBufs;
+    const float* pb = sPeer + nb * (1 + kMaxText) * kRows + t;   // the partner's row t
     float nrm = 0.f;
-    for (int g = 0; g < kGroups; ++g) nrm += sNrm[(buf * kGroups + g) * kRows + r];
+    for (int g = 0; g < kGroups; ++g) nrm += sNrm[(nb * kGroups + g) * kRows + t];
+    if (nrank > 1) nrm += pb[0];
     const float inv = 1.f / (sqrtf(nrm) + a.eps);
     float d[kMaxText];
 #pragma unroll
-    for (int j = 0; j < kMaxText; ++j) {
-      d[j] = 0.f;
-      if (j < nt)
-        for (int g = 0; g < kGroups; ++g) d[j] += sDot[((buf * kGroups + g) * kMaxText + j) * kRows + r];
-    }
+    for (int j = 0; j < kMaxText; ++j)
+      d[j] = j >= ntx ? 0.f : (nrank > 1 ? pb[(1 + j) * kRows] : sDot[(db * kMaxText + j) * kRows + t]);
     float best = 0.f;
 #pragma unroll
     for (int j = 1; j < kMaxText; ++j)
-      if (j < nt) best = fmaxf(best, 1.f / (1.f + __expf(a.tau * (d[j] - d[0]) * inv)));
+      if (j < ntx) best = fmaxf(best, 1.f / (1.f + __expf(a.tau * (d[j] - d[0]) * inv)));
     a.rel[pr] = best;
   };
 
-  // each CTA decodes one contiguous range of tiles
-  const int64_t t_per = (n_tiles + gridDim.x - 1) / gridDim.x;
-  const int64_t t_begin = min(n_tiles, (int64_t)blockIdx.x * t_per), t_end = min(n_tiles, t_begin + t_per);
-  int64_t tile = t_begin;
-  if (tile < t_end) {
-    load_rows(tile);
-    row_dots();
-    store_rows(0);
+  // each cluster decodes one contiguous range of tiles (both CTAs the same range)
+  const int64_t n_cl = gridDim.x / nrank, cl = blockIdx.x / nrank;
+  const int64_t t_per = (n_tiles + n_cl - 1) / n_cl;
+  const int64_t t_begin = min(n_tiles, cl * t_per), t_end = min(n_tiles, t_begin + t_per);
+  const int n_local = (int)(t_end - t_begin);
+  if (n_local > 0) {
+    load_rows(t_begin);
+    stage_a();
+    stage_dots(0);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (n_local > 0 && t == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    issue(0);
+  }
+  if (n_local > 1) load_rows(t_begin + 1);
+
+  // The exchange of a column-split pair, in kXBufs buffers (tile i in buffer i mod kXBufs):
+  // the second CTA stores its 128 half norms into the first CTA's buffer with asynchronous
+  // stores that complete the buffer's `full` mbarrier; the first CTA, once it has read them,
+  // arrives on the second CTA's `consumed` mbarrier, which the second CTA waits for before
+  // it reuses the buffer.  Every wait is bounded (a timeout sets the error flag and ends
+  // this thread's part in the exchange).
+  // A phase of `full` takes exactly one arrival: thread 0 arms it only while its own waits
+  // succeed (a phase it saw complete), never twice.
+  auto recv_wait = [&](int i) {   // first CTA: the half norms of tile i are in
+    const uint32_t fb = full0 + 8u * (uint32_t)(i % kXBufs);
+    if (t == 0 && xfer_ok) mbar_arrive_expect(fb, (uint32_t)((1 + ntx) * kRows * 4));
+    if (t < kRows && xfer_ok && !mbar_wait_cluster(fb, (uint32_t)(i / kXBufs) & 1u)) {
+      xfer_ok = false;
+      if (a.err) atomicExch(a.err, 1);
+    }
+  };
+  auto recv_done = [&](int i) {   // first CTA, after a barrier behind the reads of tile i
+    if (t == 0 && i + kXBufs < n_local) mbar_arrive_remote(cluster_addr(cons0 + 8u * (uint32_t)(i % kXBufs), 1u));
+  };
+  // second CTA, threads t < 128: row t of tile i, its half norm v and (zero = false) the
+  // prompt dots it formed for the tile
+  auto send = [&](int i, float v, bool zero) {
+    if (xfer_ok && i >= kXBufs &&
+        !mbar_wait_cluster(cons0 + 8u * (uint32_t)(i % kXBufs), (uint32_t)(i / kXBufs - 1) & 1u)) {
+      xfer_ok = false;
+      if (a.err) atomicExch(a.err, 1);
+    }
+    if (xfer_ok) {
+      const uint32_t rb = cluster_addr(full0 + 8u * (uint32_t)(i % kXBufs), 0u);
+      const float* pb = sPeer + (i % kXBufs) * (1 + kMaxText) * kRows + t;   // the same row there
+      st_async_f32(cluster_addr(smem_u32(pb), 0u), v, rb);
+      for (int j = 0; j < ntx; ++j)
+        st_async_f32(cluster_addr(smem_u32(pb + (1 + j) * kRows), 0u),
+                     zero ? 0.f : sDot[((i % kDotBufs) * kMaxText + j) * kRows + t], rb);
+    }
+  };
+
   uint32_t phase = 0;
   bool failed = false;
-  for (int it = 0; tile < t_end; ++tile, ++it) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (t == 0) {
-      for (int ks = 0; ks < L / 8; ++ks) {
-        const uint64_t ad = smem_desc(a_base + 256u * ks, 128u, sbo);
-        for (int n0 = 0; n0 < Dc; n0 += 256) {
-          const int N = min(256, Dc - n0);
-          const uint64_t bd = smem_desc(b_base + (uint32_t)(n0 >> 3) * sbo + 256u * ks, 128u, sbo);
-          mma_tf32(tmem + (uint32_t)n0, ad, bd, idesc_tf32(kRows, N), ks > 0 ? 1u : 0u);
-        }
-      }
-      mma_commit(bar);
-    }
-    // issue the next tile's weight loads (first used after this tile's epilogue, so their
-    // latency hides behind its stores) and finish the previous tile's relevance while the
-    // tensor cores run
-    const int64_t next = tile + 1;
-    if (next < t_end) load_rows(next);
-    if (want_rel && h == 0 && it > 0) finish_rel(tile - 1, it - 1);
+  int done = 0;   // tiles whose epilogue is complete
+  for (int it = 0; it < n_local; ++it) {
+    const int64_t tile = t_begin + it;
+    // the MMAs of this tile are done: A is free and accumulator it & 1 is final
     const bool ok = mbar_wait(bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {   // every thread takes the same branch
@@ -334,17 +514,32 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: TMEM lanes 32 (warp mod 4) .. + 31 = pixels; chunks h, h + 4, ... of F
-    const int64_t p = tile * kRows + 32 * (warp & 3) + lane;
+    if (it + 1 < n_local) stage_a();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();   // next A staged
+    if (it + 1 < n_local && t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue((it + 1) & 1);   // runs during this tile's epilogue
+    }
+    if (it + 1 < n_local) stage_dots((it + 1) % kDotBufs);
+    if (it + 2 < n_local) load_rows(tile + 2);   // consumed after the next tile's MMAs
+    if (want_rel && it >= lag) {
+      if (exch && rank == 0) recv_wait(it - lag);   // the partner's half norms and dots
+      if (rel_here && t < kRows) finish_rel(tile - lag, it - lag);
+    }
+    // epilogue: TMEM lanes 32 (warp mod 4) .. + 31 = pixels; chunks w / 4, w / 4 + 4, ...
+    const int q4 = warp & 3, cg = warp >> 2;
+    const int64_t p = tile * kRows + 32 * q4 + lane;
     const bool store = p < a.P && a.F != nullptr;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)((it & 1) * Db);
     float n4[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c0 = 32 * h; c0 < Dc; c0 += 32 * kGroups) {
+    for (int c0 = 32 * cg; c0 < Dh; c0 += 32 * kGroups) {
       float v[32];
       tmem_ld32(lane_addr + (uint32_t)c0, v);
-      const int nv = min(32, Dc - c0);   // a multiple of 16
+      const int nv = min(32, Dh - c0);   // a multiple of 16
       if (store) {
-        float* fp = a.F + (int64_t)c0 * a.P + p;
+        float* fp = a.F + (int64_t)(n_lo + c0) * a.P + p;
         if (nv == 32) {
 #pragma unroll
           for (int j = 0; j < 32; ++j, fp += a.P) *fp = v[j];
@@ -363,24 +558,41 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
       }
     }
     if (want_rel)
-      sNrm[((it & 1) * kGroups + h) * kRows + 32 * (warp & 3) + lane] = (n4[0] + n4[1]) + (n4[2] + n4[3]);
+      sNrm[((it % kXBufs) * kGroups + cg) * kRows + 32 * q4 + lane] = (n4[0] + n4[1]) + (n4[2] + n4[3]);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();   // MMA done, TMEM read, previous relevance done: A and the other buffers free
-    if (next < t_end) {
-      row_dots();
-      store_rows((it + 1) & 1);
+    __syncthreads();   // accumulator it & 1 read, norms of this tile complete
+    if (exch) {
+      if (rank == 0 && it >= lag) recv_done(it - lag);
+      if (rank == 1 && t < kRows) {
+        float s = 0.f;
+        for (int g = 0; g < kGroups; ++g) s += sNrm[((it % kXBufs) * kGroups + g) * kRows + t];
+        send(it, s, false);
+      }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();   // next A tile staged; norms and dots consumed
+    done = it + 1;
   }
   if (failed) {
     if (t == 0 && a.err) atomicExch(a.err, 1);
     mbar_wait(bar, phase ^ 1u);   // bounded: let this CTA's own MMAs drain before freeing TMEM
-  } else if (want_rel && h == 0 && t_begin < t_end) {
-    // the last tile's relevance (its partials were published by the loop's last barrier)
-    const int64_t last = t_end - 1;
-    finish_rel(last, (int)(last - t_begin));
+  }
+  if (exch) {
+    // finish the exchange for every tile the partner still sends (zeros after a failure),
+    // then meet once more: neither CTA leaves while the other may still address it
+    if (rank == 0) {
+      for (int i = max(0, done - lag); i < n_local; ++i) {
+        recv_wait(i);
+        if (!failed && t < kRows) finish_rel(t_begin + i, i);
+        __syncthreads();
+        recv_done(i);
+      }
+    } else if (t < kRows) {
+      for (int i = done; i < n_local; ++i) send(i, 0.f, true);
+    }
+    __syncwarp();
+    cluster_arrive();
+    cluster_wait();
+  } else if (!failed && rel_here && t < kRows && n_local > 0) {
+    finish_rel(t_end - 1, n_local - 1);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
@@ -388,7 +600,6 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
                  : "memory");
 }
-
 // w_i = softmax(z_i): one warp per Gaussian, L <= 64 logits (two per lane).
 template <bool BF16>
 __global__ void __launch_bounds__(256)
@@ -443,7 +654,7 @@ k_vq_weights_bwd(const float* __restrict__ z, const float* __restrict__ g, int64
   if (lane + 32 < L) gz[row * L + lane + 32] = wb * (gb - d);
 }
 
-size_t decode_smem(int L, int Dc) { return DecodeSmem(L, Dc).total; }
+size_t decode_smem(int L, int Dh) { return DecodeSmem(L, Dh).total; }
 
 }  // namespace
 }  // namespace gs
@@ -488,25 +699,42 @@ gs_status gs_vq_decode(const float* wmap, int64_t P, int32_t L, const float* cod
   if (cudaGetDevice(&dev) != cudaSuccess) return GS_ERR_CUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  // At most 512 / ncols CTAs may hold their tensor memory on one SM at a time: request
-  // enough shared memory that no more than that many are resident (a further CTA would only
-  // wait inside its allocation).
+  // Up to 256 columns one CTA holds the split codebook; above, a cluster of two splits the
+  // columns (the first takes the larger share, a multiple of 16 for the MMA's N).
+  const int nc = Dc <= kMaxDh ? 1 : 2;
+  const int Dh0 = nc == 1 ? Dc : std::min(kMaxDh, (Dc / 2 + 15) / 16 * 16);
+  // Each CTA holds two accumulators of Db columns.  At most 512 / ncols CTAs may hold their
+  // tensor memory on one SM at a time: request enough shared memory that no more than that
+  // many are resident (a further CTA would only wait inside its allocation).
+  const int Db = (Dh0 + 31) / 32 * 32;
   int ncols = 32;
-  while (ncols < Dc) ncols <<= 1;
+  while (ncols < 2 * Db) ncols <<= 1;
   const int per_sm = 512 / ncols;
-  size_t smem = decode_smem(L, Dc);
+  size_t smem = decode_smem(L, Dh0);
   if (per_sm < kMaxResident && smem_sm > 0)
     smem = std::max<size_t>(smem, (size_t)smem_sm / (size_t)(per_sm + 1) + 1024);
   if (cudaFuncSetAttribute(k_vq_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return GS_ERR_CUDA;
-  DecodeArgs a{wmap, P, L, codebook, Dc, F_out, text, relevance ? n_text : 0, tau, 1e-8f,
+  DecodeArgs a{wmap, P, L, codebook, Dc, Dh0, F_out, text, relevance ? n_text : 0, tau, 1e-8f,
                relevance, err};
   const int64_t n_tiles = (P + kRows - 1) / kRows;
-  const unsigned grid = (unsigned)min64(n_tiles, (int64_t)sms * per_sm);
-  k_vq_decode<<<grid, kVT, smem, (cudaStream_t)stream>>>(a);
+  const int64_t clusters = min64(n_tiles, (int64_t)sms * per_sm / nc);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(clusters * nc), 1, 1);
+  cfg.blockDim = dim3(kVT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_vq_decode, a);
   note_launch();
-  return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
 }  // extern "C"
