@@ -99,7 +99,8 @@ struct gs_workspace {
   DevBuf<float> g2d;
   DevBuf<float> pose_partials;
   // per instance: sorted depth keys and ids, their ping-pong space, the slot's tile
-  DevBuf<uint32_t> inst_key, inst_id, inst_key2, inst_id2;
+  DevBuf<uint32_t> inst_key, inst_id;   // sort scratch keys, sorted ids
+  DevBuf<uint2> inst_kv;                 // scattered (key, id) pairs
   // per tile / pixel
   DevBuf<uint2> ranges;
   DevBuf<uint32_t> tile_order, queue;   // heavy-first tile order; persistent-kernel queues
@@ -236,8 +237,7 @@ cudaError_t ensure_gauss(gs_workspace* ws, int64_t n) {
 cudaError_t ensure_inst(gs_workspace* ws, int64_t cap) {
   const size_t m = (size_t)std::max<int64_t>(cap, 1);
   cudaError_t e;
-  if ((e = ws->inst_key.ensure(m)) || (e = ws->inst_id.ensure(m)) ||
-      (e = ws->inst_key2.ensure(m)) || (e = ws->inst_id2.ensure(m)))
+  if ((e = ws->inst_key.ensure(m)) || (e = ws->inst_id.ensure(m)) || (e = ws->inst_kv.ensure(m)))
     return e;
   return cudaSuccess;
 }
@@ -301,7 +301,7 @@ void gs_workspace_destroy(gs_workspace* ws) {
     cudaDeviceSynchronize();
     ws->rec.release(); ws->depth_key.release(); ws->ntiles.release();
     ws->rect.release(); ws->item_max.release(); ws->g2d.release(); ws->pose_partials.release();
-    ws->inst_key.release(); ws->inst_id.release(); ws->inst_key2.release(); ws->inst_id2.release();
+    ws->inst_key.release(); ws->inst_id.release(); ws->inst_kv.release();
     ws->ranges.release(); ws->T_final.release(); ws->n_contrib.release();
     ws->tile_order.release(); ws->queue.release(); ws->tile_count.release(); ws->tile_cursor.release();
     ws->counters.release(); ws->stats64.release();
@@ -349,7 +349,7 @@ gs_status gs_workspace_bytes(gs_workspace* ws, int64_t* bytes) {
   auto add = [&b](const auto& buf) { b += buf.cap * sizeof(*buf.p); };
   add(ws->rec); add(ws->depth_key); add(ws->ntiles); add(ws->rect); add(ws->item_max);
   add(ws->g2d); add(ws->pose_partials);
-  add(ws->inst_key); add(ws->inst_id); add(ws->inst_key2); add(ws->inst_id2);
+  add(ws->inst_key); add(ws->inst_id); add(ws->inst_kv);
   add(ws->ranges); add(ws->tile_order); add(ws->queue); add(ws->tile_count); add(ws->tile_cursor);
   add(ws->T_final); add(ws->n_contrib); add(ws->counters); add(ws->stats64);
   *bytes = (int64_t)b;
@@ -434,10 +434,9 @@ gs_status gs_bin_tiles(gs_workspace* ws, int64_t* n_instances_out, void* stream)
   b.ranges = ws->ranges.p;
   b.order = ws->tile_order.p;
   b.queue = ws->queue.p + 4;
+  b.kv = ws->inst_kv.p;
   b.key0 = ws->inst_key.p;
   b.id0 = ws->inst_id.p;
-  b.key1 = ws->inst_key2.p;
-  b.id1 = ws->inst_id2.p;
   b.counters = cnt;
   ws->ordered = launch_bin(b, st);
   ws->tile_counts_dirty = false;   // the scan cleared them
@@ -730,13 +729,11 @@ gs_status ws_reserve_fixed(gs_workspace* ws, int64_t n_gauss, int64_t n_pixels, 
   return GS_OK;
 }
 
-void ws_lend_instances(gs_workspace* ws, uint32_t* key0, uint32_t* id0, uint32_t* key1,
-                       uint32_t* id1, int64_t cap) {
+void ws_lend_instances(gs_workspace* ws, uint2* kv, uint32_t* key0, uint32_t* id0, int64_t cap) {
   const size_t m = (size_t)std::max<int64_t>(cap, 0);
+  ws->inst_kv.lend(kv, m);
   ws->inst_key.lend(key0, m);
   ws->inst_id.lend(id0, m);
-  ws->inst_key2.lend(key1, m);
-  ws->inst_id2.lend(id1, m);
 }
 
 bool ws_fits(const gs_workspace* ws, int64_t n_gauss, int64_t n_pixels, int64_t n_tiles) {

@@ -66,7 +66,7 @@ void launch_project(const gs_scene& sc, const CamDev& cam, GaussRec* rec, uint32
 
 // gs_sort.cu: binning in tile buckets (scan, scatter, per-tile radix sort; the count is
 // added by the projection).  After launch_bin, tile t's Gaussians occupy slots [ranges[t].x, ranges[t].y) of id0 in
-// (depth, id) order (key0 holds the unsorted depth keys; key1, id1 are scratch); slots are capped
+// (depth, id) order (kv holds the scattered (key, id) pairs; kv and key0 are also scratch); slots are capped
 // at `cap` (an instance count above it sets kErrInstOverflow).  `order` receives the
 // heavy-first tile order when there are at most kMaxOrderedTiles tiles (the return value
 // says whether it was written).  No host synchronisation.
@@ -83,8 +83,9 @@ struct BinArgs {
   uint2* ranges;                 // [n_tiles] out
   uint32_t* order;               // [n_tiles] out (heavy-first)
   uint32_t* queue;               // two words: the persistent sort's queue head and leave count
-  uint32_t *key0, *id0;          // [cap] id0 out: sorted Gaussian ids; key0: depth keys
-  uint32_t *key1, *id1;          // [cap] scratch (ranges longer than shared memory)
+  uint2* kv;                     // [cap] (depth key, id) pairs of the scatter
+  uint32_t *key0, *id0;          // [cap] id0 out: sorted Gaussian ids; key0: scratch (ranges
+                                 // longer than shared memory)
   uint32_t* counters;            // workspace counters (status word)
 };
 constexpr int kMaxOrderedTiles = 1 << 18;

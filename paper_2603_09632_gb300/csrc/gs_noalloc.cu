@@ -30,11 +30,10 @@ constexpr size_t oRec = 0;
 constexpr size_t oKey = al(oRec + kNaMaxGauss * sizeof(GaussRec));
 constexpr size_t oNt = al(oKey + kNaMaxGauss * 4);
 constexpr size_t oRect = al(oNt + kNaMaxGauss * 4);
-constexpr size_t oK0 = al(oRect + kNaMaxGauss * 8);        // instance depth keys / ids
-constexpr size_t oI0 = al(oK0 + kNaMaxInst * 4);
-constexpr size_t oK1 = al(oI0 + kNaMaxInst * 4);          // their ping-pong space
-constexpr size_t oI1 = al(oK1 + kNaMaxInst * 4);
-constexpr size_t oTf = al(oI1 + kNaMaxInst * 4);
+constexpr size_t oKV = al(oRect + kNaMaxGauss * 8);        // instance (key, id) pairs
+constexpr size_t oK0 = al(oKV + kNaMaxInst * 8);          // sort scratch keys
+constexpr size_t oI0 = al(oK0 + kNaMaxInst * 4);          // sorted ids
+constexpr size_t oTf = al(oI0 + kNaMaxInst * 4);
 constexpr size_t oNc = al(oTf + kNaMaxPix * 4);
 constexpr size_t oRanges = al(oNc + kNaMaxPix * 4);
 constexpr size_t oOrder = al(oRanges + kNaMaxTiles * 8);
@@ -126,8 +125,8 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   uint32_t* key = reinterpret_cast<uint32_t*>(base + oKey);
   uint32_t* nt = reinterpret_cast<uint32_t*>(base + oNt);
   uint2* rect = reinterpret_cast<uint2*>(base + oRect);
+  uint2* kv = reinterpret_cast<uint2*>(base + oKV);
   uint32_t *k0 = reinterpret_cast<uint32_t*>(base + oK0), *i0 = reinterpret_cast<uint32_t*>(base + oI0);
-  uint32_t *k1 = reinterpret_cast<uint32_t*>(base + oK1), *i1 = reinterpret_cast<uint32_t*>(base + oI1);
   float* Tf = reinterpret_cast<float*>(base + oTf);
   uint32_t* nc = reinterpret_cast<uint32_t*>(base + oNc);
   uint2* ranges = reinterpret_cast<uint2*>(base + oRanges);
@@ -167,10 +166,9 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   b.ranges = ranges;
   b.order = order;
   b.queue = queue + 2;
+  b.kv = kv;
   b.key0 = k0;
   b.id0 = i0;
-  b.key1 = k1;
-  b.id1 = i1;
   b.counters = cnt;
   const bool ordered = launch_bin(b, st);
   const TileQueue tq{queue, queue + 1, ordered ? order : nullptr, (int)ntl};

@@ -38,7 +38,7 @@ using gs::RasterJob;
 
 constexpr int kMaxLanes = 4;
 constexpr double kAgingS = 0.05;          // a request that waited 50 ms is not overtaken
-constexpr int64_t kInstBytes = 16;        // per instance: key, id and their ping-pong space
+constexpr int64_t kInstBytes = 16;        // per instance: (key, id) pair, scratch key, sorted id
 constexpr int64_t kGaussBytes = 112;      // per Gaussian in a request workspace (planning)
 constexpr int64_t kPixBytes = 8;          // per pixel: final transmittance, last contributor
 constexpr int64_t kMaxPixPerRequest = 3840LL * 2160LL;
@@ -78,7 +78,8 @@ struct gs_server {
   Lane lanes[kMaxLanes];
   void* arena = nullptr;
   int64_t arena_inst = 0;              // instance slots in the arena
-  uint32_t* arr[4] = {};               // key0, id0, key1, id1: [arena_inst] each
+  uint2* kv = nullptr;                 // (key, id) pairs [arena_inst]
+  uint32_t* arr[2] = {};               // scratch keys, sorted ids: [arena_inst] each
   std::unique_ptr<gs_serve::Scheduler<gs_request>> sched;
 };
 
@@ -123,8 +124,7 @@ void launch(gs_server* sv, int lane, std::vector<gs_serve::Item<gs_request>>& it
     gs_workspace* ws = ln.ws[(size_t)it.slot];
     const gs_scene sc = scene_of(sv, it.req.scene_id);
     const int64_t o = it.offset;
-    gs::ws_lend_instances(ws, sv->arr[0] + o, sv->arr[1] + o, sv->arr[2] + o, sv->arr[3] + o,
-                          it.cost);
+    gs::ws_lend_instances(ws, sv->kv + o, sv->arr[0] + o, sv->arr[1] + o, it.cost);
     gs_status s = gs_bin_tiles(ws, nullptr, ln.stream);
     RasterJob j;
     if (s == GS_OK) s = gs::ws_job(ws, sc, &j);
@@ -271,7 +271,8 @@ gs_status start_locked(gs_server* sv) {
     free_lanes(sv);
     return GS_ERR_OOM;
   }
-  for (int k = 0; k < 4; ++k) sv->arr[k] = static_cast<uint32_t*>(sv->arena) + (size_t)k * inst;
+  sv->kv = static_cast<uint2*>(sv->arena);
+  for (int k = 0; k < 2; ++k) sv->arr[k] = reinterpret_cast<uint32_t*>(sv->kv + inst) + (size_t)k * inst;
   if (cudaDeviceSynchronize() != cudaSuccess) return GS_ERR_CUDA;
   sv->pix_cap = pix;
   sv->tile_cap = tiles;

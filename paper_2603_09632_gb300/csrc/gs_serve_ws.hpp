@@ -6,9 +6,9 @@
 
 namespace gs {
 gs_status ws_reserve_fixed(gs_workspace* ws, int64_t n_gauss, int64_t n_pixels, int64_t n_tiles);
-// The instance buffers become the caller's ranges (cap slots each; not freed by the workspace).
-void ws_lend_instances(gs_workspace* ws, uint32_t* key0, uint32_t* id0, uint32_t* key1,
-                       uint32_t* id1, int64_t cap);
+// The instance buffers become the caller's ranges (cap slots each: (key, id) pairs, scratch
+// keys, sorted ids; not freed by the workspace).
+void ws_lend_instances(gs_workspace* ws, uint2* kv, uint32_t* key0, uint32_t* id0, int64_t cap);
 bool ws_fits(const gs_workspace* ws, int64_t n_gauss, int64_t n_pixels, int64_t n_tiles);
 // Asynchronous copy of the projection's tile-instance count to *host (pinned).
 gs_status ws_instances_async(gs_workspace* ws, uint32_t* host, cudaStream_t st);

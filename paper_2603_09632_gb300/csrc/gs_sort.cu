@@ -10,7 +10,7 @@
 //   2. scan: one block turns the counts into tile ranges [start, end) and a heavy-first
 //      tile order for the persistent raster kernels;
 //   3. scatter: every (Gaussian, tile) instance takes a slot in its tile's range
-//      (unordered) and stores the Gaussian's depth key and id there;
+//      (unordered) and stores the Gaussian's depth key and id there as one 8-byte pair;
 //   4. sort: one block per tile sorts its range by depth with a stable LSD radix sort in
 //      shared memory (8-bit digits; a pass whose digit is the same for the whole range is
 //      skipped), then orders runs of equal depth by id, which makes the order the total
@@ -153,8 +153,7 @@ constexpr int kScatterR = 4;
 __global__ void __launch_bounds__(kThreads)
 k_bin_scatter(int64_t n, const uint32_t* __restrict__ ntiles, const uint2* __restrict__ rect,
               const uint32_t* __restrict__ depth_key, int TX, int n_tiles, int64_t cap,
-              uint32_t* __restrict__ cursor, uint32_t* __restrict__ inst_key,
-              uint32_t* __restrict__ inst_id) {
+              uint32_t* __restrict__ cursor, uint2* __restrict__ inst_kv) {
   const int lane = threadIdx.x & 31;
   const int64_t g0 = (int64_t)blockIdx.x * kThreads + (threadIdx.x & ~31);
   const int64_t gl = g0 + lane;
@@ -184,8 +183,7 @@ k_bin_scatter(int64_t n, const uint32_t* __restrict__ ntiles, const uint2* __res
           const uint32_t pos = bs + __popc(peers[r] & ((1u << lane) - 1u));
           if ((int64_t)pos < cap) {
             const int64_t g = g0 + owner[r];
-            inst_key[pos] = depth_key[g];
-            inst_id[pos] = (uint32_t)g;
+            inst_kv[pos] = make_uint2(depth_key[g], (uint32_t)g);   // one 8-byte store
           }
         }
       }
@@ -304,11 +302,14 @@ __device__ __forceinline__ uint32_t block_diff_bits(uint32_t v_or, uint32_t v_an
 }
 
 // One block per tile (persistent, heavy-first): sort the tile's range by (depth, id).
-// The sorted ids are left in id0 (the sorted keys are not written back: nothing reads
-// them); (key1, id1) is the ping-pong space of ranges longer than kSeg.
+// Input: the (key, id) pairs of kv in scatter order; output: the sorted ids in id0 (the
+// sorted keys are not written back: nothing reads them).  Ranges longer than kSeg are
+// sorted through global memory: the first pass reads the pairs and writes (key0, id0);
+// later passes alternate between (key0, id0) and the range's own part of kv, read as n
+// keys followed by n ids (its pairs are consumed by the first pass).
 __global__ void __launch_bounds__(kThreads)
-k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict__ key0,
-           uint32_t* __restrict__ id0, uint32_t* __restrict__ key1, uint32_t* __restrict__ id1) {
+k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint2* __restrict__ kv,
+           uint32_t* __restrict__ key0, uint32_t* __restrict__ id0) {
   __shared__ uint32_t s_k[2][kSeg], s_v[2][kSeg];
   __shared__ uint32_t s_w[kWarps * kRadix];
   __shared__ uint32_t s_dstart[kRadix], s_run[kRadix], s_cnt[kRadix];
@@ -326,24 +327,23 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
     const uint2 rg = ranges[tile];
     const int s = (int)rg.x, n = (int)(rg.y - rg.x);
     if (n <= 1) {
+      if (n == 1 && threadIdx.x == 0) id0[s] = kv[s].y;
       __syncthreads();
       continue;
     }
-    // digit bytes that differ across the range (the others need no pass)
-    uint32_t vo = 0, va = 0xFFFFFFFFu;
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-      const uint32_t k = key0[s + i];
-      vo |= k;
-      va &= k;
-    }
-    const uint32_t diff = block_diff_bits(vo, va, s_red);
     if (n <= kSeg) {
-      int cur = 0;
+      // the pairs into shared memory, and the digit bytes that differ across the range
+      // (the others need no pass)
+      uint32_t vo = 0, va = 0xFFFFFFFFu;
       for (int i = threadIdx.x; i < n; i += kThreads) {
-        s_k[0][i] = key0[s + i];
-        s_v[0][i] = id0[s + i];
+        const uint2 e = kv[s + i];
+        s_k[0][i] = e.x;
+        s_v[0][i] = e.y;
+        vo |= e.x;
+        va &= e.x;
       }
-      __syncthreads();
+      const uint32_t diff = block_diff_bits(vo, va, s_red);   // (its barrier publishes the chunk)
+      int cur = 0;
       const int R = (n + kThreads - 1) / kThreads;
       for (int p = 0; p < 4; ++p) {
         if (((diff >> (8 * p)) & 0xFFu) == 0u) continue;
@@ -364,14 +364,24 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
       __syncthreads();
       for (int i = threadIdx.x; i < n; i += kThreads) id0[s + i] = s_v[cur][i];
     } else {
-      // long range: LSD passes through global memory, chunks of kSeg taken in order
-      uint32_t *ka = key0 + s, *ia = id0 + s, *kb = key1 + s, *ib = id1 + s;
+      uint32_t vo = 0, va = 0xFFFFFFFFu;
+      for (int i = threadIdx.x; i < n; i += kThreads) {
+        const uint32_t k = kv[s + i].x;
+        vo |= k;
+        va &= k;
+      }
+      const uint32_t diff = block_diff_bits(vo, va, s_red);
+      // long range: LSD passes through global memory, chunks of kSeg taken in order.
+      // Source (ka, ia), null while the data is still in the pairs; destination (kb, ib).
+      uint32_t* const wk = reinterpret_cast<uint32_t*>(kv + s);   // the range's part of kv
+      uint32_t *ka = nullptr, *ia = nullptr, *kb = key0 + s, *ib = id0 + s;
       for (int p = 0; p < 4; ++p) {
         if (((diff >> (8 * p)) & 0xFFu) == 0u) continue;
         // digit histogram of the whole range -> running output offsets per digit
         s_cnt[threadIdx.x] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += kThreads) atomicAdd(&s_cnt[(ka[i] >> (8 * p)) & 0xFFu], 1u);
+        for (int i = threadIdx.x; i < n; i += kThreads)
+          atomicAdd(&s_cnt[((ka ? ka[i] : kv[s + i].x) >> (8 * p)) & 0xFFu], 1u);
         __syncthreads();
         {   // exclusive scan of the 256 digit counts, one per thread
           const uint32_t c = s_cnt[threadIdx.x];
@@ -391,8 +401,14 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
         for (int c0 = 0; c0 < n; c0 += kSeg) {
           const int cnt = min(kSeg, n - c0);
           for (int i = threadIdx.x; i < cnt; i += kThreads) {
-            s_k[0][i] = ka[c0 + i];
-            s_v[0][i] = ia[c0 + i];
+            if (ka) {
+              s_k[0][i] = ka[c0 + i];
+              s_v[0][i] = ia[c0 + i];
+            } else {
+              const uint2 e = kv[s + c0 + i];
+              s_k[0][i] = e.x;
+              s_v[0][i] = e.y;
+            }
           }
           __syncthreads();
           ChunkRank cr;
@@ -412,12 +428,22 @@ k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint32_t* __restrict_
           s_run[threadIdx.x] += s_cnt[threadIdx.x];
           __syncthreads();
         }
-        uint32_t* t0 = ka;
+        // the next pass reads what this one wrote and writes the other buffer
+        const bool to_wk = kb == key0 + s;
         ka = kb;
-        kb = t0;
-        t0 = ia;
         ia = ib;
-        ib = t0;
+        kb = to_wk ? wk : key0 + s;
+        ib = to_wk ? wk + n : id0 + s;
+      }
+      if (!ka) {   // every key equal: unpack the pairs for the tie order
+        for (int i = threadIdx.x; i < n; i += kThreads) {
+          const uint2 e = kv[s + i];
+          key0[s + i] = e.x;
+          id0[s + i] = e.y;
+        }
+        __syncthreads();
+        ka = key0 + s;
+        ia = id0 + s;
       }
       order_ties(ka, ia, n);
       __syncthreads();
@@ -500,13 +526,13 @@ bool launch_bin(const BinArgs& b, cudaStream_t st) {
   note_launch();
   if (b.n > 0) {
     k_bin_scatter<<<gb, kThreads, 0, st>>>(b.n, b.ntiles, b.rect, b.depth_key, b.TX, T, b.cap,
-                                           b.cursor, b.key0, b.id0);
+                                           b.cursor, b.kv);
     note_launch();
   }
   // per-tile sort: persistent blocks over the tiles, heaviest first
   const TileQueue tq{b.queue, b.queue + 1, order, T};
   const int grid = persistent_grid(k_bin_sort, kThreads, 0, T);
-  k_bin_sort<<<grid, kThreads, 0, st>>>(tq, b.ranges, b.key0, b.id0, b.key1, b.id1);
+  k_bin_sort<<<grid, kThreads, 0, st>>>(tq, b.ranges, b.kv, b.key0, b.id0);
   note_launch();
   return order != nullptr;
 }
