@@ -307,7 +307,9 @@ __device__ __forceinline__ uint32_t block_diff_bits(uint32_t v_or, uint32_t v_an
 // sorted through global memory: the first pass reads the pairs and writes (key0, id0);
 // later passes alternate between (key0, id0) and the range's own part of kv, read as n
 // keys followed by n ids (its pairs are consumed by the first pass).
-__global__ void __launch_bounds__(kThreads)
+// Five blocks per SM (48 registers, no spill; shared memory holds five): the ranking is a
+// chain of shared-memory round trips, so resident warps are what hides its latency.
+__global__ void __launch_bounds__(kThreads, 5)
 k_bin_sort(TileQueue tq, const uint2* __restrict__ ranges, uint2* __restrict__ kv,
            uint32_t* __restrict__ key0, uint32_t* __restrict__ id0) {
   __shared__ uint32_t s_k[2][kSeg], s_v[2][kSeg];
