@@ -248,7 +248,8 @@ cudaError_t ensure_pix(gs_workspace* ws, int64_t npix, int64_t ntiles) {
       (e = ws->n_contrib.ensure((size_t)std::max<int64_t>(npix, 1))))
     return e;
   const size_t t = (size_t)std::max<int64_t>(ntiles, 1);
-  if ((e = ws->tile_order.ensure(t)) || (e = ws->tile_count.ensure_zeroed(t)) ||
+  // the tile counts are kept as per-row differences: TY (TX + 1) <= 2 TX TY words
+  if ((e = ws->tile_order.ensure(t)) || (e = ws->tile_count.ensure_zeroed(2 * t)) ||
       (e = ws->tile_cursor.ensure(t)))
     return e;
   return ws->ranges.ensure(t);

@@ -77,8 +77,8 @@ struct BinArgs {
   const uint32_t* depth_key;     // [n]
   int TX, n_tiles;
   int64_t cap;                   // instance slots available
-  uint32_t* tile_count;          // [n_tiles] tile instance counts (from the projection; the
-                                 // scan zeroes them after reading)
+  uint32_t* tile_count;          // [TY (TX + 1)] per-row tile count differences (from the
+                                 // projection; the row pass and the scan zero them)
   uint32_t* cursor;              // [n_tiles] scratch
   uint2* ranges;                 // [n_tiles] out
   uint32_t* order;               // [n_tiles] out (heavy-first)
@@ -164,15 +164,58 @@ __device__ __forceinline__ void warp_tile_instances(uint32_t nt, uint2 rc, int T
   }
 }
 
-// Adds each lane's tile instances to tile_count: one atomic per distinct tile per warp round.
+// Slot of tile i (row-major, TX tiles per row) in the binning's per-tile count array,
+// which holds TY rows of TX + 1 words: the projection adds row differences there, and the
+// binning's row pass turns each row into counts in place (the last word of a row is the
+// difference past the right edge).
+__device__ __forceinline__ uint32_t tile_slot(uint32_t i, int TX) { return i + i / (uint32_t)TX; }
+
+// The count step's form, the same on the host and in the kernels: frames of at least 4096
+// tiles (Gaussians covering many tiles) add per-row differences (warp_count_rows, then the
+// binning's row pass); smaller frames add per-tile counts at tile_slot (warp_count_tiles,
+// merged within a warp) and need no row pass.
+constexpr int kRowCountTiles = 4096;
+__host__ __device__ inline bool count_tile_rows(int n_tiles) { return n_tiles >= kRowCountTiles; }
+
+// Adds each lane's tile instances at tile_slot: one atomic per distinct tile per warp round.
 __device__ __forceinline__ void warp_count_tiles(uint32_t nt, uint2 rc, int TX, int n_tiles,
                                                  uint32_t* tile_count) {
   warp_tile_instances(nt, rc, TX, [&](int, uint32_t tile) {
     const bool ok = tile < (uint32_t)n_tiles;
     const uint32_t peers = __match_any_sync(0xffffffffu, ok ? tile : 0xFFFFFFFFu);
     if (ok && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0)
-      atomicAdd(&tile_count[tile], (uint32_t)__popc(peers));
+      atomicAdd(&tile_count[tile_slot(tile, TX)], (uint32_t)__popc(peers));
   });
+}
+
+// Adds each lane's tile rectangle to the per-row difference array: +1 at its first tile
+// and -1 past its last tile of every tile row it covers (two atomics per row; the row
+// pass of the binning sums them into per-tile counts).  The warp's rows are flattened
+// across its lanes, 32 per round.
+__device__ __forceinline__ void warp_count_rows(uint32_t nt, uint2 rc, int TX, uint32_t* tile_diff) {
+  const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
+  const uint32_t rows = nt ? y1 - y0 : 0u;
+  const WarpInstances wi = warp_instances_begin(rows, rc);
+  const unsigned full = 0xffffffffu;
+  const uint32_t stride = (uint32_t)TX + 1u;
+  for (uint32_t base = 0; base < wi.total; base += 32) {
+    const uint32_t k = base + (threadIdx.x & 31);
+    // owner: the last lane whose first row is <= k (it has at least one row)
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const int mid = (lo + hi + 1) >> 1;
+      const uint32_t e = __shfl_sync(full, wi.excl, mid);
+      if (e <= k) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t oe = __shfl_sync(full, wi.excl, lo);
+    const uint32_t rx = __shfl_sync(full, rc.x, lo), ry = __shfl_sync(full, rc.y, lo);
+    if (k < wi.total) {
+      const uint32_t row = (rx >> 16) + (k - oe);
+      atomicAdd(&tile_diff[row * stride + (rx & 0xFFFFu)], 1u);
+      atomicAdd(&tile_diff[row * stride + (ry & 0xFFFFu)], 0xFFFFFFFFu);   // -1
+    }
+  }
 }
 
 __device__ __forceinline__ void queue_leave(const TileQueue& tq, unsigned participants) {

@@ -38,7 +38,7 @@ constexpr size_t oNc = al(oTf + kNaMaxPix * 4);
 constexpr size_t oRanges = al(oNc + kNaMaxPix * 4);
 constexpr size_t oOrder = al(oRanges + kNaMaxTiles * 8);
 constexpr size_t oTCount = al(oOrder + kNaMaxTiles * 4);    // binning scratch
-constexpr size_t oTCursor = al(oTCount + kNaMaxTiles * 4);
+constexpr size_t oTCursor = al(oTCount + kNaMaxTiles * 8);   // (per-row differences: <= 2 words a tile)
 constexpr size_t oCnt = al(oTCursor + kNaMaxTiles * 4);     // counters
 constexpr size_t oQueue = al(oCnt + kCntNum * 4);           // persistent-kernel queues
 constexpr size_t kNaBytes = al(oQueue + 8 * 4);
@@ -141,7 +141,7 @@ extern "C" gs_status gs_render_fwd_noalloc(const gs_scene* scene, const gs_camer
   // cleared here as well since nothing else initialises this array)
   if (cudaMemsetAsync(cnt, 0, kCntNum * 4, st) != cudaSuccess ||
       cudaMemsetAsync(queue, 0, 8 * 4, st) != cudaSuccess ||
-      cudaMemsetAsync(tcount, 0, ntl * 4, st) != cudaSuccess)
+      cudaMemsetAsync(tcount, 0, (size_t)cd.TY * (cd.TX + 1) * 4, st) != cudaSuccess)
     return GS_ERR_CUDA;
   launch_project(*scene, cd, rec, key, nt, rect, cnt, tcount, st);
   // the instance count decides whether the request fits: one synchronisation

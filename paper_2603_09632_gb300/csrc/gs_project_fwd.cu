@@ -232,8 +232,14 @@ k_project(int64_t n, CamDev cam, const float* __restrict__ means, const float* _
     cnt_i = nt;
     rc_l = rc;
   }
-  // per-tile instance counts for the binning (the count step of the tile buckets)
-  if (tile_count) warp_count_tiles(cnt_i, rc_l, cam.TX, cam.TX * cam.TY, tile_count);
+  // per-tile instance counts for the binning (the count step of the tile buckets): per-row
+  // differences on large frames, per-tile counts otherwise (uniform over the launch)
+  if (tile_count) {
+    if (count_tile_rows(cam.TX * cam.TY))
+      warp_count_rows(cnt_i, rc_l, cam.TX, tile_count);
+    else
+      warp_count_tiles(cnt_i, rc_l, cam.TX, cam.TX * cam.TY, tile_count);
+  }
   // V and I for the workspace counters: warp sums, then one atomic per block
   __shared__ uint32_t s_cnt[2];
   if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0u;

@@ -42,13 +42,37 @@ __device__ __forceinline__ int order_key(uint32_t count) {
   return kScanThreads - 1 - (int)min(count, (uint32_t)(kScanThreads - 1));
 }
 
+// Row pass of the tile counts: the projection left per-row differences (TY rows of TX + 1
+// words, +1 where a rectangle's row starts and -1 past its end); each row becomes its
+// inclusive prefix sums in place, i.e. the tile counts at tile_slot(i), and the word past
+// the row's last tile is cleared.  One warp per row.
+__global__ void __launch_bounds__(kThreads)
+k_bin_rows(uint32_t* __restrict__ tile_diff, int TX, int TY) {
+  const int row = blockIdx.x * kWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= TY) return;   // uniform over the warp
+  uint32_t* r = tile_diff + (int64_t)row * (TX + 1);
+  uint32_t carry = 0;
+  for (int x0 = 0; x0 < TX; x0 += 32) {
+    const int x = x0 + lane;
+    uint32_t v = x < TX ? r[x] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, v, o);
+      if (lane >= o) v += y;
+    }
+    if (x < TX) r[x] = carry + v;
+    carry += __shfl_sync(kFull, v, 31);
+  }
+  if (lane == 0) r[TX] = 0u;
+}
+
 // Exclusive scan of the tile counts -> ranges (clamped to the instance capacity), write
 // cursors, the overflow flag, and the heavy-first order (a counting sort of the tiles by
 // list length, longest first; the order inside a bucket is arbitrary and results do not
 // depend on it).  The counts are zeroed after their last read, ready for the next
 // projection.  One block.
 __global__ void __launch_bounds__(kScanThreads)
-k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
+k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int TX, int64_t cap,
            uint2* __restrict__ ranges, uint32_t* __restrict__ cursor, uint32_t* __restrict__ order,
            uint32_t* counters) {
   __shared__ uint32_t s_warp[kScanThreads / 32];
@@ -64,8 +88,8 @@ k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
     uint32_t sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanPer; ++j) {
-      c[j] = i0 + j < n_tiles ? tile_count[i0 + j] : 0u;
-      if (!order && i0 + j < n_tiles) tile_count[i0 + j] = 0u;   // last read without an order
+      c[j] = i0 + j < n_tiles ? tile_count[tile_slot(i0 + j, TX)] : 0u;
+      if (!order && i0 + j < n_tiles) tile_count[tile_slot(i0 + j, TX)] = 0u;   // last read without an order
       sum += c[j];
       if (order) {   // bucket histogram: one shared atomic per distinct bucket per warp
         const int key = i0 + j < n_tiles ? order_key(c[j]) : kScanThreads;
@@ -134,8 +158,8 @@ k_bin_scan(uint32_t* __restrict__ tile_count, int n_tiles, int64_t cap,
   __syncthreads();
   for (int i0 = 0; i0 < n_tiles; i0 += kScanThreads) {   // warp-aggregated bucket slots
     const int i = i0 + t;
-    const int key = i < n_tiles ? order_key(tile_count[i]) : kScanThreads;
-    if (i < n_tiles) tile_count[i] = 0u;   // last read
+    const int key = i < n_tiles ? order_key(tile_count[tile_slot(i, TX)]) : kScanThreads;
+    if (i < n_tiles) tile_count[tile_slot(i, TX)] = 0u;   // last read
     const unsigned peers = __match_any_sync(kFull, key);
     const int leader = __ffs(peers) - 1;
     uint32_t base = 0;
@@ -523,7 +547,12 @@ bool launch_bin(const BinArgs& b, cudaStream_t st) {
   if (T <= 0) return false;
   const unsigned gb = (unsigned)max64(ceil_div(b.n, kThreads), 1);
   uint32_t* order = T <= kMaxOrderedTiles ? b.order : nullptr;
-  k_bin_scan<<<1, kScanThreads, 0, st>>>(b.tile_count, T, b.cap, b.ranges, b.cursor, order,
+  if (count_tile_rows(T)) {   // the projection left per-row differences
+    const int TY = T / b.TX;
+    k_bin_rows<<<(unsigned)ceil_div(TY, kWarps), kThreads, 0, st>>>(b.tile_count, b.TX, TY);
+    note_launch();
+  }
+  k_bin_scan<<<1, kScanThreads, 0, st>>>(b.tile_count, T, b.TX, b.cap, b.ranges, b.cursor, order,
                                          b.counters);
   note_launch();
   if (b.n > 0) {

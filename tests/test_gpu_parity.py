@@ -298,9 +298,9 @@ def test_argument_errors():
 
 # ---------------------------------------------------------------- binning edge cases
 
-def _lists_equal(oracle, sc, cam):
+def _lists_equal(oracle, sc, cam, rast=None):
     from paper_2603_09632_gb300 import _lib as L
-    gpu = U.run(sc, cam)
+    gpu = U.run(sc, cam, rast=rast)
     TX, TY = oracle.tiles(cam)
     keys, ids, ranges = oracle.tile_lists(sc, cam)
     tiles_g, ids_g, ranges_g = L.gs_get_instances(gpu["rast"].ws, TX * TY)
@@ -343,3 +343,48 @@ def test_equal_depths_are_ordered_by_id(oracle, crowded):
     gpu, ranges = _lists_equal(oracle, sc, cam)
     if crowded:
         assert (ranges[:, 1] - ranges[:, 0]).max() > 2048
+
+
+def _large_frame_scene(W, H, n=40_000, seed=31):
+    """A room seen at W x H (at least 4096 tiles: the projection counts tile instances as
+    per-row differences there) plus a few large Gaussians in front of the camera, whose
+    rectangles reach the right and bottom edges of the tile grid (clamped)."""
+    sc = S.room_scene(n, n_feat=4, sh_degree=0, seed=seed)
+    cam = S.room_trajectory(8, W, H, 0.9 * W)[1]
+    R, t = np.asarray(cam.R, np.float64), np.asarray(cam.t, np.float64)
+    centre = -R.T @ t
+    fwd = R.T @ np.array([0.0, 0.0, 1.0])
+    rng = np.random.default_rng(seed)
+    for k in range(6):   # overwrite a few Gaussians: 0.3-0.6 m in front, large
+        i = k * 997
+        right = R.T @ np.array([1.0, 0.0, 0.0])
+        down = R.T @ np.array([0.0, 1.0, 0.0])
+        sc.means[i] = centre + fwd * rng.uniform(1.0, 2.0) + right * rng.uniform(0.2, 0.8) + down * rng.uniform(0.1, 0.5)
+        sc.scales[i] = rng.uniform(0.15, 0.3, 3)
+    return sc, cam
+
+
+@pytest.mark.parametrize("W,H", [(1090, 1030), (1024, 1024)])
+def test_tile_lists_bit_exact_row_counted_frames(oracle, W, H):
+    """Frames of at least 4096 tiles (ragged and exact tile multiples): the tile counts come
+    from per-row differences and the binning's row pass; keys, ids and ranges must equal
+    the oracle's, and large Gaussians must reach the last tile column."""
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    assert TX * TY >= 4096
+    sc, cam = _large_frame_scene(W, H)
+    proj = oracle.project(sc, cam, "f32")
+    rect = proj["rect"][proj["valid"]]
+    assert (rect[:, 2] == TX).any()      # some rectangle is clamped at the right edge
+    _lists_equal(oracle, sc, cam)
+
+
+def test_counting_forms_alternate_on_one_workspace(oracle):
+    """Per-row (>= 4096 tiles) and per-tile (< 4096 tiles) counting alternating on one
+    rasterizer: each binning must leave the count array clear for the next projection,
+    whichever form that projection uses."""
+    from paper_2603_09632_gb300.render import Rasterizer
+    rast = Rasterizer(U.device())
+    big = _large_frame_scene(1090, 1030, n=20_000, seed=33)
+    small = small_room(n=20_000, W=200, H=136, D=4, deg=0, pose=2)
+    for sc, cam in (big, small, big, small):
+        _lists_equal(oracle, sc, cam, rast=rast)
