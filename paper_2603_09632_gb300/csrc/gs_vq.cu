@@ -14,12 +14,14 @@
 // rounded to tf32 (|x - hi - lo| <= 2^-22 |x|), and W E = Whi Ehi + Wlo Ehi + Whi Elo (the
 // dropped Wlo Elo is below 2^-22 of the product).  The split codebook of D = 512 columns
 // does not fit one CTA's shared memory, so above 256 columns a cluster of two CTAs (two
-// SMs) decodes the same tiles, each its half of the columns; the half-norms |F|^2 that the
-// relevance needs are sent to the first CTA through distributed shared memory.  Each CTA
+// SMs) decodes the same tiles, each its half of the columns; the second CTA forms the
+// prompt dots of the relevance and sends them with its half norms |F|^2 to the first CTA
+// through distributed shared memory (st.async completing an mbarrier).  Each CTA
 // keeps two accumulators in tensor memory, so the next tile's MMAs run during this tile's
 // epilogue, and the next weights are fetched while both run.  Every mbarrier wait is
-// bounded; on a timeout the kernel records an error, still meets every cluster barrier its
-// partner will reach, waits (bounded) for its own MMAs, frees its tensor memory and returns.
+// bounded; on a timeout the kernel records an error, finishes its part of the pair's
+// exchange (bounded waits), meets the pair's final cluster barrier, waits (bounded) for its
+// own MMAs, frees its tensor memory and returns.
 #include <algorithm>
 #include <cstdint>
 
@@ -272,11 +274,11 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(smem + sm.bar + 8 * k)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // E t_j for every codeword k over all Dc columns (in the CTA that forms the prompt dots:
-  // the second of a pair, or the only one): the prompts are
-  // staged in the operand area, idle until the codebook and the first tile are staged
-  // (n_text Dc <= 8 Dc floats fit: the A and B areas hold 2 L (128 + Dh) >= 8 Dc floats for
-  // L >= 8 and Dh >= Dc / 2); one warp per codeword, lanes over the columns
+  // E t_j for every codeword k over all Dc columns, in the CTA that forms the prompt dots
+  // (the second of a pair, or the only one).  The prompts are staged in the operand area,
+  // idle until the codebook and the first tile are staged (n_text Dc <= 8 Dc floats fit:
+  // the A and B areas hold 2 L (128 + Dh) >= 8 Dc floats for L >= 8 and Dh >= Dc / 2); one
+  // warp per codeword, lanes over the columns.
   const int ntx = want_rel ? a.n_text : 0;                 // prompts of the relevance
   const int nt = (want_rel && rank == nrank - 1) ? ntx : 0;  // ... whose dots this CTA forms
   if (nt > 0) {
