@@ -509,17 +509,18 @@ __global__ void __launch_bounds__(kVT, 1) k_vq_decode(DecodeArgs a) {
   for (int it = 0; it < n_local; ++it) {
     const int64_t tile = t_begin + it;
     // the MMAs of this tile are done: A is free and accumulator it & 1 is final
+    // (a thread that saw them complete may overwrite their A operand at once; a timeout is
+    // made uniform at the staging barrier)
     const bool ok = mbar_wait(bar, phase);
     phase ^= 1u;
-    if (__syncthreads_or(!ok)) {   // every thread takes the same branch
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && it + 1 < n_local) stage_a();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (__syncthreads_or(!ok)) {   // next A staged; every thread takes the same branch
       failed = true;
       break;
     }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (it + 1 < n_local) stage_a();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();   // next A staged
     if (it + 1 < n_local && t == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       issue((it + 1) & 1);   // runs during this tile's epilogue
