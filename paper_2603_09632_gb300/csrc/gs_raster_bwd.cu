@@ -462,18 +462,46 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
             sz = fmaf(w, e.w, sz);
             }
           }
+          // the ten sums over the G = 16 lanes of Gaussian j by a reduce-scatter (each level
+          // halves the values a lane carries: 5 + 3 + 2 + 1 shuffles instead of 4 x 10), then
+          // every lane reads the ten totals from the lanes holding them (0 1 2 4 5 8 9 10 12 13)
+          static_assert(G == 16, "the reduce-scatter is laid out for 16 lanes per Gaussian");
+          {
+            const float v[10] = {mx, my, mxx, mxy, myy, so, sr, sg, sb, sz};
+            float r1[6], r2[4], r3[2];
   #pragma unroll
-          for (int o = G / 2; o > 0; o >>= 1) {
-            mx += __shfl_xor_sync(0xffffffffu, mx, o);
-            my += __shfl_xor_sync(0xffffffffu, my, o);
-            mxx += __shfl_xor_sync(0xffffffffu, mxx, o);
-            mxy += __shfl_xor_sync(0xffffffffu, mxy, o);
-            myy += __shfl_xor_sync(0xffffffffu, myy, o);
-            so += __shfl_xor_sync(0xffffffffu, so, o);
-            sr += __shfl_xor_sync(0xffffffffu, sr, o);
-            sg += __shfl_xor_sync(0xffffffffu, sg, o);
-            sb += __shfl_xor_sync(0xffffffffu, sb, o);
-            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+            for (int k = 0; k < 5; ++k) {
+              const bool hi = pg & 8;
+              const float send = hi ? v[k] : v[k + 5], keep = hi ? v[k + 5] : v[k];
+              r1[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+            r1[5] = 0.f;
+  #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const bool hi = pg & 4;
+              const float send = hi ? r1[k] : r1[k + 3], keep = hi ? r1[k + 3] : r1[k];
+              r2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            r2[3] = 0.f;
+  #pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              const bool hi = pg & 2;
+              const float send = hi ? r2[k] : r2[k + 2], keep = hi ? r2[k + 2] : r2[k];
+              r3[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+            }
+            const bool hi = pg & 1;
+            const float r4 = (hi ? r3[1] : r3[0]) + __shfl_xor_sync(0xffffffffu, hi ? r3[0] : r3[1], 1);
+            const int base = lane & 16;
+            mx = __shfl_sync(0xffffffffu, r4, base + 0);
+            my = __shfl_sync(0xffffffffu, r4, base + 1);
+            mxx = __shfl_sync(0xffffffffu, r4, base + 2);
+            mxy = __shfl_sync(0xffffffffu, r4, base + 4);
+            myy = __shfl_sync(0xffffffffu, r4, base + 5);
+            so = __shfl_sync(0xffffffffu, r4, base + 8);
+            sr = __shfl_sync(0xffffffffu, r4, base + 9);
+            sg = __shfl_sync(0xffffffffu, r4, base + 10);
+            sb = __shfl_sync(0xffffffffu, r4, base + 12);
+            sz = __shfl_sync(0xffffffffu, r4, base + 13);
           }
           if (pg == 0 && j < bc) {
             const float4 r0 = s_r0[jb0 + j];
