@@ -44,6 +44,8 @@ def test_mix_equals_alone():
     for i in range(9):
         s = i % 3
         W, H = RES[rng.integers(len(RES))]
+        if i == 4:   # a frame of >= 4096 tiles: its projection counts tiles by row differences
+            W, H = 1088, 1024
         cam = S.room_trajectory(12, W, H, 0.9 * W, seed=100 + i)[int(rng.integers(12))]
         D = scenes[s].n_feat
         out = _outputs(torch, dev, cam, D)
