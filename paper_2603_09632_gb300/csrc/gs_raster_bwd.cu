@@ -13,8 +13,9 @@
 // taken in chunks of 256 entries; each chunk is gathered once, entries that no pixel of
 // the tile can blend are dropped (conservative test, outputs unchanged) and the rest are
 // compacted into shared memory.  The compacted chunk is processed in batches of B
-// Gaussians.  Phase 1 (one thread per pixel) writes w and dL/do of each (pixel, Gaussian)
-// pair to shared memory (dL/dsigma = -o dL/do where the alpha cap does not hold, so it is
+// Gaussians.  Phase 1 (one thread per pixel, branch-free over the batch's live entries, with
+// g.x_i formed ahead of the blend decision so that it overlaps the opacity evaluation)
+// writes w and dL/do of each (pixel, Gaussian) pair to shared memory (dL/dsigma = -o dL/do where the alpha cap does not hold, so it is
 // not stored).  Phase 2 reduces over the 256 pixels of the
 // tile: the feature gradient is the contraction W^T g_F with 4x4 register blocks (pixel
 // parts summed through per-warp partials in shared memory, in a fixed order), and
@@ -300,46 +301,49 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
 
         // phase 1: per pixel, reverse over the batch
         for (int j = B - 1; j >= 0; --j) {
+          if (!(live >> j & 1u)) continue;   // entries not live for this strip are never read
           float w = 0.f, go = 0.f;
-          if ((live >> j & 1u) && s_orig[jb0 + j] < nc) {
-            const float4 r0 = s_r0[jb0 + j];
-            const float4 r1 = s_r1[jb0 + j];
-            const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-            if (sigma >= 0.f && sigma <= r1.w) {
-              const float G = blend_gauss(sigma);
-              const float oG = __fmul_rn(r1.y, G);
-              const float a = fminf(kAlphaMax, oG);
-              if (a >= kAlphaMin) {
-                const float inv = __fdividef(1.f, 1.f - a);
-                T = T * inv;                        // T_i
-                w = a * T;
-                if constexpr (!FO) {
-                const float4 r2 = s_r2[jb0 + j];
-                float2 d01 = mul2(make_float2(gC0, gC1), make_float2(r2.x, r2.y));
-                float2 d23 = mul2(make_float2(gC2, gD), make_float2(r2.z, r1.z));
-                if constexpr (DP > 0) {
-                  const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
+          const float4 r0 = s_r0[jb0 + j];
+          const float4 r1 = s_r1[jb0 + j];
+          // g.x_i does not depend on the blend decisions below: it is formed on every lane
+          // of a live entry, so that it overlaps the opacity evaluation
+          float dot = 0.f;
+          if constexpr (!FO) {
+            const float4 r2 = s_r2[jb0 + j];
+            float2 d01 = mul2(make_float2(gC0, gC1), make_float2(r2.x, r2.y));
+            float2 d23 = mul2(make_float2(gC2, gD), make_float2(r2.z, r1.z));
+            if constexpr (DP > 0) {
+              const float4* f4 = reinterpret_cast<const float4*>(s_f + j * DP);
   #pragma unroll
-                  for (int q = 0; q < DP / 4; ++q) {
-                    const float4 f = f4[q];
-                    d01 = fma2(gF[2 * q], make_float2(f.x, f.y), d01);
-                    d23 = fma2(gF[2 * q + 1], make_float2(f.z, f.w), d23);
-                  }
-                }
-                const float dot = (d01.x + d01.y) + (d23.x + d23.y);
-                const float galpha = T * (dot - s_run) + gAT * inv;
-                s_run = a * dot + (1.f - a) * s_run;
-                // dL/do = galpha G; dL/dsigma = -galpha a = -o dL/do (phase 2b scales the
-                // moments of dL/do by -o); both zero where the 0.99 cap holds alpha
-                if (oG <= kAlphaMax) go = galpha * G;
-                }
+              for (int q = 0; q < DP / 4; ++q) {
+                const float4 f = f4[q];
+                d01 = fma2(gF[2 * q], make_float2(f.x, f.y), d01);
+                d23 = fma2(gF[2 * q + 1], make_float2(f.z, f.w), d23);
               }
             }
+            dot = (d01.x + d01.y) + (d23.x + d23.y);
           }
-          if (live >> j & 1u) {   // entries not live for this strip are never read
-            s_W[j * kWS + t] = w;
-            if constexpr (!FO) s_GO[j * kWS + t] = go;
+          const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+          // branch-free: every lane evaluates, and the blend decision selects the updates
+          // (the same values as the branches would give), so consecutive entries overlap
+          const float G = blend_gauss(sigma);
+          const float oG = __fmul_rn(r1.y, G);
+          const float a = fminf(kAlphaMax, oG);
+          const bool ok = (s_orig[jb0 + j] < nc) & (sigma >= 0.f) & (sigma <= r1.w) & (a >= kAlphaMin);
+          const float inv = __fdividef(1.f, 1.f - a);
+          const float Tn = T * inv;                 // T_i
+          if (ok) w = a * Tn;
+          if constexpr (!FO) {
+            const float galpha = Tn * (dot - s_run) + gAT * inv;
+            const float sn = a * dot + (1.f - a) * s_run;
+            // dL/do = galpha G; dL/dsigma = -galpha a = -o dL/do (phase 2b scales the
+            // moments of dL/do by -o); both zero where the 0.99 cap holds alpha
+            if (ok && oG <= kAlphaMax) go = galpha * G;
+            if (ok) s_run = sn;
           }
+          if (ok) T = Tn;
+          s_W[j * kWS + t] = w;
+          if constexpr (!FO) s_GO[j * kWS + t] = go;
         }
         __syncthreads();
 

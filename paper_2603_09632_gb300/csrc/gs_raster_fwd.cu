@@ -9,7 +9,9 @@
 // storage costs no per-pixel conversion).  Each warp owns an 8 x 4 pixel strip and visits
 // only the batch entries that can reach it (ballot over a per-strip box test), stops when
 // all its pixels have terminated (checked before each group of 32 candidates), and the
-// CTA stops when all 128 pixels have.
+// CTA stops when all 128 pixels have.  The walk is software-pipelined by one entry: the
+// colour, depth and feature terms of an entry are added while the next entry's opacity is
+// evaluated, so the accumulation and the evaluation chain overlap in one warp.
 #include <algorithm>
 
 #include "gs_blend.cuh"
@@ -133,6 +135,24 @@ k_raster_fwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq, FeatLoss fl
     int last = 0;     // 1 + list position of the last blended entry
     int lastj = -1;   // its batch slot, resolved to a list position once per batch
     bool done = !inside;
+    int pj = -1;      // entry whose terms are still to be added (software pipeline)
+    float pw = 0.f;   // its weight for this pixel (0 where it does not blend)
+    float pz = 0.f;   // its depth
+    auto accumulate = [&](int j, float w, float z) {
+      const float4 r2 = s_r2[j];
+      const float2 w2 = splat2(w);
+      c01 = fma2(w2, make_float2(r2.x, r2.y), c01);
+      c2d = fma2(w2, make_float2(r2.z, z), c2d);
+      if constexpr (DP > 0) {
+        const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * DP);
+#pragma unroll
+        for (int q = 0; q < DP / 4; ++q) {
+          const float4 f = f4[q];
+          acc[2 * q] = fma2(w2, make_float2(f.x, f.y), acc[2 * q]);
+          acc[2 * q + 1] = fma2(w2, make_float2(f.z, f.w), acc[2 * q + 1]);
+        }
+      }
+    };
 
     for (int b0 = start; b0 < end; b0 += kB) {
       if (__syncthreads_count(done) == kB) break;
@@ -171,45 +191,34 @@ k_raster_fwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq, FeatLoss fl
                               q0.x, q0.y, q0.z, q0.w, q1.x) <= q1.w;
         }
         unsigned live = __ballot_sync(0xffffffffu, hit);
-      while (live) {
-        const int j = g0 + __ffs(live) - 1;
-        live &= live - 1;
-        const float4 r0 = s_r0[j];
-        const float4 r1 = s_r1[j];
-        float w = 0.f;
-        if (!done) {
+        while (live) {
+          const int j = g0 + __ffs(live) - 1;
+          live &= live - 1;
+          const float4 r0 = s_r0[j];
+          const float4 r1 = s_r1[j];
           const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-          if (sigma >= 0.f && sigma <= r1.w) {
-            const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
-            if (a >= kAlphaMin) {
-              const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
-              if (Tn < kTMin) {
-                done = true;
-              } else {
-                w = __fmul_rn(a, T);
-                T = Tn;
-                lastj = j;
-              }
+          const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
+          // the previous entry is accumulated while this one's opacity is evaluated (the
+          // two are independent; each pixel still adds its terms in list order)
+          if (pj >= 0) accumulate(pj, pw, pz);
+          float w = 0.f;
+          if (!done && sigma >= 0.f && sigma <= r1.w && a >= kAlphaMin) {
+            const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+            if (Tn < kTMin) {
+              done = true;
+            } else {
+              w = __fmul_rn(a, T);
+              T = Tn;
+              lastj = j;
             }
           }
-        }
-        {   // accumulate unconditionally: w = 0 adds nothing, and live entries almost always blend
-          const float4 r2 = s_r2[j];
-          const float2 w2 = splat2(w);
-          c01 = fma2(w2, make_float2(r2.x, r2.y), c01);
-          c2d = fma2(w2, make_float2(r2.z, r1.z), c2d);
-          if constexpr (DP > 0) {
-            const float4* f4 = reinterpret_cast<const float4*>(s_feat + j * DP);
-#pragma unroll
-            for (int q = 0; q < DP / 4; ++q) {
-              const float4 f = f4[q];
-              acc[2 * q] = fma2(w2, make_float2(f.x, f.y), acc[2 * q]);
-              acc[2 * q + 1] = fma2(w2, make_float2(f.z, f.w), acc[2 * q + 1]);
-            }
-          }
+          pj = j;
+          pw = w;
+          pz = r1.z;
         }
       }
-      }
+      if (pj >= 0) accumulate(pj, pw, pz);   // before the batch's features are replaced
+      pj = -1;
       if (lastj >= 0) { last = s_orig[lastj] + 1; lastj = -1; }
     }
     if (inside) {
