@@ -212,6 +212,21 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
     int last = 0;     // 1 + list position of the last blended entry
     int lastk = -1;   // its batch slot, resolved once per batch
     bool done = !it.in_img;
+    auto accumulate = [&](int k, float w, float z) {
+      const float4 r2 = s_r[3 * k + 2];
+      const float2 w2 = splat2(w);
+      c01 = fma2(w2, make_float2(r2.x, r2.y), c01);
+      c2d = fma2(w2, make_float2(r2.z, z), c2d);
+      if constexpr (DP > 0) {
+        const float4* f4 = reinterpret_cast<const float4*>(s_f + k * DP);
+#pragma unroll
+        for (int e = 0; e < DP / 4; ++e) {
+          const float4 f = f4[e];
+          acc[2 * e] = fma2(w2, make_float2(f.x, f.y), acc[2 * e]);
+          acc[2 * e + 1] = fma2(w2, make_float2(f.z, f.w), acc[2 * e + 1]);
+        }
+      }
+    };
 
     for (int b0 = start; b0 < end; b0 += 32) {
       if (__all_sync(kFull, done)) break;
@@ -219,42 +234,33 @@ k_grid_fwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
       __syncwarp();
       if constexpr (DP > 0) stage_feats<DP, BF16>(feats, D, s_id, nk, s_f);
       __syncwarp();
+      int pk = -1;        // entry whose terms are still to be added (software pipeline)
+      float pw = 0.f, pz = 0.f;
+      bool pany = false;  // some sample of the warp blends it
       for (int k = 0; k < nk; ++k) {
         const float4 r0 = s_r[3 * k];
         const float4 r1 = s_r[3 * k + 1];
+        const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+        const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
+        // the previous entry is accumulated while this one's opacity is evaluated
+        if (pany) accumulate(pk, pw, pz);
         float w = 0.f;
-        if (!done) {
-          const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-          if (sigma >= 0.f && sigma <= r1.w) {
-            const float a = fminf(kAlphaMax, __fmul_rn(r1.y, blend_gauss(sigma)));
-            if (a >= kAlphaMin) {
-              const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
-              if (Tn < kTMin) {
-                done = true;
-              } else {
-                w = __fmul_rn(a, T);
-                T = Tn;
-                lastk = k;
-              }
-            }
+        if (!done && sigma >= 0.f && sigma <= r1.w && a >= kAlphaMin) {
+          const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+          if (Tn < kTMin) {
+            done = true;
+          } else {
+            w = __fmul_rn(a, T);
+            T = Tn;
+            lastk = k;
           }
         }
-        if (__any_sync(kFull, w != 0.f)) {
-          const float4 r2 = s_r[3 * k + 2];
-          const float2 w2 = splat2(w);
-          c01 = fma2(w2, make_float2(r2.x, r2.y), c01);
-          c2d = fma2(w2, make_float2(r2.z, r1.z), c2d);
-          if constexpr (DP > 0) {
-            const float4* f4 = reinterpret_cast<const float4*>(s_f + k * DP);
-#pragma unroll
-            for (int e = 0; e < DP / 4; ++e) {
-              const float4 f = f4[e];
-              acc[2 * e] = fma2(w2, make_float2(f.x, f.y), acc[2 * e]);
-              acc[2 * e + 1] = fma2(w2, make_float2(f.z, f.w), acc[2 * e + 1]);
-            }
-          }
-        }
+        pk = k;
+        pw = w;
+        pz = r1.z;
+        pany = __any_sync(kFull, w != 0.f);
       }
+      if (pany) accumulate(pk, pw, pz);   // before the staging slots are refilled
       if (lastk >= 0) { last = s_orig[lastk] + 1; lastk = -1; }
       __syncwarp();   // the staging slots are refilled by the next batch
     }
@@ -492,40 +498,42 @@ k_grid_bwd(CamDev cam, TileQueue tq, int CH, const GaussRec* __restrict__ rec,
         float w = 0.f, gs = 0.f, go = 0.f;
         const float4 r0 = s_r[3 * k];
         const float4 r1 = s_r[3 * k + 1];
-        if (it.in_img && s_orig[k] < nc) {
-          const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
-          if (sigma >= 0.f && sigma <= r1.w) {
-            const float G = blend_gauss(sigma);
-            const float oG = __fmul_rn(r1.y, G);
-            const float a = fminf(kAlphaMax, oG);
-            if (a >= kAlphaMin) {
-              const float inv = __fdividef(1.f, 1.f - a);
-              T = T * inv;   // T_i
-              w = a * T;
-              if constexpr (!FO) {
-                const float4 r2 = s_r[3 * k + 2];
-                float dot = gC0 * r2.x + gC1 * r2.y + gC2 * r2.z + gD * r1.z;
-                if constexpr (DP > 0) {
-                  const float4* f4 = reinterpret_cast<const float4*>(s_f + k * DP);
+        // g.x_i does not depend on the blend decisions: formed first, so that it overlaps
+        // the opacity evaluation, which is branch-free (the decision selects the updates)
+        float dot = 0.f;
+        if constexpr (!FO) {
+          const float4 r2 = s_r[3 * k + 2];
+          float2 d01 = mul2(make_float2(gC0, gC1), make_float2(r2.x, r2.y));
+          float2 d23 = mul2(make_float2(gC2, gD), make_float2(r2.z, r1.z));
+          if constexpr (DP > 0) {
+            const float4* f4 = reinterpret_cast<const float4*>(s_f + k * DP);
 #pragma unroll
-                  for (int e = 0; e < DP / 4; ++e) {
-                    const float4 f = f4[e];
-                    dot = fmaf(gF[4 * e], f.x, dot);
-                    dot = fmaf(gF[4 * e + 1], f.y, dot);
-                    dot = fmaf(gF[4 * e + 2], f.z, dot);
-                    dot = fmaf(gF[4 * e + 3], f.w, dot);
-                  }
-                }
-                const float galpha = T * (dot - s_run) + gAT * inv;
-                s_run = a * dot + (1.f - a) * s_run;
-                if (oG <= kAlphaMax) {
-                  go = galpha * G;
-                  gs = -galpha * a;
-                }
-              }
+            for (int e = 0; e < DP / 4; ++e) {
+              const float4 f = f4[e];
+              d01 = fma2(make_float2(gF[4 * e], gF[4 * e + 1]), make_float2(f.x, f.y), d01);
+              d23 = fma2(make_float2(gF[4 * e + 2], gF[4 * e + 3]), make_float2(f.z, f.w), d23);
             }
           }
+          dot = (d01.x + d01.y) + (d23.x + d23.y);
         }
+        const float sigma = blend_sigma(__fsub_rn(fx, r0.x), __fsub_rn(fy, r0.y), r0.z, r0.w, r1.x);
+        const float G = blend_gauss(sigma);
+        const float oG = __fmul_rn(r1.y, G);
+        const float a = fminf(kAlphaMax, oG);
+        const bool ok = it.in_img & (s_orig[k] < nc) & (sigma >= 0.f) & (sigma <= r1.w) & (a >= kAlphaMin);
+        const float inv = __fdividef(1.f, 1.f - a);
+        const float Tn = T * inv;   // T_i
+        if (ok) w = a * Tn;
+        if constexpr (!FO) {
+          const float galpha = Tn * (dot - s_run) + gAT * inv;
+          const float sn = a * dot + (1.f - a) * s_run;
+          if (ok && oG <= kAlphaMax) {
+            go = galpha * G;
+            gs = -galpha * a;
+          }
+          if (ok) s_run = sn;
+        }
+        if (ok) T = Tn;
         s_W[w_slot(lane, k)] = w;
         const bool any = __any_sync(kFull, w != 0.f);
         if (any) wlive |= 1u << k;
