@@ -372,7 +372,7 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
             for (int ws = 0; ws < NSP; ++ws) {
               const int q0 = p0 + ws * QS;
               const unsigned lv = (s_live[q0 >> 5] >> (4 * jb)) & 15u;
-  #pragma unroll 2
+  #pragma unroll 4
               for (int q = q0; q < (lv ? q0 + QS : q0); q += 4) {
                 float4 wv[4], ev[4];
   #pragma unroll
@@ -446,6 +446,11 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
           float so = 0.f, sr = 0.f, sg = 0.f, sb = 0.f, sz = 0.f;
           // strip by strip: the G lanes of Gaussian j skip whole strips it cannot reach
           constexpr int PPS = 32 / G;   // pixels per strip per lane
+          static_assert(G == 16 && kStripW == 8 && kStripH == 4, "pixel offsets below");
+          // pixel q = 32 ws + pg + 16 u lies at column 8 (ws & 1) + (pg & 7) and row
+          // 4 (ws >> 1) + (pg >> 3) + 2 u of the tile (strip_px / strip_py of q)
+          const float xl = (float)(pg & 7) - 7.5f, yl = (float)(pg >> 3) - 7.5f;
+  #pragma unroll
           for (int ws = 0; ws < kT / 32; ++ws) {
             if (!(s_live[ws] >> j & 1u)) continue;   // uniform over the G lanes of j
   #pragma unroll
@@ -453,7 +458,7 @@ k_raster_bwd(const __grid_constant__ RasterJobs<NJ> J, TileQueue tq) {
             const int q = ws * 32 + pg + u * G;
             const float w = s_W[j * kWS + q], go = s_GO[j * kWS + q];
             const float4 e = s_E4[q];
-            const float x = (float)strip_px(q) - 7.5f, y = (float)strip_py(q) - 7.5f;
+            const float x = xl + (float)(8 * (ws & 1)), y = yl + (float)(4 * (ws >> 1) + 2 * u);
             mx = fmaf(go, x, mx);
             my = fmaf(go, y, my);
             mxx = fmaf(go * x, x, mxx);
