@@ -75,3 +75,67 @@ def test_binding_names_match_header():
     src = open(os.path.join(ROOT, "paper_2603_09632_gb300", "_lib.py")).read()
     for n in ("gs_project", "gs_bin_tiles", "gs_render_fwd", "gs_render_bwd"):
         assert f"def {n}(" in src
+
+
+def _header_signatures():
+    """name -> (return kind, [parameter kinds]) of every function gs.h declares."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "gs.h")).read(), flags=re.S)
+    out = {}
+    for ret, name, args in re.findall(r"\b(gs_status|void|int64_t|const char\s*\*)\s+(gs_\w+)\s*\(([^)]*)\)\s*;", src):
+        params = [a.strip() for a in args.split(",") if a.strip() and a.strip() != "void"]
+        out[name] = (_c_kind(ret), [_c_kind(p) for p in params])
+    return out
+
+
+def _c_kind(decl):
+    """Kind of a C type (as it crosses the ABI): pointer, i32, i64, u64, f32 or none."""
+    d = " ".join(decl.split())
+    if "*" in d:
+        return "ptr"
+    t = d.rsplit(" ", 1)[0] if " " in d else d
+    t = t.replace("const ", "")
+    if t in ("void",):
+        return "none"
+    if t in ("int", "int32_t", "gs_status"):
+        return "i32"
+    return {"int64_t": "i64", "uint64_t": "u64", "float": "f32", "double": "f64"}[t]
+
+
+def _binding_signatures():
+    """name -> (return kind, [argument kinds]) of the ctypes declarations in _lib.py, read
+    from its source (the signature table of its loader) without loading the library."""
+    import ast
+    src = open(os.path.join(ROOT, "paper_2603_09632_gb300", "_lib.py")).read()
+    table = None
+    for node in ast.walk(ast.parse(src)):
+        if isinstance(node, ast.Assign) and any(getattr(t, "id", None) == "sig" for t in node.targets):
+            table = node.value
+    assert isinstance(table, ast.Dict)
+
+    class _C:   # the ctypes names the table uses, mapped to ABI kinds
+        c_void_p = c_char_p = "ptr"
+        c_int = c_int32 = "i32"
+        c_int64 = "i64"
+        c_uint64 = "u64"
+        c_float = "f32"
+        c_double = "f64"
+
+        @staticmethod
+        def POINTER(_):
+            return "ptr"
+
+    env = {"C": _C, "P": "ptr", "i64": "i64", "i32": "i32", "st": "i32", "None": None}
+    out = {}
+    for k, v in zip(table.keys, table.values):
+        args, res = eval(compile(ast.Expression(v), "<sig>", "eval"), env)
+        out[k.value] = ("none" if res is None else res, list(args))
+    return out
+
+
+def test_binding_signatures_match_header():
+    # every function of gs.h has a ctypes declaration with the same number and kinds of
+    # arguments (pointer, 32- or 64-bit integer, float, double) and the same return kind
+    hdr, bind = _header_signatures(), _binding_signatures()
+    assert set(hdr) == set(bind), (sorted(set(hdr) - set(bind)), sorted(set(bind) - set(hdr)))
+    bad = {n: (hdr[n], bind[n]) for n in hdr if hdr[n] != bind[n]}
+    assert not bad, bad
